@@ -1,0 +1,108 @@
+"""Brute-force dense operators for tiny grids (a pin for the structured oracle).
+
+A and B of Eqs. 33-34 are assembled entry by entry with explicit loops over
+the Yee samples, as (6 components flattened) x (6 components flattened)
+matrices; the original splitting formulae are then applied with dense
+``numpy.linalg.solve``.  Rows of tangential wall E samples are zero (PEC), so
+those samples stay at their initial value 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .grid import COMPS, Grid
+
+
+def layout(grid: Grid):
+    off = {}
+    n = 0
+    for c in COMPS:
+        off[c] = n
+        sk, sj, si = grid.shape(c)
+        n += sk * sj * si
+    return off, n
+
+
+def to_vec(grid: Grid, u: dict) -> np.ndarray:
+    return np.concatenate([u[c].ravel() for c in COMPS])
+
+
+def from_vec(grid: Grid, x: np.ndarray) -> dict:
+    off, _ = layout(grid)
+    out = {}
+    for c in COMPS:
+        sh = grid.shape(c)
+        out[c] = x[off[c]: off[c] + sh[0] * sh[1] * sh[2]].reshape(sh).copy()
+    return out
+
+
+def assemble(grid: Grid, mat: dict):
+    """Dense A (Eq. 33) and B (Eq. 34)."""
+    off, n = layout(grid)
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    dx, dy, dz = grid.dx, grid.dy, grid.dz
+    A = np.zeros((n, n))
+    B = np.zeros((n, n))
+
+    def idx(c, k, j, i):
+        sk, sj, si = grid.shape(c)
+        return off[c] + (k * sj + j) * si + i
+
+    def loop(c):
+        sk, sj, si = grid.shape(c)
+        for k in range(sk):
+            for j in range(sj):
+                for i in range(si):
+                    yield k, j, i
+
+    for k, j, i in loop("ex"):
+        if 1 <= j <= ny - 1 and 1 <= k <= nz - 1:
+            r = idx("ex", k, j, i); e = mat["ex"][k, j, i]
+            A[r, idx("hz", k, j, i)] += 1 / (e * dy); A[r, idx("hz", k, j - 1, i)] -= 1 / (e * dy)
+            B[r, idx("hy", k, j, i)] -= 1 / (e * dz); B[r, idx("hy", k - 1, j, i)] += 1 / (e * dz)
+    for k, j, i in loop("ey"):
+        if 1 <= i <= nx - 1 and 1 <= k <= nz - 1:
+            r = idx("ey", k, j, i); e = mat["ey"][k, j, i]
+            A[r, idx("hx", k, j, i)] += 1 / (e * dz); A[r, idx("hx", k - 1, j, i)] -= 1 / (e * dz)
+            B[r, idx("hz", k, j, i)] -= 1 / (e * dx); B[r, idx("hz", k, j, i - 1)] += 1 / (e * dx)
+    for k, j, i in loop("ez"):
+        if 1 <= i <= nx - 1 and 1 <= j <= ny - 1:
+            r = idx("ez", k, j, i); e = mat["ez"][k, j, i]
+            A[r, idx("hy", k, j, i)] += 1 / (e * dx); A[r, idx("hy", k, j, i - 1)] -= 1 / (e * dx)
+            B[r, idx("hx", k, j, i)] -= 1 / (e * dy); B[r, idx("hx", k, j - 1, i)] += 1 / (e * dy)
+    for k, j, i in loop("hx"):
+        r = idx("hx", k, j, i); m = mat["hx"][k, j, i]
+        A[r, idx("ey", k + 1, j, i)] += 1 / (m * dz); A[r, idx("ey", k, j, i)] -= 1 / (m * dz)
+        B[r, idx("ez", k, j + 1, i)] -= 1 / (m * dy); B[r, idx("ez", k, j, i)] += 1 / (m * dy)
+    for k, j, i in loop("hy"):
+        r = idx("hy", k, j, i); m = mat["hy"][k, j, i]
+        A[r, idx("ez", k, j, i + 1)] += 1 / (m * dx); A[r, idx("ez", k, j, i)] -= 1 / (m * dx)
+        B[r, idx("ex", k + 1, j, i)] -= 1 / (m * dz); B[r, idx("ex", k, j, i)] += 1 / (m * dz)
+    for k, j, i in loop("hz"):
+        r = idx("hz", k, j, i); m = mat["hz"][k, j, i]
+        A[r, idx("ex", k, j + 1, i)] += 1 / (m * dy); A[r, idx("ex", k, j, i)] -= 1 / (m * dy)
+        B[r, idx("ey", k, j, i + 1)] -= 1 / (m * dx); B[r, idx("ey", k, j, i)] += 1 / (m * dx)
+    return A, B
+
+
+def cn(Oi, Oe, tau, x, f=None):
+    """(I - tau Oi) x' = (I + tau Oe) x (+ tau f), dense."""
+    I = np.eye(Oi.shape[0])
+    rhs = x + tau * (Oe @ x)
+    if f is not None:
+        rhs = rhs + tau * f
+    return np.linalg.solve(I - tau * Oi, rhs)
+
+
+def adi_step(A, B, dt, x, f=None):
+    return cn(B, A, dt / 2, cn(A, B, dt / 2, x, f), f)
+
+
+def lod1_step(A, B, dt, x, f=None):
+    return cn(B, B, dt / 2, cn(A, A, dt / 2, x, f), f)
+
+
+def ss2_step(A, B, dt, x, f=None):
+    x = cn(A, A, dt / 4, x, f)
+    x = cn(B, B, dt / 2, x, f)
+    return cn(A, A, dt / 4, x, f)

@@ -1,0 +1,241 @@
+"""Yee grid, materials and the Maxwell splitting operators of the oracle.
+
+Sec. III of the paper: lossless isotropic medium, u = (Ex, Ey, Ez, Hx, Hy, Hz),
+splitting operators A (Eq. 33) and B (Eq. 34) built from first differences
+d_x, d_y, d_z, and b = dt/(2 eps), d = dt/(2 mu) (Eq. 36).
+
+Readings of what the paper leaves open (each is a documented choice):
+* differences are the standard Yee second-order central differences between
+  staggered samples (sample layout in ``workloads``);
+* the walls are perfect electric conductors: tangential E samples on the six
+  walls are fixed at zero and are not unknowns;
+* for inhomogeneous media, eps at an E sample is the mean of the (up to four)
+  cells sharing that edge, mu at an H sample the mean of the (up to two)
+  cells sharing that face; eliminating H then gives (b_j/2) d(d d w) with b at
+  the E sample and d at the H faces, which reduces to the paper's (bd/2) d^2
+  for a homogeneous medium.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from .tridiag import thomas
+
+C0 = 299792458.0
+MU0 = 1.25663706212e-6
+EPS0 = 1.0 / (MU0 * C0 * C0)
+
+E_COMPS = ("ex", "ey", "ez")
+H_COMPS = ("hx", "hy", "hz")
+COMPS = E_COMPS + H_COMPS
+AXIS = {"x": 2, "y": 1, "z": 0}          # array axis of each direction ([k, j, i] layout)
+
+# The three (E, H, line axis, sign) pairs of each operator.  A (Eq. 33) holds
+# +(1/eps) d_y Hz, +(1/eps) d_z Hx, +(1/eps) d_x Hy in its E rows and
+# +(1/mu) d_z Ey, +(1/mu) d_x Ez, +(1/mu) d_y Ex in its H rows; B (Eq. 34)
+# holds the other half of the curls with a minus sign.
+PAIRS = {
+    "A": (("ex", "hz", "y", +1.0), ("ey", "hx", "z", +1.0), ("ez", "hy", "x", +1.0)),
+    "B": (("ex", "hy", "z", -1.0), ("ey", "hz", "x", -1.0), ("ez", "hx", "y", -1.0)),
+}
+
+
+def shape(comp, nx, ny, nz):
+    return {
+        "ex": (nz + 1, ny + 1, nx), "ey": (nz + 1, ny, nx + 1), "ez": (nz, ny + 1, nx + 1),
+        "hx": (nz, ny, nx + 1), "hy": (nz, ny + 1, nx), "hz": (nz + 1, ny, nx),
+    }[comp]
+
+
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+
+    @property
+    def spacing(self):
+        return {"x": self.dx, "y": self.dy, "z": self.dz}
+
+    def shape(self, comp):
+        return shape(comp, self.nx, self.ny, self.nz)
+
+    def zeros(self):
+        return {c: np.zeros(self.shape(c)) for c in COMPS}
+
+    def dt_cfl(self) -> float:
+        """Explicit-Yee stability limit 1/(c0 sqrt(sum 1/d^2)) over the active
+        directions (x, y only when nz == 1)."""
+        s = 1.0 / self.dx ** 2 + 1.0 / self.dy ** 2
+        if self.nz > 1:
+            s += 1.0 / self.dz ** 2
+        return 1.0 / (C0 * math.sqrt(s))
+
+    def cell_volume(self) -> float:
+        return self.dx * self.dy * self.dz
+
+    # -- PEC -----------------------------------------------------------------
+    def e_interior_mask(self, comp) -> np.ndarray:
+        """1 where an E sample is an unknown, 0 on the walls (tangential E)."""
+        m = np.ones(self.shape(comp))
+        if comp == "ex":
+            m[:, 0, :] = 0; m[:, -1, :] = 0; m[0] = 0; m[-1] = 0
+        elif comp == "ey":
+            m[:, :, 0] = 0; m[:, :, -1] = 0; m[0] = 0; m[-1] = 0
+        elif comp == "ez":
+            m[:, :, 0] = 0; m[:, :, -1] = 0; m[:, 0, :] = 0; m[:, -1, :] = 0
+        return m
+
+
+# ---------------------------------------------------------------------------
+# Materials
+# ---------------------------------------------------------------------------
+
+def _avg(cells: np.ndarray, pad: tuple, windows) -> np.ndarray:
+    """Mean of the in-domain cells in each window.  ``pad`` pads the cell
+    array by one on the axes flagged; ``windows`` lists the slices to add."""
+    padw = [(1, 1) if p else (0, 0) for p in pad]
+    val = np.pad(cells, padw)
+    cnt = np.pad(np.ones_like(cells), padw)
+    s = sum(val[w] for w in windows)
+    n = sum(cnt[w] for w in windows)
+    return s / n
+
+
+def material_at_samples(grid: Grid, eps_r_cell=None, mu_r_cell=None) -> dict:
+    """Absolute eps at every E sample and mu at every H sample."""
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    er = np.ones((nz, ny, nx)) if eps_r_cell is None else np.asarray(eps_r_cell, dtype=np.float64)
+    mr = np.ones((nz, ny, nx)) if mu_r_cell is None else np.asarray(mu_r_cell, dtype=np.float64)
+    b = slice(None)
+    out = {}
+    # Ex edge (i+1/2, j, k): cells (i, j-1..j, k-1..k)
+    out["ex"] = EPS0 * _avg(er, (1, 1, 0), [(slice(0, nz + 1), slice(0, ny + 1), b),
+                                            (slice(1, nz + 2), slice(0, ny + 1), b),
+                                            (slice(0, nz + 1), slice(1, ny + 2), b),
+                                            (slice(1, nz + 2), slice(1, ny + 2), b)])
+    # Ey edge (i, j+1/2, k): cells (i-1..i, j, k-1..k)
+    out["ey"] = EPS0 * _avg(er, (1, 0, 1), [(slice(0, nz + 1), b, slice(0, nx + 1)),
+                                            (slice(1, nz + 2), b, slice(0, nx + 1)),
+                                            (slice(0, nz + 1), b, slice(1, nx + 2)),
+                                            (slice(1, nz + 2), b, slice(1, nx + 2))])
+    # Ez edge (i, j, k+1/2): cells (i-1..i, j-1..j, k)
+    out["ez"] = EPS0 * _avg(er, (0, 1, 1), [(b, slice(0, ny + 1), slice(0, nx + 1)),
+                                            (b, slice(1, ny + 2), slice(0, nx + 1)),
+                                            (b, slice(0, ny + 1), slice(1, nx + 2)),
+                                            (b, slice(1, ny + 2), slice(1, nx + 2))])
+    # Hx face (i, j+1/2, k+1/2): cells (i-1..i, j, k)
+    out["hx"] = MU0 * _avg(mr, (0, 0, 1), [(b, b, slice(0, nx + 1)), (b, b, slice(1, nx + 2))])
+    # Hy face (i+1/2, j, k+1/2): cells (i, j-1..j, k)
+    out["hy"] = MU0 * _avg(mr, (0, 1, 0), [(b, slice(0, ny + 1), b), (b, slice(1, ny + 2), b)])
+    # Hz face (i+1/2, j+1/2, k): cells (i, j, k-1..k)
+    out["hz"] = MU0 * _avg(mr, (1, 0, 0), [(slice(0, nz + 1), b, b), (slice(1, nz + 2), b, b)])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# First differences between staggered samples
+# ---------------------------------------------------------------------------
+
+def diff_h_to_e(h: np.ndarray, axis: int, spacing: float, e_shape) -> np.ndarray:
+    """d/d(eta) of an H component at the E samples: (H[j] - H[j-1]) / d for
+    the interior E nodes j = 1..N-1 along ``axis``; zero at the two end nodes
+    (the PEC mask later zeroes every wall sample anyway)."""
+    out = np.zeros(e_shape)
+    n = e_shape[axis] - 1          # number of cells along the line
+    hi = [slice(None)] * 3
+    lo = [slice(None)] * 3
+    tgt = [slice(None)] * 3
+    hi[axis] = slice(1, n)
+    lo[axis] = slice(0, n - 1)
+    tgt[axis] = slice(1, n)
+    out[tuple(tgt)] = (h[tuple(hi)] - h[tuple(lo)]) / spacing
+    return out
+
+
+def diff_e_to_h(e: np.ndarray, axis: int, spacing: float) -> np.ndarray:
+    """d/d(eta) of an E component at the H samples: (E[j+1] - E[j]) / d."""
+    hi = [slice(None)] * 3
+    lo = [slice(None)] * 3
+    hi[axis] = slice(1, None)
+    lo[axis] = slice(0, -1)
+    return (e[tuple(hi)] - e[tuple(lo)]) / spacing
+
+
+def apply_op(grid: Grid, mat: dict, op: str, u: dict) -> dict:
+    """O u for O = A (Eq. 33) or B (Eq. 34), PEC walls applied."""
+    out = {c: np.zeros(grid.shape(c)) for c in COMPS}
+    for ec, hc, ax, sgn in PAIRS[op]:
+        a = AXIS[ax]
+        sp = grid.spacing[ax]
+        out[ec] += sgn * diff_h_to_e(u[hc], a, sp, grid.shape(ec)) / mat[ec]
+        out[hc] += sgn * diff_e_to_h(u[ec], a, sp) / mat[hc]
+    for ec in E_COMPS:
+        out[ec] *= grid.e_interior_mask(ec)
+    return out
+
+
+def add(u: dict, v: dict, alpha: float = 1.0) -> dict:
+    return {c: u[c] + alpha * v[c] for c in u}
+
+
+def scale(u: dict, alpha: float) -> dict:
+    return {c: alpha * u[c] for c in u}
+
+
+# ---------------------------------------------------------------------------
+# Tridiagonal line systems
+# ---------------------------------------------------------------------------
+
+def line_operator_coeffs(gE: np.ndarray, gH: np.ndarray, axis: int, spacing: float):
+    """Coefficients of the line operator w -> gE_j * [gH_{j+1/2}(w_{j+1}-w_j)
+    - gH_{j-1/2}(w_j - w_{j-1})] / d^2 at the interior nodes j = 1..N-1, with
+    the system axis moved last.  Returns (lower, centre, upper) such that the
+    operator is lower*w_{j-1} + centre*w_j + upper*w_{j+1}."""
+    ge = np.moveaxis(gE, axis, -1)[..., 1:-1]
+    gh = np.moveaxis(gH, axis, -1)
+    gm = gh[..., :-1]             # face j-1/2 of node j (j = 1..N-1)
+    gp = gh[..., 1:]              # face j+1/2
+    s2 = spacing * spacing
+    lower = ge * gm / s2
+    upper = ge * gp / s2
+    centre = -(lower + upper)
+    return lower, centre, upper
+
+
+def solve_lines(alpha: float, lower, centre, upper, rhs_e: np.ndarray, axis: int) -> np.ndarray:
+    """Solve alpha*w - (lower, centre, upper)-operator w = rhs along ``axis``
+    for the interior nodes; w = 0 on the two end nodes (PEC)."""
+    r = np.moveaxis(rhs_e, axis, -1)
+    x = thomas(-lower, alpha - centre, -upper, r[..., 1:-1])
+    w = np.zeros_like(r)
+    w[..., 1:-1] = x
+    return np.moveaxis(w, -1, axis)
+
+
+def solve_implicit(grid: Grid, mat: dict, op: str, tau: float, rhs: dict) -> dict:
+    """Solve (I - tau*O) u = rhs for O = A or B, by eliminating H pair by pair.
+
+    For a pair with E row  E - sgn*(tau/eps) d(H) = rE  and H row
+    H - sgn*(tau/mu) d(E) = rH, substituting H = rH + sgn*(tau/mu) d(E) gives
+    the tridiagonal line system E - (tau/eps) d((tau/mu) d E) = rE + sgn*(tau/eps) d(rH);
+    H is then recovered explicitly.  tau may be negative."""
+    out = {}
+    for ec, hc, ax, sgn in PAIRS[op]:
+        a = AXIS[ax]
+        sp = grid.spacing[ax]
+        mask = grid.e_interior_mask(ec)
+        gE = tau / mat[ec]
+        gH = tau / mat[hc]
+        rE = (rhs[ec] + sgn * gE * diff_h_to_e(rhs[hc], a, sp, grid.shape(ec))) * mask
+        lo, ce, up = line_operator_coeffs(gE, gH, a, sp)
+        w = solve_lines(1.0, lo, ce, up, rE, a) * mask
+        out[ec] = w
+        out[hc] = rhs[hc] + sgn * gH * diff_e_to_h(w, a, sp)
+    return out
