@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark: 3-D FADI cell-steps/s on one GB300 (FP32 fields with FP64-formed
+coefficients; FP64 form alongside), with HBM roofline, end-to-end time through
+the C ABI with host buffers, and the FP64 CPU oracle as the baseline.
+
+Workload: 256^3-cell PEC cavity, 1 mm cells, vacuum, CFL 4, initial E = sum of
+8 seeded cavity eigenmodes (N(0,1) amplitudes).  A step is one FADI time step:
+procedures A and B, each three fused line-solve kernels over all six arrays.
+The state (457 MB in FP32) exceeds the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): independent replicas, one grid per GPU, no collective
+in the data path; value = all ranks' cell-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D FADI cell-steps/s on 1 GB300, FP32 vs FP64 at stated error; % HBM peak"
+UNIT = "cell-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per axis")
+    ap.add_argument("--cfl", type=float, default=4.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_fields(n):
+    import workloads as W
+    d = 1e-3
+    modes = W.random_modes(2, n, n, n, d, d, d, count=8)
+    return W.mode_sum_fields(modes, n, n, n)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args, prec, fields, time_kernels=True):
+    """Device-resident timing of K steps; returns dict of measurements."""
+    import torch
+    from paper_2011_14043_gb300 import Simulation
+    n = args.n
+    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl)
+    sim.set_fields(fields)
+    sim.step(args.warmup)            # includes the Eq. 10 initialization
+    sim.synchronize()
+    stream = torch.cuda.ExternalStream(sim._stream.value) if sim._stream.value else torch.cuda.current_stream()
+    sim.reset_stats()
+    sim.set_timing(time_kernels)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = sim.stats()
+    sim.set_timing(False)
+    energy = sim.energy()
+    sim.close()
+    return {"ms": ms, "stats": st, "energy": energy}
+
+
+def run_e2e(args, prec, fields):
+    """Same metric through the C ABI with pinned host buffers: H2D of the
+    initial fields, K steps, D2H of all six field components, all timed."""
+    import numpy as np
+    import torch
+    from paper_2011_14043_gb300 import Simulation
+    n = args.n
+    np_dtype = np.float32 if prec == "f32" else np.float64
+    t_dtype = torch.float32 if prec == "f32" else torch.float64
+    host_in = {}
+    host_out = {}
+    for c, v in fields.items():
+        t = torch.empty(v.shape, dtype=t_dtype, pin_memory=True)
+        t.numpy()[...] = v.astype(np_dtype)
+        host_in[c] = t
+        host_out[c] = torch.empty(v.shape, dtype=t_dtype, pin_memory=True)
+    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in fields:
+        sim.set_field(c, host_in[c].numpy())
+    sim.step(args.steps)
+    for c in fields:
+        sim.get_field(c, out=host_out[c].numpy())
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sim.close()
+    nbytes = sum(v.numel() * v.element_size() for v in host_in.values())
+    return {"s": t1 - t0, "h2d": nbytes, "d2h": nbytes}
+
+
+def cpu_baseline(n, steps=1):
+    """The FP64 numpy oracle timed on this host on a bounded sample."""
+    import oracle.grid as G
+    import oracle.schemes as S
+    fields = workload_fields(n)
+    g = G.Grid(n, n, n, 1e-3, 1e-3, 1e-3)
+    P = S.Problem(g, 4.0 * g.dt_cfl())
+    v = S.fadi_init(P, fields)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        v = S.fadi_step(P, v, k)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, dt
+
+
+def reference_arm(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle.grid as G
+    import oracle.schemes as S
+    n = args.n
+    fields = workload_fields(n)
+    g = G.Grid(n, n, n, 1e-3, 1e-3, 1e-3)
+    P = S.Problem(g, args.cfl * g.dt_cfl())
+    k_steps = max(1, min(args.steps, 3))
+    w_steps = min(args.warmup, 1)
+    v = S.fadi_init(P, fields)
+    for k in range(w_steps):
+        v = S.fadi_step(P, v, k)
+    t0 = time.perf_counter()
+    for k in range(k_steps):
+        v = S.fadi_step(P, v, w_steps + k)
+    dt = time.perf_counter() - t0
+    val = n ** 3 * k_steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": k_steps, "warmup": w_steps, "ms_per_step": 1e3 * dt / k_steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FADI {n}^3 PEC cavity, 1 mm cells, vacuum, CFL {args.cfl}, 8 seeded modes",
+                   "grid": [n, n, n], "scheme": "fadi"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{k_steps} of the {args.steps} requested steps of the full {n}^3 "
+                                   f"workload (FP64 numpy oracle, single thread)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2011_14043_gb300 import build
+    build()
+    fields = workload_fields(args.n)
+    n = args.n
+    cells = n ** 3
+
+    # --- device-resident timed region (FP32 headline) -------------------------
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.4)
+    r32 = run_gpu(args, "f32", fields)
+    clocks = sampler.stop()
+    ms = r32["ms"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * cells * args.steps / (ms / 1e3)
+
+    # dominant kernel roofline from live CUDA events in the timed region
+    st = r32["stats"]
+    peaks, peak_kind = measured_peaks()
+    cls_names = ["y-lines", "z-lines", "x-lines"]
+    dom = max(range(3), key=lambda c: st["timed_ms"][c])
+    avg_ms = st["timed_ms"][dom] / max(1, st["timed_launches"][dom])
+    achieved = st["bytes_per_launch"][dom] / (avg_ms / 1e3) / 1e9
+    per_class = {cls_names[c]: {"launches": st["timed_launches"][c],
+                                "avg_ms": st["timed_ms"][c] / max(1, st["timed_launches"][c]),
+                                "gbs": st["bytes_per_launch"][c] / (st["timed_ms"][c] / max(1, st["timed_launches"][c]) / 1e3) / 1e9
+                                if st["timed_ms"][c] > 0 else None}
+                 for c in range(3)}
+    step_bytes = 96.0 * cells  # 2 procedures x 6 arrays x (4 B read + 4 B write)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": f"proc line solve, {cls_names[dom]}", "peak_kind": peak_kind,
+                "step_achieved": step_bytes * args.steps / (r32["ms"] / 1e3) / 1e9,
+                "step_frac": step_bytes * args.steps / (r32["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "per_class": per_class}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"FADI {n}^3 PEC cavity, 1 mm cells, vacuum, CFL {args.cfl}, 8 seeded modes",
+                   "grid": [n, n, n], "scheme": "fadi", "parallelism": f"replicas x{ws}",
+                   "l2": "state 457 MB > 129 MB L2, no flush"},
+        "roofline": roofline,
+        "gpu_launches": st["launches"],
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_fp64:
+        a = argparse.Namespace(**vars(args))
+        a.steps = max(3, min(args.steps, 20))
+        r64 = run_gpu(a, "f64", fields, time_kernels=False)
+        v64 = cells * a.steps / (r64["ms"] / 1e3)
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / a.steps, "steps": a.steps,
+                        "hbm_frac": 192.0 * cells * a.steps / (r64["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    if not args.no_e2e:
+        e = run_e2e(args, "f32", fields)
+        ev = ws * cells * args.steps / e["s"]
+        line["e2e"] = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": e["h2d"] / args.steps,
+                       "d2h_bytes_per_step": e["d2h"] / args.steps}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, s = cpu_baseline(n, steps=1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 FADI step of the full {n}^3 workload, FP64 numpy oracle, "
+                                          f"single thread ({s:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * fdtd.h -- C ABI of the GB300 fundamental-scheme implicit FDTD library.
+ *
+ * Method: E. L. Tan, "Fundamental Schemes for Efficient Unconditionally Stable
+ * Implicit Finite-Difference Time-Domain Methods" (arXiv 2011.14043).
+ * The library advances Maxwell's equations on a 3-D Yee grid with PEC walls
+ * using one of the fundamental schemes of Sec. II:
+ *   FDTD_FADI   fundamental ADI, Eqs. 7-10 (component form Eqs. 37-44)
+ *   FDTD_FLOD   fundamental LOD1/SS1, Eq. 15
+ *   FDTD_FSS    fundamental second-order split step (SS2), Eq. 17
+ *   FDTD_FLOD2  fundamental LOD2 with input/output processing, Eqs. 21-23
+ * Each time step is a sequence of updating procedures.  A procedure is, for
+ * each of three (E, H) component pairs, an implicit update with a
+ * matrix-operator-free right-hand side (a batch of tridiagonal line solves
+ * along x, y or z), an explicit H update from the solved E, and the
+ * subtraction E <- w - E (Sec. III, Eqs. 38-44 and 45-52).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Errors: every call returns FDTD_OK (0) or a negative FDTD_ERR_* code and
+ *   never throws or aborts.  After FDTD_ERR_CUDA the handle is poisoned: every
+ *   later call except fdtd_destroy returns FDTD_ERR_STATE.
+ * Arrays: component arrays are C-contiguous [k][j][i] (x fastest) in the
+ *   compact Yee shapes (nx, ny, nz = cells):
+ *     EX (nz+1, ny+1, nx)   EY (nz+1, ny, nx+1)   EZ (nz, ny+1, nx+1)
+ *     HX (nz, ny, nx+1)     HY (nz, ny+1, nx)     HZ (nz+1, ny, nx)
+ *   Element type is the handle's precision: double for FDTD_F64, float for
+ *   FDTD_F32.  Per-cell material arrays are double, shape (nz, ny, nx).
+ * Ownership: the library owns all device memory it allocates.  Pointers
+ *   passed in are only read (or written, for outputs) during the call; with
+ *   on_device != 0 they are device pointers on the handle's device, else
+ *   host pointers.
+ * Streams: a handle is bound to one CUDA stream (NULL = legacy default
+ *   stream) given at creation; device work is enqueued on it.  Calls that
+ *   return host data synchronise that stream.  Handles are not thread-safe.
+ * Walls: perfect electric conductor on all six walls; tangential E on the
+ *   walls is held at zero (values passed in for those samples are ignored).
+ * 2-D: nz == 1 gives the 2-D TM case (Ez, Hx, Hy), the CFL limit then uses
+ *   dx and dy only.
+ */
+#ifndef FDTD_H_
+#define FDTD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_OK 0
+#define FDTD_ERR_INVALID_ARG (-1)   /* bad pointer, size, index or value */
+#define FDTD_ERR_OOM (-2)           /* device or host allocation failed */
+#define FDTD_ERR_CUDA (-3)          /* a CUDA call failed; handle poisoned */
+#define FDTD_ERR_TIMEOUT (-4)       /* a bounded device wait gave up */
+#define FDTD_ERR_UNSTABLE (-5)      /* non-finite field or invariant growth */
+#define FDTD_ERR_UNSUPPORTED (-6)   /* valid request this build does not implement */
+#define FDTD_ERR_STATE (-7)         /* call not valid in the handle's state */
+
+typedef enum { FDTD_FADI = 0, FDTD_FLOD = 1, FDTD_FSS = 2, FDTD_FLOD2 = 3 } fdtd_scheme;
+typedef enum { FDTD_F64 = 0, FDTD_F32 = 1 } fdtd_precision;
+typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, FDTD_HZ = 5 } fdtd_comp;
+
+/* Problem statement (Sec. III: grid, lossless isotropic medium, dt).
+ * dt > 0 is used as given; otherwise dt = cfl * dt_CFL with
+ * dt_CFL = 1 / (c0 * sqrt(1/dx^2 + 1/dy^2 [+ 1/dz^2 when nz > 1])),
+ * c0 = 299792458 m/s.  tune[] are kernel-shape overrides (0 = automatic):
+ * tune[0] nodes per thread of y/z-line solves, tune[1] unused. */
+typedef struct {
+  int32_t nx, ny, nz;        /* cells per axis, each >= 1; nx, ny >= 2 */
+  double dx, dy, dz;         /* cell sizes [m], > 0 */
+  double dt;                 /* time step [s] */
+  double cfl;                /* CFL number, used when dt <= 0 */
+  int32_t scheme;            /* fdtd_scheme */
+  int32_t precision;         /* fdtd_precision: FP64, or FP32 fields with
+                                coefficients formed in FP64 */
+  int32_t tune[2];
+} fdtd_desc;
+
+typedef struct fdtd_s fdtd_t;
+
+/* Create a handle: validates desc, allocates the six state arrays (zero
+ * fields, vacuum) on the current CUDA device, precomputes in FP64 the
+ * factorised tridiagonal coefficients of every procedure (Sec. IV: "5N
+ * flops ... with precomputed bidiagonally factorized elements").
+ * stream: a cudaStream_t or NULL.  *out receives the handle. */
+int fdtd_create(const fdtd_desc* desc, void* stream, fdtd_t** out);
+
+/* Release all device and host memory of the handle (NULL is a no-op). */
+int fdtd_destroy(fdtd_t* h);
+
+/* The time step in use [s]. */
+int fdtd_get_dt(const fdtd_t* h, double* dt);
+
+/* Per-cell relative permittivity / permeability (host, nz*ny*nx doubles,
+ * each > 0 and finite; NULL means 1 everywhere).  eps at an E sample is the
+ * mean of the in-domain cells sharing that edge; mu at an H sample the mean
+ * of the cells sharing that face.  Non-uniform mu returns
+ * FDTD_ERR_UNSUPPORTED.  Only valid before the first fdtd_step. */
+int fdtd_set_material(fdtd_t* h, const double* eps_r_cell, const double* mu_r_cell);
+
+/* Set one physical field component at the current time (compact Yee shape,
+ * handle precision).  For FADI the auxiliary state (Eq. 10) is formed from
+ * the physical fields on the next fdtd_step. */
+int fdtd_set_field(fdtd_t* h, int comp, const void* data, int on_device);
+
+/* Read one physical field component at the current time.  FADI applies the
+ * output relation u = u~/2 (Eq. 9) in the equivalent state form
+ * u = (I + dt/2 B)^{-1} (v - pending source); FLOD2 applies its output
+ * processing (Eq. 23); FLOD/FSS return the state. */
+int fdtd_get_field(fdtd_t* h, int comp, void* out, int on_device);
+
+/* Raw scheme state (FADI: auxiliary v of Eq. 8; FLOD2: u^{n+1/4} of Eq. 21;
+ * else the field) for checkpointing; same layout as fdtd_get_field. */
+int fdtd_get_state(fdtd_t* h, int comp, void* out, int on_device);
+int fdtd_set_state(fdtd_t* h, int comp, const void* data, int on_device);
+
+/* Point current source on one E sample (comp EX/EY/EZ, sample indices in the
+ * component's compact shape, not on a wall).  current[n] (host, n < count)
+ * is the current I [A] used by step n, i.e. I(t_n + dt/2); steps beyond
+ * count use 0.  It enters as f_E = -I/(A eps) with A the sample's dual-face
+ * area; each procedure of length h adds (h/2) f to the original-form
+ * right-hand side (the paper omits sources; this is the reading used).
+ * One source per handle; a new call replaces it; count == 0 removes it. */
+int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* current, int64_t count);
+
+/* Record one physical field sample after every step.  *id receives the
+ * probe index (0, 1, ...).  At most 16 probes. */
+int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id);
+
+/* Advance nsteps time steps (asynchronous on the handle's stream). */
+int fdtd_step(fdtd_t* h, int64_t nsteps);
+
+/* Copy the first n recorded values of a probe (host buffer); n may not
+ * exceed the number of steps taken since the probe was added. */
+int fdtd_get_probe(fdtd_t* h, int id, double* out, int64_t n);
+
+/* FP64 reductions: out[0] = field energy 1/2 dV sum(eps E^2 + mu H^2) of the
+ * physical field; out[1] = the same quadratic form of the scheme state (the
+ * exactly conserved invariant of a source-free run: equal to out[0] for
+ * FLOD/FSS).  Returns FDTD_ERR_UNSTABLE if either is not finite. */
+int fdtd_energy(fdtd_t* h, double out[2]);
+
+/* Number of steps taken. */
+int fdtd_steps_done(const fdtd_t* h, int64_t* n);
+
+/* Wait for the handle's stream. */
+int fdtd_synchronize(fdtd_t* h);
+
+/* Launch accounting and per-kernel timing.  Launch classes of the
+ * line-solve kernels: 0 = lines along y, 1 = lines along z, 2 = lines
+ * along x.  bytes_per_launch is the algorithmic traffic of one launch: the
+ * pair's E and H samples, each read once and written once. */
+typedef struct {
+  int64_t launches;              /* all kernels this handle enqueued */
+  int64_t timed_launches[3];     /* line-solve launches timed, per class */
+  double timed_ms[3];            /* their summed device time [ms] */
+  double bytes_per_launch[3];    /* algorithmic bytes of one launch */
+} fdtd_stats;
+
+/* enable != 0: record a CUDA event pair around every line-solve launch
+ * (on the handle's stream) until disabled.  Costs one event record per
+ * launch boundary. */
+int fdtd_set_timing(fdtd_t* h, int enable);
+
+/* Fill *out (synchronises the stream to resolve pending events). */
+int fdtd_get_stats(fdtd_t* h, fdtd_stats* out);
+
+/* Zero the counters and drop recorded events. */
+int fdtd_reset_stats(fdtd_t* h);
+
+/* Static description of an error code. */
+const char* fdtd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H_ */

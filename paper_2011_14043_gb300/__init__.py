@@ -1,0 +1,208 @@
+"""GB300-native fundamental-scheme implicit FDTD (arXiv 2011.14043).
+
+Python face of the C ABI in ``include/fdtd.h``.  Every step of the time
+stepper runs in the CUDA library (``csrc/``); this module only marshals
+arguments.  PyTorch is used for device buffers and the current CUDA stream.
+
+    sim = Simulation(nx, ny, nz, dx, dy, dz, scheme="fadi", precision="f32", cfl=4.0)
+    sim.set_field("ez", ez0)          # numpy (host) or torch CUDA tensor (device)
+    sim.step(1000)
+    ez = sim.get_field("ez")          # numpy; device=True gives a torch tensor
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import COMPS, PRECISIONS, SCHEMES, FdtdDesc, FdtdError, FdtdStats, check, lib
+
+__all__ = ["Simulation", "FdtdError", "comp_shape", "build"]
+
+
+def comp_shape(comp: str, nx: int, ny: int, nz: int) -> tuple:
+    return {
+        "ex": (nz + 1, ny + 1, nx), "ey": (nz + 1, ny, nx + 1), "ez": (nz, ny + 1, nx + 1),
+        "hx": (nz, ny, nx + 1), "hy": (nz, ny + 1, nx), "hz": (nz + 1, ny, nx),
+    }[comp]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force, verbose=verbose)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Simulation:
+    """One grid on one GPU, bound to a CUDA stream (default: torch's current)."""
+
+    def __init__(self, nx, ny, nz, dx, dy=None, dz=None, *, scheme="fadi", precision="f32",
+                 dt=0.0, cfl=0.0, stream=None, tune=(0, 0)):
+        dy = dx if dy is None else dy
+        dz = dx if dz is None else dz
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.scheme = scheme
+        self.precision = precision
+        self.dtype = np.float64 if precision == "f64" else np.float32
+        d = FdtdDesc()
+        d.nx, d.ny, d.nz = self.nx, self.ny, self.nz
+        d.dx, d.dy, d.dz = float(dx), float(dy), float(dz)
+        d.dt = float(dt)
+        d.cfl = float(cfl)
+        d.scheme = SCHEMES[scheme]
+        d.precision = PRECISIONS[precision]
+        d.tune[0], d.tune[1] = int(tune[0]), int(tune[1])
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        self._stream = ctypes.c_void_p(int(stream))
+        h = ctypes.c_void_p()
+        check(lib().fdtd_create(ctypes.byref(d), self._stream, ctypes.byref(h)), "fdtd_create")
+        self._h = h
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fdtd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- properties ----------------------------------------------------------
+    @property
+    def dt(self) -> float:
+        v = ctypes.c_double()
+        check(lib().fdtd_get_dt(self._h, ctypes.byref(v)), "fdtd_get_dt")
+        return v.value
+
+    @property
+    def steps_done(self) -> int:
+        v = ctypes.c_int64()
+        check(lib().fdtd_steps_done(self._h, ctypes.byref(v)), "fdtd_steps_done")
+        return v.value
+
+    def shape(self, comp: str) -> tuple:
+        return comp_shape(comp, self.nx, self.ny, self.nz)
+
+    # -- problem set-up ------------------------------------------------------
+    def set_material(self, eps_r_cell=None, mu_r_cell=None):
+        def ptr(a):
+            if a is None:
+                return None, None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.shape != (self.nz, self.ny, self.nx):
+                raise ValueError(f"material shape {a.shape} != {(self.nz, self.ny, self.nx)}")
+            return a, a.ctypes.data_as(ctypes.c_void_p)
+        ea, ep = ptr(eps_r_cell)
+        ma, mp = ptr(mu_r_cell)
+        check(lib().fdtd_set_material(self._h, ep, mp), "fdtd_set_material")
+
+    def _put(self, fn, comp, data, what):
+        c = COMPS[comp]
+        if hasattr(data, "is_cuda") and data.is_cuda:
+            torch = _torch()
+            want = torch.float64 if self.precision == "f64" else torch.float32
+            t = data.to(want).contiguous()
+            if tuple(t.shape) != self.shape(comp):
+                raise ValueError(f"{comp} shape {tuple(t.shape)} != {self.shape(comp)}")
+            check(fn(self._h, c, ctypes.c_void_p(t.data_ptr()), 1), what)
+            torch.cuda.current_stream().synchronize()
+        else:
+            a = np.ascontiguousarray(data, dtype=self.dtype)
+            if a.shape != self.shape(comp):
+                raise ValueError(f"{comp} shape {a.shape} != {self.shape(comp)}")
+            check(fn(self._h, c, a.ctypes.data_as(ctypes.c_void_p), 0), what)
+
+    def _get(self, fn, comp, device, what, out=None):
+        c = COMPS[comp]
+        if out is not None:
+            if out.shape != self.shape(comp) or out.dtype != self.dtype or not out.flags.c_contiguous:
+                raise ValueError(f"out must be a C-contiguous {self.dtype.__name__} array of shape {self.shape(comp)}")
+            check(fn(self._h, c, out.ctypes.data_as(ctypes.c_void_p), 0), what)
+            return out
+        if device:
+            torch = _torch()
+            t = torch.empty(self.shape(comp), dtype=torch.float64 if self.precision == "f64" else torch.float32,
+                            device="cuda")
+            check(fn(self._h, c, ctypes.c_void_p(t.data_ptr()), 1), what)
+            return t
+        a = np.empty(self.shape(comp), dtype=self.dtype)
+        check(fn(self._h, c, a.ctypes.data_as(ctypes.c_void_p), 0), what)
+        return a
+
+    def set_field(self, comp: str, data):
+        self._put(lib().fdtd_set_field, comp, data, "fdtd_set_field")
+
+    def set_fields(self, fields: dict):
+        for c, v in fields.items():
+            self.set_field(c, v)
+
+    def get_field(self, comp: str, device: bool = False, out=None):
+        """Physical field component; ``out`` (host array, e.g. pinned) is filled in place."""
+        return self._get(lib().fdtd_get_field, comp, device, "fdtd_get_field", out)
+
+    def get_fields(self, device: bool = False) -> dict:
+        return {c: self.get_field(c, device) for c in COMPS}
+
+    def set_state(self, comp: str, data):
+        self._put(lib().fdtd_set_state, comp, data, "fdtd_set_state")
+
+    def get_state(self, comp: str, device: bool = False):
+        return self._get(lib().fdtd_get_state, comp, device, "fdtd_get_state")
+
+    def set_source(self, comp: str, i: int, j: int, k: int, current):
+        cur = np.ascontiguousarray(current, dtype=np.float64)
+        check(lib().fdtd_set_source(self._h, COMPS[comp], int(i), int(j), int(k),
+                                    cur.ctypes.data_as(ctypes.c_void_p), cur.size), "fdtd_set_source")
+        self._src_keep = cur
+
+    def add_probe(self, comp: str, i: int, j: int, k: int) -> int:
+        pid = ctypes.c_int()
+        check(lib().fdtd_add_probe(self._h, COMPS[comp], int(i), int(j), int(k), ctypes.byref(pid)),
+              "fdtd_add_probe")
+        return pid.value
+
+    def get_probe(self, pid: int, n: int) -> np.ndarray:
+        out = np.empty(int(n), dtype=np.float64)
+        check(lib().fdtd_get_probe(self._h, int(pid), out.ctypes.data_as(ctypes.c_void_p), int(n)),
+              "fdtd_get_probe")
+        return out
+
+    # -- stepping and reductions -----------------------------------------------
+    def step(self, n: int = 1):
+        check(lib().fdtd_step(self._h, int(n)), "fdtd_step")
+
+    def synchronize(self):
+        check(lib().fdtd_synchronize(self._h), "fdtd_synchronize")
+
+    def set_timing(self, enable: bool):
+        check(lib().fdtd_set_timing(self._h, 1 if enable else 0), "fdtd_set_timing")
+
+    def stats(self) -> dict:
+        st = FdtdStats()
+        check(lib().fdtd_get_stats(self._h, ctypes.byref(st)), "fdtd_get_stats")
+        return {"launches": st.launches, "timed_launches": list(st.timed_launches),
+                "timed_ms": list(st.timed_ms), "bytes_per_launch": list(st.bytes_per_launch)}
+
+    def reset_stats(self):
+        check(lib().fdtd_reset_stats(self._h), "fdtd_reset_stats")
+
+    def energy(self) -> tuple:
+        out = (ctypes.c_double * 2)()
+        check(lib().fdtd_energy(self._h, out), "fdtd_energy")
+        return out[0], out[1]

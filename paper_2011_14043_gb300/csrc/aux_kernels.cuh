@@ -1,0 +1,104 @@
+// Auxiliary kernels: explicit operator half-steps (FADI input
+// initialization, Eq. 10), probe recording, FP64 energy reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "line_kernels.cuh"
+
+namespace fdtd {
+
+// Out-of-place explicit half-step of one pair of an operator O:
+//   E_out_j = E_j + kb_j (H_j - H_{j-1})   at the interior nodes j = 1..N-1
+//   H_out_f = H_f + kd (E_{f+1} - E_f)     at the faces f = 0..N-1
+// on the pair's active lines (the same geometry as the procedure kernels).
+// With kb = s*tau/(eps d_eta), kd = s*tau/(mu d_eta) this is (I + tau O).
+template <typename T, bool PER_NODE>
+__global__ void explicit_pair_kernel(const PairParams<T> p, int rows) {
+  const long long n_lines = rows ? (long long)p.n_o * p.n_o2 : (long long)(p.lane_hi - p.lane_lo) * p.n_o;
+  const long long total = n_lines * p.N;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(g % p.N);
+    const long long line = g / p.N;
+    long long base;
+    if (rows) {
+      const int jo = p.o_lo + (int)(line % p.n_o);
+      const int ko = p.o2_lo + (int)(line / p.n_o);
+      base = (long long)ko * p.os2 + (long long)jo * p.os;
+    } else {
+      const int nl = p.lane_hi - p.lane_lo;
+      const int i = p.lane_lo + (int)(line % nl);
+      const int o = p.o_lo + (int)(line / nl);
+      base = (long long)o * p.os + i;
+    }
+    const long long at = base + (long long)j * p.ls;
+    const T hf = p.h_in[at];
+    if (j >= 1) {
+      const T kb = PER_NODE ? p.kb_sign * p.nkb[at] : p.kb;
+      p.e_out[at] = p.e_in[at] + kb * (hf - p.h_in[at - p.ls]);
+    } else {
+      p.e_out[at] = p.e_in[at];
+    }
+    const T enext = (j + 1 < p.N) ? p.e_in[at + p.ls] : T(0);
+    p.h_out[at] = hf + p.kd * (enext - p.e_in[at]);
+  }
+}
+
+// y[i] += a * x[i] at one element (point source added to a state array).
+template <typename T>
+__global__ void add_point_kernel(T* y, long long at, double a) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) y[at] = (T)((double)y[at] + a);
+}
+
+constexpr int kMaxProbes = 16;
+
+template <typename T>
+struct ProbeParams {
+  const T* arr[kMaxProbes];
+  long long at[kMaxProbes];
+  int n;
+};
+
+// mode 0: stash[p] = value;  mode 1: out[p][col] = (stash[p] + value)/2;
+// mode 2: out[p][col] = value.
+template <typename T>
+__global__ void probe_kernel(const ProbeParams<T> pp, double* stash, double* out, long long ld,
+                             long long col, int mode) {
+  const int q = threadIdx.x;
+  if (q >= pp.n) return;
+  const double v = (double)pp.arr[q][pp.at[q]];
+  if (mode == 0) {
+    stash[q] = v;
+  } else if (mode == 1) {
+    out[(long long)q * ld + col] = 0.5 * (stash[q] + v);
+  } else {
+    out[(long long)q * ld + col] = v;
+  }
+}
+
+// Per-block partial sums of w * x^2 in FP64 (w = scalar weight, or a
+// per-element FP64 weight times the scalar when wv != nullptr).
+template <typename T>
+__global__ void weighted_sumsq_kernel(const T* x, const double* wv, double w, long long n,
+                                      double* partial) {
+  double acc = 0.0;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+       g += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)x[g];
+    acc += (wv ? wv[g] : 1.0) * v * v;
+  }
+  acc *= w;
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  }
+}
+
+}  // namespace fdtd

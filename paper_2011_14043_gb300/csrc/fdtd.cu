@@ -1,0 +1,1198 @@
+// Host side of the C ABI declared in include/fdtd.h.
+//
+// Device data layout: every one of the six components is stored in the same
+// padded box of (nz+1) planes x (ny+1) rows x pitch elements, pitch a
+// multiple of 32 elements (128-byte aligned rows for FP32).  Sample (i, j, k)
+// of any component lives at k*plane + j*pitch + i; entries outside the
+// component's compact Yee shape are zero and never written.  Node j of a
+// grid line and face j of the paired H component share an element offset,
+// which is what lets one kernel walk both.
+//
+// The hot loop is in line_kernels.cuh; this file holds validation, FP64
+// coefficient precompute, the scheme schedules (Sec. II) and the launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "aux_kernels.cuh"
+#include "line_kernels.cuh"
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+
+enum { EX = 0, EY, EZ, HX, HY, HZ };
+enum { AX_X = 0, AX_Y = 1, AX_Z = 2 };
+
+struct PairGeom {
+  int ec = 0, hc = 0, axis = 0, sign = 0, N = 0;
+  bool rows = false;
+  long long ls = 0, os = 0, os2 = 0;
+  int lane_lo = 0, lane_hi = 0, o_lo = 0, n_o = 0, o2_lo = 0, n_o2 = 0;
+  long long n_lines() const {
+    return rows ? (long long)n_o * n_o2 : (long long)std::max(0, lane_hi - lane_lo) * n_o;
+  }
+  bool empty() const { return N < 2 || n_lines() <= 0; }
+};
+
+// Coefficients of one pair for one procedure length h.
+struct PairCoef {
+  double kb = 0, kd = 0;  // signed s*b/d_eta, s*d/d_eta
+  double dh = 0;          // |d|/(2 d_eta)
+  void* tab = nullptr;    // uniform media: [3][tlen] (1/beta, m, c) in T
+  int tlen = 0;
+  void* nkb = nullptr;    // per-node media (field layout, T)
+  void* nib = nullptr;
+};
+
+struct StridedCfg {
+  bool ok = false;
+  int lanes = 32, L = 16;
+};
+
+struct ProcCoef {
+  bool valid = false;
+  int op = 0;  // 0 = A, 1 = B
+  double h = 0;
+  PairCoef pc[3];
+};
+
+}  // namespace
+
+struct fdtd_s {
+  fdtd_desc desc;
+  int nx, ny, nz;
+  double dx, dy, dz, dt;
+  int scheme, prec;
+  size_t esize;
+  cudaStream_t stream;
+  long long pitch, plane, count;
+  void* f[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* scratch[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  PairGeom geom[2][3];
+  StridedCfg strided_cfg[2];  // y lines, z lines
+  ProcCoef proc[3];  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing)
+  bool per_node = false;
+  double eps_r = 1.0, mu_r = 1.0;          // uniform media
+  double* eps_node[3] = {nullptr, nullptr, nullptr};  // per-node eps_r at E samples (device)
+  std::vector<double> eps_host[3];  // the same on the host, only while coefficients are built
+  bool poisoned = false;
+  bool pending_init = true;   // FADI/FLOD2: state holds the physical field
+  bool output_valid = false;  // scratch holds the physical field of this step
+  long long steps = 0;
+  // source
+  int src_comp = -1, src_i = 0, src_j = 0, src_k = 0;
+  std::vector<double> src_current;
+  double src_scale = 0;  // f_E = src_scale * I
+  // probes
+  int nprobes = 0;
+  int probe_comp[fdtd::kMaxProbes];
+  long long probe_at[fdtd::kMaxProbes];
+  long long probe_start[fdtd::kMaxProbes];
+  double* d_probe = nullptr;   // [kMaxProbes][probe_cap]
+  double* d_stash = nullptr;
+  long long probe_cap = 0;
+  double* d_partial = nullptr;
+  int partial_n = 0;
+  // accounting
+  long long launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;     // reusable events
+  std::vector<std::pair<int, std::pair<int, int>>> ev_rec;  // (class, (start ev, stop ev))
+  long long timed_launches[3] = {0, 0, 0};
+  double timed_ms[3] = {0, 0, 0};
+  double bytes_per_launch[3] = {0, 0, 0};
+};
+
+namespace {
+
+int cuda_fail(fdtd_t* h, cudaError_t e) {
+  if (e == cudaSuccess) return FDTD_OK;
+  if (h) h->poisoned = true;
+  fprintf(stderr, "fdtd: CUDA error: %s\n", cudaGetErrorString(e));
+  return FDTD_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return cuda_fail(h, _e);       \
+  } while (0)
+
+void comp_extent(int c, int nx, int ny, int nz, int* sx, int* sy, int* sz) {
+  switch (c) {
+    case EX: *sx = nx; *sy = ny + 1; *sz = nz + 1; break;
+    case EY: *sx = nx + 1; *sy = ny; *sz = nz + 1; break;
+    case EZ: *sx = nx + 1; *sy = ny + 1; *sz = nz; break;
+    case HX: *sx = nx + 1; *sy = ny; *sz = nz; break;
+    case HY: *sx = nx; *sy = ny + 1; *sz = nz; break;
+    default: *sx = nx; *sy = ny; *sz = nz + 1; break;
+  }
+}
+
+// The three (E, H, axis, sign) pairs of A (Eq. 33) and B (Eq. 34).
+void build_geometry(fdtd_t* h) {
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  const int E_[2][3] = {{EX, EY, EZ}, {EX, EY, EZ}};
+  const int H_[2][3] = {{HZ, HX, HY}, {HY, HZ, HX}};
+  const int A_[2][3] = {{AX_Y, AX_Z, AX_X}, {AX_Z, AX_X, AX_Y}};
+  for (int op = 0; op < 2; ++op) {
+    for (int q = 0; q < 3; ++q) {
+      PairGeom g;
+      g.ec = E_[op][q];
+      g.hc = H_[op][q];
+      g.axis = A_[op][q];
+      g.sign = op == 0 ? +1 : -1;
+      g.rows = g.axis == AX_X;
+      g.N = g.axis == AX_X ? nx : (g.axis == AX_Y ? ny : nz);
+      // x range of lines (strided) and the other transverse ranges:
+      // tangential E on a wall is not an unknown, so those lines are skipped.
+      if (g.axis == AX_X) {
+        g.ls = 1;
+        g.os = h->pitch;
+        g.os2 = h->plane;
+        if (g.ec == EY) {  // Ey lines (j, k): j in [0, ny), k in [1, nz-1]
+          g.o_lo = 0; g.n_o = ny; g.o2_lo = 1; g.n_o2 = nz - 1;
+        } else {           // Ez lines: j in [1, ny-1], k in [0, nz)
+          g.o_lo = 1; g.n_o = ny - 1; g.o2_lo = 0; g.n_o2 = nz;
+        }
+      } else if (g.axis == AX_Y) {
+        g.ls = h->pitch;
+        g.os = h->plane;
+        if (g.ec == EX) {  // Ex lines (i, k): i in [0, nx), k in [1, nz-1]
+          g.lane_lo = 0; g.lane_hi = nx; g.o_lo = 1; g.n_o = nz - 1;
+        } else {           // Ez lines (i, k): i in [1, nx-1], k in [0, nz)
+          g.lane_lo = 1; g.lane_hi = nx; g.o_lo = 0; g.n_o = nz;
+        }
+      } else {
+        g.ls = h->plane;
+        g.os = h->pitch;
+        if (g.ec == EX) {  // Ex lines (i, j): i in [0, nx), j in [1, ny-1]
+          g.lane_lo = 0; g.lane_hi = nx; g.o_lo = 1; g.n_o = ny - 1;
+        } else {           // Ey lines (i, j): i in [1, nx-1], j in [0, ny)
+          g.lane_lo = 1; g.lane_hi = nx; g.o_lo = 0; g.n_o = ny;
+        }
+      }
+      if (g.n_o < 0) g.n_o = 0;
+      if (g.n_o2 < 0) g.n_o2 = 0;
+      h->geom[op][q] = g;
+    }
+  }
+}
+
+// nodes per lane of the x-line kernel: the smallest instantiated L with 32 L >= N
+int pick_rows_L(int N) {
+  static const int kL[] = {1, 2, 4, 8, 12, 16, 24, 32};
+  const int need = (N + 31) / 32;
+  for (int L : kL)
+    if (L >= need) return L;
+  return -1;
+}
+
+double spacing(const fdtd_t* h, int axis) { return axis == AX_X ? h->dx : (axis == AX_Y ? h->dy : h->dz); }
+
+template <typename T>
+int upload(fdtd_t* h, void** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.size());
+  for (size_t q = 0; q < src.size(); ++q) tmp[q] = (T)src[q];
+  if (!*dst) CK(cudaMalloc(dst, tmp.size() * sizeof(T)));
+  CK(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int upload_any(fdtd_t* h, void** dst, const std::vector<double>& src) {
+  return h->prec == FDTD_F64 ? upload<double>(h, dst, src) : upload<float>(h, dst, src);
+}
+
+void free_coef(ProcCoef& pc) {
+  for (auto& c : pc.pc) {
+    if (c.tab) cudaFree(c.tab);
+    if (c.nkb) cudaFree(c.nkb);
+    if (c.nib) cudaFree(c.nib);
+    c = PairCoef();
+  }
+  pc.valid = false;
+}
+
+// eps_r at every E sample: mean of the in-domain cells sharing the edge.
+void edge_eps(const fdtd_t* h, const double* er, int c, std::vector<double>& out) {
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  out.assign((size_t)h->count, 0.0);
+  int sx, sy, sz;
+  comp_extent(c, nx, ny, nz, &sx, &sy, &sz);
+  for (int k = 0; k < sz; ++k)
+    for (int j = 0; j < sy; ++j)
+      for (int i = 0; i < sx; ++i) {
+        double s = 0;
+        int n = 0;
+        for (int a = -1; a <= 0; ++a)
+          for (int b = -1; b <= 0; ++b) {
+            int ci = i, cj = j, ck = k;
+            if (c == EX) { cj = j + a; ck = k + b; }
+            if (c == EY) { ci = i + a; ck = k + b; }
+            if (c == EZ) { ci = i + a; cj = j + b; }
+            if (ci < 0 || cj < 0 || ck < 0 || ci >= nx || cj >= ny || ck >= nz) continue;
+            s += er[((size_t)ck * ny + cj) * nx + ci];
+            ++n;
+          }
+        out[(size_t)k * h->plane + (size_t)j * h->pitch + i] = n ? s / n : 1.0;
+      }
+}
+
+// FP64 factorisation of the line systems of one procedure (operator op,
+// length hh):  1/2 w_j - (b_j/2)(d/d^2)(w_{j+1} - 2 w_j + w_{j-1}) = r_j.
+int build_proc(fdtd_t* h, int slot, int op, double hh) {
+  ProcCoef& P = h->proc[slot];
+  free_coef(P);
+  P.op = op;
+  P.h = hh;
+  for (int q = 0; q < 3; ++q) {
+    const PairGeom& g = h->geom[op][q];
+    PairCoef& c = P.pc[q];
+    const double de = spacing(h, g.axis);
+    const double d = hh / (2.0 * kMu0 * h->mu_r);
+    c.kd = g.sign * d / de;
+    c.dh = std::fabs(d) / (2.0 * de);
+    if (!h->per_node) {
+      const double b = hh / (2.0 * kEps0 * h->eps_r);
+      c.kb = g.sign * b / de;
+      const double off = -b * d / (2.0 * de * de);
+      const double diag = 0.5 + b * d / (de * de);
+      const int N = std::max(g.N, 1);
+      c.tlen = ((std::max(N + 64, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
+      std::vector<double> ib(c.tlen, 0.0), tab(3 * (size_t)c.tlen, 0.0);
+      double beta = 0;
+      for (int j = 1; j <= N - 1; ++j) {
+        beta = (j == 1) ? diag : diag - off * off * ib[j - 1];
+        ib[j] = 1.0 / beta;
+      }
+      for (int j = 0; j < c.tlen; ++j) {
+        tab[j] = ib[j];
+        tab[c.tlen + j] = (j >= 1) ? off * ib[j - 1] : 0.0;
+        tab[2 * c.tlen + j] = off * ib[j];
+      }
+      int rc = upload_any(h, &c.tab, tab);
+      if (rc) return rc;
+    } else {
+      // per-node: |b_j|/d_eta and 1/beta_j at every E node of the pair's lines
+      std::vector<double> nkb((size_t)h->count, 0.0), nib((size_t)h->count, 0.0);
+      const double* er = h->eps_host[g.ec].data();
+      const double s2 = de * de;
+      const long long nl = g.n_lines();
+      for (long long line = 0; line < nl; ++line) {
+        long long base;
+        if (g.rows) {
+          const int jo = g.o_lo + (int)(line % g.n_o);
+          const int ko = g.o2_lo + (int)(line / g.n_o);
+          base = (long long)ko * g.os2 + (long long)jo * g.os;
+        } else {
+          const int nlx = g.lane_hi - g.lane_lo;
+          const int i = g.lane_lo + (int)(line % nlx);
+          const int o = g.o_lo + (int)(line / nlx);
+          base = (long long)o * g.os + i;
+        }
+        double ibm = 0, om = 0;
+        for (int j = 1; j <= g.N - 1; ++j) {
+          const long long at = base + (long long)j * g.ls;
+          const double b = hh / (2.0 * kEps0 * er[at]);
+          const double o = -b * d / (2.0 * s2);
+          const double diag = 0.5 + b * d / s2;
+          const double beta = diag - o * om * ibm;
+          const double ib = 1.0 / beta;
+          nkb[at] = std::fabs(b) / de;
+          nib[at] = ib;
+          ibm = ib;
+          om = o;
+        }
+      }
+      c.kb = g.sign * (hh >= 0 ? 1.0 : -1.0);  // kb_sign
+      int rc = upload_any(h, &c.nkb, nkb);
+      if (rc) return rc;
+      rc = upload_any(h, &c.nib, nib);
+      if (rc) return rc;
+    }
+  }
+  P.valid = true;
+  return FDTD_OK;
+}
+
+int build_all_coefs(fdtd_t* h) {
+  const double dt = h->dt;
+  int rc;
+  if (h->scheme == FDTD_FSS) {
+    if ((rc = build_proc(h, 0, 0, dt / 2))) return rc;
+    if ((rc = build_proc(h, 1, 1, dt))) return rc;
+  } else {
+    if ((rc = build_proc(h, 0, 0, dt))) return rc;
+    if ((rc = build_proc(h, 1, 1, dt))) return rc;
+  }
+  if (h->scheme == FDTD_FLOD2) {
+    if ((rc = build_proc(h, 2, 1, dt / 2))) return rc;
+  } else {
+    free_coef(h->proc[2]);
+  }
+  return FDTD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+
+
+template <typename T>
+fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCoef& c, double sgn,
+                                double alpha, double beta, double kd_mul, void* const* in,
+                                void* const* out) {
+  fdtd::PairParams<T> p;
+  p.e_in = (const T*)in[g.ec];
+  p.h_in = (const T*)in[g.hc];
+  p.e_out = (T*)out[g.ec];
+  p.h_out = (T*)out[g.hc];
+  p.ls = g.ls;
+  p.os = g.os;
+  p.os2 = g.os2;
+  p.lane_lo = g.lane_lo;
+  p.lane_hi = g.lane_hi;
+  p.o_lo = g.o_lo;
+  p.n_o = g.n_o;
+  p.o2_lo = g.o2_lo;
+  p.n_o2 = g.n_o2;
+  p.N = g.N;
+  p.kb = (T)(sgn * c.kb);
+  p.kd = (T)(sgn * kd_mul * c.kd);
+  p.alpha = (T)alpha;
+  p.beta = (T)beta;
+  p.tab = (const T*)c.tab;
+  p.tlen = c.tlen;
+  p.nkb = (const T*)c.nkb;
+  p.nib = (const T*)c.nib;
+  p.kb_sign = (T)(sgn * c.kb);
+  p.dh = (T)c.dh;
+  p.src_i = p.src_o = p.src_o2 = p.src_j = -1;
+  p.src_rhs = T(0);
+  p.src_post = T(0);
+  (void)h;
+  return p;
+}
+
+// Place a point value at sample (i, j, k) of component comp on the pair's
+// line coordinates, if that component is the pair's E component.
+template <typename T>
+void set_src(const fdtd_t* h, const PairGeom& g, fdtd::PairParams<T>& p, double rhs, double post) {
+  if (h->src_comp != g.ec) return;
+  const int si = h->src_i, sj = h->src_j, sk = h->src_k;
+  if (g.axis == AX_X) {
+    p.src_o = sj; p.src_o2 = sk; p.src_j = si;
+  } else if (g.axis == AX_Y) {
+    p.src_i = si; p.src_o = sk; p.src_j = sj;
+  } else {
+    p.src_i = si; p.src_o = sj; p.src_j = sk;
+  }
+  p.src_rhs = (T)rhs;
+  p.src_post = (T)post;
+}
+
+template <typename T, int LANES, int L>
+void launch_strided_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, bool per_node) {
+  const int P = (g.N + L - 1) / L;
+  dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
+  const int threads = P * LANES;
+  const size_t smem = 4 * (size_t)P * LANES * sizeof(T);
+  if (per_node)
+    fdtd::proc_strided_kernel<T, LANES, L, true><<<grid, threads, smem, h->stream>>>(p);
+  else
+    fdtd::proc_strided_kernel<T, LANES, L, false><<<grid, threads, smem, h->stream>>>(p);
+}
+
+template <typename T, int L>
+void launch_rows_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, bool per_node) {
+  const int wpb = 8;
+  const long long nl = g.n_lines();
+  const unsigned blocks = (unsigned)((nl + wpb - 1) / wpb);
+  if (per_node)
+    fdtd::proc_rows_kernel<T, L, true><<<blocks, wpb * 32, 0, h->stream>>>(p);
+  else
+    fdtd::proc_rows_kernel<T, L, false><<<blocks, wpb * 32, 0, h->stream>>>(p);
+}
+
+// (LANES, L) of the y/z line kernels.  A block holds every segment of LANES
+// lines, so P * LANES threads with P = ceil(N / L); the choice must fit the
+// register file (checked against the compiled kernel's attributes).
+template <typename T, int LANES, int L>
+const void* strided_fn(bool pn) {
+  return pn ? (const void*)fdtd::proc_strided_kernel<T, LANES, L, true>
+            : (const void*)fdtd::proc_strided_kernel<T, LANES, L, false>;
+}
+
+template <typename T>
+const void* strided_fn_rt(bool pn, int lanes, int L) {
+  if (lanes == 32 && L == 8) return strided_fn<T, 32, 8>(pn);
+  if (lanes == 32 && L == 16) return strided_fn<T, 32, 16>(pn);
+  if (lanes == 32 && L == 32) return strided_fn<T, 32, 32>(pn);
+  if (lanes == 16 && L == 8) return strided_fn<T, 16, 8>(pn);
+  if (lanes == 16 && L == 16) return strided_fn<T, 16, 16>(pn);
+  if (lanes == 16 && L == 32) return strided_fn<T, 16, 32>(pn);
+  if (lanes == 8 && L == 16) return strided_fn<T, 8, 16>(pn);
+  if (lanes == 8 && L == 32) return strided_fn<T, 8, 32>(pn);
+  return nullptr;
+}
+
+template <typename T>
+void launch_strided(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, bool pn, int lanes, int L) {
+  if (lanes == 32 && L == 8) launch_strided_L<T, 32, 8>(h, g, p, pn);
+  else if (lanes == 32 && L == 16) launch_strided_L<T, 32, 16>(h, g, p, pn);
+  else if (lanes == 32 && L == 32) launch_strided_L<T, 32, 32>(h, g, p, pn);
+  else if (lanes == 16 && L == 8) launch_strided_L<T, 16, 8>(h, g, p, pn);
+  else if (lanes == 16 && L == 16) launch_strided_L<T, 16, 16>(h, g, p, pn);
+  else if (lanes == 16 && L == 32) launch_strided_L<T, 16, 32>(h, g, p, pn);
+  else if (lanes == 8 && L == 16) launch_strided_L<T, 8, 16>(h, g, p, pn);
+  else if (lanes == 8 && L == 32) launch_strided_L<T, 8, 32>(h, g, p, pn);
+}
+
+template <typename T>
+StridedCfg choose_strided(int N, bool pn, int tune_L) {
+  // preference order: widest rows first (coalescing), then the L that keeps
+  // registers low enough for two or more resident blocks.
+  static const int cand32[][2] = {{32, 16}, {32, 8}, {32, 32}, {16, 32}, {8, 32}};
+  static const int cand64[][2] = {{16, 16}, {16, 8}, {16, 32}, {8, 16}, {8, 32}};
+  const int(*cand)[2] = sizeof(T) == 8 ? cand64 : cand32;
+  StridedCfg best;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int q = 0; q < 5; ++q) {
+      const int lanes = cand[q][0], L = cand[q][1];
+      if (pass == 0 && tune_L && L != tune_L) continue;
+      const int P = (N + L - 1) / L;
+      const void* fn = strided_fn_rt<T>(pn, lanes, L);
+      if (!fn) continue;
+      cudaFuncAttributes a;
+      if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) continue;
+      if (P * lanes > a.maxThreadsPerBlock) continue;
+      best.ok = true;
+      best.lanes = lanes;
+      best.L = L;
+      return best;
+    }
+  }
+  return best;
+}
+
+int take_event(fdtd_t* h, int* idx) {
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  h->ev_pool.push_back(e);
+  *idx = (int)h->ev_pool.size() - 1;
+  return FDTD_OK;
+}
+
+int resolve_events(fdtd_t* h) {
+  if (h->ev_rec.empty()) return FDTD_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->ev_rec) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[r.second.first], h->ev_pool[r.second.second]));
+    h->timed_ms[r.first] += ms;
+    h->timed_launches[r.first] += 1;
+  }
+  h->ev_rec.clear();
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  return FDTD_OK;
+}
+
+template <typename T>
+int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
+  if (g.empty()) return FDTD_OK;
+  const bool pn = h->per_node;
+  const int cls = g.axis == AX_Y ? 0 : (g.axis == AX_Z ? 1 : 2);
+  int ev0 = -1, ev1 = -1;
+  if (h->timing) {
+    int rc = take_event(h, &ev0);
+    if (rc) return rc;
+    if ((rc = take_event(h, &ev1))) return rc;
+    CK(cudaEventRecord(h->ev_pool[ev0], h->stream));
+  }
+  h->launches++;
+  if (g.rows) {
+    switch (pick_rows_L(g.N)) {
+      case 1: launch_rows_L<T, 1>(h, g, p, pn); break;
+      case 2: launch_rows_L<T, 2>(h, g, p, pn); break;
+      case 4: launch_rows_L<T, 4>(h, g, p, pn); break;
+      case 8: launch_rows_L<T, 8>(h, g, p, pn); break;
+      case 12: launch_rows_L<T, 12>(h, g, p, pn); break;
+      case 16: launch_rows_L<T, 16>(h, g, p, pn); break;
+      case 24: launch_rows_L<T, 24>(h, g, p, pn); break;
+      case 32: launch_rows_L<T, 32>(h, g, p, pn); break;
+      default: return FDTD_ERR_UNSUPPORTED;
+    }
+  } else {
+    const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];
+    if (!cfg.ok) return FDTD_ERR_UNSUPPORTED;
+    launch_strided<T>(h, g, p, pn, cfg.lanes, cfg.L);
+  }
+  CK(cudaGetLastError());
+  if (h->timing) {
+    CK(cudaEventRecord(h->ev_pool[ev1], h->stream));
+    h->ev_rec.push_back({cls, {ev0, ev1}});
+    // resolve in batches so the pool stays small
+    if (h->ev_rec.size() >= 4096) {
+      int rc = resolve_events(h);
+      if (rc) return rc;
+    }
+  }
+  return FDTD_OK;
+}
+
+// One updating procedure.  sgn = -1 runs the inverse procedure (length -h),
+// whose tridiagonal matrices are the same and whose couplings flip sign.
+// rhs_src / post_src: values at the source sample (E component only).
+template <typename T>
+int run_procedure(fdtd_t* h, int slot, double sgn, double alpha, double beta, double kd_mul,
+                  void* const* in, void* const* out, double rhs_src, double post_src) {
+  const ProcCoef& P = h->proc[slot];
+  for (int q = 0; q < 3; ++q) {
+    const PairGeom& g = h->geom[P.op][q];
+    fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], sgn, alpha, beta, kd_mul, in, out);
+    if (rhs_src != 0.0 || post_src != 0.0) set_src<T>(h, g, p, rhs_src, post_src);
+    int rc = launch_pair<T>(h, g, p);
+    if (rc) return rc;
+  }
+  return FDTD_OK;
+}
+
+// The forward procedure: E <- w - E, H <- H + kd dw, in place.
+int procedure(fdtd_t* h, int slot, double rhs_src, double post_src) {
+  return h->prec == FDTD_F64
+             ? run_procedure<double>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f, rhs_src, post_src)
+             : run_procedure<float>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f, rhs_src, post_src);
+}
+
+int procedure_ex(fdtd_t* h, int slot, double sgn, double alpha, double beta, double kd_mul,
+                 void* const* in, void* const* out, double rhs_src) {
+  return h->prec == FDTD_F64
+             ? run_procedure<double>(h, slot, sgn, alpha, beta, kd_mul, in, out, rhs_src, 0.0)
+             : run_procedure<float>(h, slot, sgn, alpha, beta, kd_mul, in, out, rhs_src, 0.0);
+}
+
+int ensure_scratch(fdtd_t* h) {
+  for (int c = 0; c < 6; ++c) {
+    if (!h->scratch[c]) {
+      CK(cudaMalloc(&h->scratch[c], (size_t)h->count * h->esize));
+      CK(cudaMemsetAsync(h->scratch[c], 0, (size_t)h->count * h->esize, h->stream));
+    }
+  }
+  return FDTD_OK;
+}
+
+int copy_state_to_scratch(fdtd_t* h) {
+  int rc = ensure_scratch(h);
+  if (rc) return rc;
+  for (int c = 0; c < 6; ++c)
+    CK(cudaMemcpyAsync(h->scratch[c], h->f[c], (size_t)h->count * h->esize, cudaMemcpyDeviceToDevice,
+                       h->stream));
+  return FDTD_OK;
+}
+
+double source_value(const fdtd_t* h, long long n) {
+  // f_E at the source sample for step n: -I(t_n + dt/2)/(A eps)
+  if (h->src_comp < 0 || n < 0 || n >= (long long)h->src_current.size()) return 0.0;
+  return h->src_scale * h->src_current[(size_t)n];
+}
+
+long long elem_index(const fdtd_t* h, int i, int j, int k) {
+  return (long long)k * h->plane + (long long)j * h->pitch + i;
+}
+
+// FADI input initialization (Eq. 10 with Eqs. 7, 8a): v^0 = (I + dt/2 B) u^0
+// plus the first sub-step's source (dt/2) f.
+template <typename T>
+int fadi_init_t(fdtd_t* h) {
+  int rc = copy_state_to_scratch(h);
+  if (rc) return rc;
+  const ProcCoef& P = h->proc[1];
+  for (int q = 0; q < 3; ++q) {
+    const PairGeom& g = h->geom[1][q];
+    if (g.empty()) continue;
+    // (I + tau B) with tau = dt/2: kb = s*b/d_eta with b = dt/(2 eps) = tau/eps
+    fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, 0.0, 1.0, h->f, h->scratch);
+    const long long total = g.n_lines() * g.N;
+    const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);
+    h->launches++;
+    if (h->per_node)
+      fdtd::explicit_pair_kernel<T, true><<<blocks, 256, 0, h->stream>>>(p, g.rows ? 1 : 0);
+    else
+      fdtd::explicit_pair_kernel<T, false><<<blocks, 256, 0, h->stream>>>(p, g.rows ? 1 : 0);
+    CK(cudaGetLastError());
+  }
+  for (int c = 0; c < 6; ++c) std::swap(h->f[c], h->scratch[c]);
+  const double f0 = source_value(h, h->steps);
+  if (f0 != 0.0) {
+    h->launches++;
+    fdtd::add_point_kernel<T><<<1, 32, 0, h->stream>>>(
+        (T*)h->f[h->src_comp], elem_index(h, h->src_i, h->src_j, h->src_k), 0.5 * h->dt * f0);
+    CK(cudaGetLastError());
+  }
+  h->output_valid = false;
+  return FDTD_OK;
+}
+
+int scheme_init(fdtd_t* h) {
+  if (!h->pending_init) return FDTD_OK;
+  int rc = FDTD_OK;
+  if (h->scheme == FDTD_FADI) {
+    rc = h->prec == FDTD_F64 ? fadi_init_t<double>(h) : fadi_init_t<float>(h);
+  } else if (h->scheme == FDTD_FLOD2) {
+    // Eq. 22: (1/2 I - dt/8 B) v = u^0, u^{1/4} = v - u^0  (procedure of length dt/2)
+    rc = procedure(h, 2, 0.0, 0.0);
+  }
+  if (rc) return rc;
+  h->pending_init = false;
+  return FDTD_OK;
+}
+
+template <typename T>
+int record_probes(fdtd_t* h, int mode) {
+  if (h->nprobes == 0) return FDTD_OK;
+  fdtd::ProbeParams<T> pp;
+  pp.n = h->nprobes;
+  for (int q = 0; q < h->nprobes; ++q) {
+    pp.arr[q] = (const T*)h->f[h->probe_comp[q]];
+    pp.at[q] = h->probe_at[q];
+  }
+  h->launches++;
+  fdtd::probe_kernel<T><<<1, 32, 0, h->stream>>>(pp, h->d_stash, h->d_probe, h->probe_cap, h->steps, mode);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int probes(fdtd_t* h, int mode) {
+  return h->prec == FDTD_F64 ? record_probes<double>(h, mode) : record_probes<float>(h, mode);
+}
+
+int ensure_probe_capacity(fdtd_t* h, long long need) {
+  if (h->nprobes == 0 || need <= h->probe_cap) return FDTD_OK;
+  long long cap = std::max<long long>(need, 2 * h->probe_cap);
+  cap = std::max<long long>(cap, 1024);
+  double* np = nullptr;
+  CK(cudaMalloc(&np, sizeof(double) * fdtd::kMaxProbes * cap));
+  CK(cudaMemsetAsync(np, 0, sizeof(double) * fdtd::kMaxProbes * cap, h->stream));
+  if (h->d_probe) {
+    CK(cudaMemcpy2DAsync(np, sizeof(double) * cap, h->d_probe, sizeof(double) * h->probe_cap,
+                         sizeof(double) * h->probe_cap, fdtd::kMaxProbes, cudaMemcpyDeviceToDevice,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_probe);
+  }
+  h->d_probe = np;
+  h->probe_cap = cap;
+  return FDTD_OK;
+}
+
+// One time step of the handle's scheme (Sec. II):
+//   FADI  P_A(dt), P_B(dt) on the auxiliary state, the source (dt/2) f added
+//         to the state after each procedure (it is part of v, Eqs. 2, 8);
+//   FLOD  P_A(dt), P_B(dt) with +(dt/4) f in each implicit RHS (Eq. 15);
+//   FSS   P_A(dt/2), P_B(dt), P_A(dt/2) with +(h/4) f (Eq. 17);
+//   FLOD2 FLOD main iterations (Eq. 21).
+int one_step(fdtd_t* h) {
+  const long long n = h->steps;
+  const double dt = h->dt;
+  const double f = source_value(h, n);
+  int rc;
+  switch (h->scheme) {
+    case FDTD_FADI: {
+      const double fn = source_value(h, n + 1);
+      if ((rc = procedure(h, 0, 0.0, 0.5 * dt * f))) return rc;
+      if ((rc = probes(h, 0))) return rc;
+      if ((rc = procedure(h, 1, 0.0, 0.5 * dt * fn))) return rc;
+      if ((rc = probes(h, 1))) return rc;
+      break;
+    }
+    case FDTD_FLOD:
+    case FDTD_FLOD2: {
+      if ((rc = procedure(h, 0, 0.25 * dt * f, 0.0))) return rc;
+      if ((rc = procedure(h, 1, 0.25 * dt * f, 0.0))) return rc;
+      if (h->nprobes) {
+        if (h->scheme == FDTD_FLOD) {
+          if ((rc = probes(h, 2))) return rc;
+        } else {
+          // probes of the FLOD2 physical field: output processing (Eq. 23) into scratch
+          return FDTD_ERR_UNSUPPORTED;
+        }
+      }
+      break;
+    }
+    case FDTD_FSS: {
+      if ((rc = procedure(h, 0, 0.125 * dt * f, 0.0))) return rc;
+      if ((rc = procedure(h, 1, 0.25 * dt * f, 0.0))) return rc;
+      if ((rc = procedure(h, 0, 0.125 * dt * f, 0.0))) return rc;
+      if ((rc = probes(h, 2))) return rc;
+      break;
+    }
+    default:
+      return FDTD_ERR_STATE;
+  }
+  h->steps++;
+  return FDTD_OK;
+}
+
+// Physical field into scratch (FADI: (I + dt/2 B)^{-1}(v - pending source),
+// from Eqs. 2a, 8a, 9; FLOD2: output processing Eq. 23).
+int physical_to_scratch(fdtd_t* h) {
+  if (h->output_valid) return FDTD_OK;
+  int rc = copy_state_to_scratch(h);
+  if (rc) return rc;
+  if (!h->pending_init) {
+    if (h->scheme == FDTD_FADI) {
+      // u = (I + dt/2 B)^{-1} (v - (dt/2) f_pending), from Eqs. 2a, 8a and 9:
+      // the B pairs' line systems with the couplings of a procedure of length
+      // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
+      const double fp = source_value(h, h->steps);
+      rc = procedure_ex(h, 1, -1.0, 0.5, 0.0, 0.5, h->f, h->scratch, -0.5 * h->dt * fp);
+      if (rc) return rc;
+    } else if (h->scheme == FDTD_FLOD2) {
+      // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4}, u^{n+1} = v - u^{n+5/4}
+      rc = procedure_ex(h, 2, -1.0, 1.0, -1.0, 1.0, h->f, h->scratch, 0.0);
+      if (rc) return rc;
+    }
+  }
+  h->output_valid = true;
+  return FDTD_OK;
+}
+
+int check_comp(int c) { return (c >= 0 && c < 6) ? FDTD_OK : FDTD_ERR_INVALID_ARG; }
+
+int copy_component(fdtd_t* h, int comp, const void* src_padded, void* dst, int on_device) {
+  int sx, sy, sz;
+  comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  cudaMemcpy3DParms m = {};
+  m.srcPtr = make_cudaPitchedPtr((void*)src_padded, (size_t)h->pitch * h->esize, (size_t)h->pitch,
+                                 (size_t)(h->ny + 1));
+  m.dstPtr = make_cudaPitchedPtr(dst, (size_t)sx * h->esize, (size_t)sx, (size_t)sy);
+  m.extent = make_cudaExtent((size_t)sx * h->esize, (size_t)sy, (size_t)sz);
+  m.kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpy3DAsync(&m, h->stream));
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int copy_in_component(fdtd_t* h, int comp, const void* src, void* dst_padded, int on_device) {
+  int sx, sy, sz;
+  comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  cudaMemcpy3DParms m = {};
+  m.srcPtr = make_cudaPitchedPtr((void*)src, (size_t)sx * h->esize, (size_t)sx, (size_t)sy);
+  m.dstPtr = make_cudaPitchedPtr(dst_padded, (size_t)h->pitch * h->esize, (size_t)h->pitch,
+                                 (size_t)(h->ny + 1));
+  m.extent = make_cudaExtent((size_t)sx * h->esize, (size_t)sy, (size_t)sz);
+  m.kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpy3DAsync(&m, h->stream));
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+template <typename T>
+__global__ void zero_walls_kernel(T* e, int comp, int nx, int ny, int nz, long long pitch, long long plane) {
+  int sx, sy, sz;
+  if (comp == 0) { sx = nx; sy = ny + 1; sz = nz + 1; }
+  else if (comp == 1) { sx = nx + 1; sy = ny; sz = nz + 1; }
+  else { sx = nx + 1; sy = ny + 1; sz = nz; }
+  const long long total = (long long)sx * sy * sz;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(g % sx);
+    const int j = (int)((g / sx) % sy);
+    const int k = (int)(g / ((long long)sx * sy));
+    bool wall;
+    if (comp == 0) wall = (j == 0 || j == ny || k == 0 || k == nz);
+    else if (comp == 1) wall = (i == 0 || i == nx || k == 0 || k == nz);
+    else wall = (i == 0 || i == nx || j == 0 || j == ny);
+    if (wall) e[k * plane + j * pitch + i] = T(0);
+  }
+}
+
+int zero_walls(fdtd_t* h, int comp, void* arr) {
+  if (comp >= 3) return FDTD_OK;
+  h->launches++;
+  if (h->prec == FDTD_F64)
+    zero_walls_kernel<double><<<256, 256, 0, h->stream>>>((double*)arr, comp, h->nx, h->ny, h->nz, h->pitch, h->plane);
+  else
+    zero_walls_kernel<float><<<256, 256, 0, h->stream>>>((float*)arr, comp, h->nx, h->ny, h->nz, h->pitch, h->plane);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+template <typename T>
+int energy_of(fdtd_t* h, void* const* arr, double* out) {
+  const int blocks = 152 * 4;
+  if (!h->d_partial) {
+    CK(cudaMalloc(&h->d_partial, sizeof(double) * 6 * blocks));
+    h->partial_n = blocks;
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double w = c < 3 ? kEps0 * (h->per_node ? 1.0 : h->eps_r) : kMu0 * h->mu_r;
+    const double* wv = (c < 3 && h->per_node) ? h->eps_node[c] : nullptr;
+    h->launches++;
+    fdtd::weighted_sumsq_kernel<T><<<blocks, 256, 0, h->stream>>>((const T*)arr[c], wv, w, h->count,
+                                                                  h->d_partial + (size_t)c * blocks);
+    CK(cudaGetLastError());
+  }
+  std::vector<double> part((size_t)6 * blocks);
+  CK(cudaMemcpyAsync(part.data(), h->d_partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double s = 0;
+  for (double v : part) s += v;
+  *out = 0.5 * h->dx * h->dy * h->dz * s;
+  return FDTD_OK;
+}
+
+int energy(fdtd_t* h, void* const* arr, double* out) {
+  return h->prec == FDTD_F64 ? energy_of<double>(h, arr, out) : energy_of<float>(h, arr, out);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char* fdtd_strerror(int code) {
+  switch (code) {
+    case FDTD_OK: return "ok";
+    case FDTD_ERR_INVALID_ARG: return "invalid argument";
+    case FDTD_ERR_OOM: return "out of memory";
+    case FDTD_ERR_CUDA: return "CUDA error (handle poisoned)";
+    case FDTD_ERR_TIMEOUT: return "device wait timed out";
+    case FDTD_ERR_UNSTABLE: return "non-finite field or invariant";
+    case FDTD_ERR_UNSUPPORTED: return "unsupported in this build";
+    case FDTD_ERR_STATE: return "call not valid in the handle's state";
+    default: return "unknown error";
+  }
+}
+
+int fdtd_create(const fdtd_desc* desc, void* stream, fdtd_t** out) {
+  if (!desc || !out) return FDTD_ERR_INVALID_ARG;
+  *out = nullptr;
+  const fdtd_desc& d = *desc;
+  if (d.nx < 2 || d.ny < 2 || d.nz < 1 || d.nx > 1024 || d.ny > 4096 || d.nz > 4096) return FDTD_ERR_INVALID_ARG;
+  if (!(d.dx > 0) || !(d.dy > 0) || !(d.dz > 0) || !std::isfinite(d.dx) || !std::isfinite(d.dy) ||
+      !std::isfinite(d.dz))
+    return FDTD_ERR_INVALID_ARG;
+  if (d.scheme < FDTD_FADI || d.scheme > FDTD_FLOD2) return FDTD_ERR_INVALID_ARG;
+  if (d.precision != FDTD_F64 && d.precision != FDTD_F32) return FDTD_ERR_INVALID_ARG;
+  double dt = d.dt;
+  if (!(dt > 0)) {
+    if (!(d.cfl > 0) || !std::isfinite(d.cfl)) return FDTD_ERR_INVALID_ARG;
+    double s = 1.0 / (d.dx * d.dx) + 1.0 / (d.dy * d.dy);
+    if (d.nz > 1) s += 1.0 / (d.dz * d.dz);
+    dt = d.cfl / (kC0 * std::sqrt(s));
+  }
+  if (!std::isfinite(dt) || !(dt > 0)) return FDTD_ERR_INVALID_ARG;
+  fdtd_t* h = new (std::nothrow) fdtd_s();
+  if (!h) return FDTD_ERR_OOM;
+  h->desc = d;
+  h->nx = d.nx; h->ny = d.ny; h->nz = d.nz;
+  h->dx = d.dx; h->dy = d.dy; h->dz = d.dz;
+  h->dt = dt;
+  h->scheme = d.scheme;
+  h->prec = d.precision;
+  h->esize = d.precision == FDTD_F64 ? 8 : 4;
+  h->stream = (cudaStream_t)stream;
+  h->pitch = std::max(((long long)(d.nx + 1) + 31) / 32 * 32, 32LL * std::max(1, pick_rows_L(d.nx)));
+  h->plane = h->pitch * (d.ny + 1);
+  h->count = h->plane * (d.nz + 1);
+  h->pending_init = (d.scheme == FDTD_FADI || d.scheme == FDTD_FLOD2);
+  build_geometry(h);
+  // y/z line blocks hold every segment of a line; x rows need pitch >= 32 L
+  if (pick_rows_L(d.nx) < 0) { delete h; return FDTD_ERR_UNSUPPORTED; }
+  for (int ax = 0; ax < 2; ++ax) {
+    const int N = ax == 0 ? d.ny : d.nz;
+    StridedCfg a, b;
+    if (h->prec == FDTD_F64) {
+      a = choose_strided<double>(N, false, d.tune[0]);
+      b = choose_strided<double>(N, true, d.tune[0]);
+    } else {
+      a = choose_strided<float>(N, false, d.tune[0]);
+      b = choose_strided<float>(N, true, d.tune[0]);
+    }
+    // one configuration for both coefficient modes: the more constrained one
+    if (!a.ok || !b.ok) {
+      if (N >= 2) { delete h; return FDTD_ERR_UNSUPPORTED; }
+    }
+    h->strided_cfg[ax] = (a.lanes * a.L == b.lanes * b.L && a.lanes == b.lanes) ? a : b;
+  }
+  for (int c = 0; c < 6; ++c) {
+    cudaError_t e = cudaMalloc(&h->f[c], (size_t)h->count * h->esize);
+    if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
+    e = cudaMemsetAsync(h->f[c], 0, (size_t)h->count * h->esize, h->stream);
+    if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_CUDA; }
+  }
+  for (int cls = 0; cls < 3; ++cls)
+    h->bytes_per_launch[cls] = 4.0 * (double)d.nx * d.ny * d.nz * (double)h->esize;
+  cudaError_t e = cudaMalloc(&h->d_stash, sizeof(double) * fdtd::kMaxProbes);
+  if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
+  int rc = build_all_coefs(h);
+  if (rc) { fdtd_destroy(h); return rc; }
+  *out = h;
+  return FDTD_OK;
+}
+
+int fdtd_destroy(fdtd_t* h) {
+  if (!h) return FDTD_OK;
+  cudaStreamSynchronize(h->stream);
+  for (int c = 0; c < 6; ++c) {
+    if (h->f[c]) cudaFree(h->f[c]);
+    if (h->scratch[c]) cudaFree(h->scratch[c]);
+  }
+  for (auto& p : h->proc) free_coef(p);
+  for (int c = 0; c < 3; ++c)
+    if (h->eps_node[c]) cudaFree(h->eps_node[c]);
+  if (h->d_probe) cudaFree(h->d_probe);
+  if (h->d_stash) cudaFree(h->d_stash);
+  if (h->d_partial) cudaFree(h->d_partial);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return FDTD_OK;
+}
+
+int fdtd_get_dt(const fdtd_t* h, double* dt) {
+  if (!h || !dt) return FDTD_ERR_INVALID_ARG;
+  *dt = h->dt;
+  return FDTD_OK;
+}
+
+int fdtd_steps_done(const fdtd_t* h, int64_t* n) {
+  if (!h || !n) return FDTD_ERR_INVALID_ARG;
+  *n = h->steps;
+  return FDTD_OK;
+}
+
+int fdtd_synchronize(fdtd_t* h) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->steps > 0) return FDTD_ERR_STATE;
+  const size_t nc = (size_t)h->nx * h->ny * h->nz;
+  const double e0 = eps ? eps[0] : 1.0, m0 = mu ? mu[0] : 1.0;
+  bool e_uniform = true, m_uniform = true;
+  for (size_t q = 0; q < nc; ++q) {
+    if (eps) {
+      if (!(eps[q] > 0) || !std::isfinite(eps[q])) return FDTD_ERR_INVALID_ARG;
+      if (eps[q] != e0) e_uniform = false;
+    }
+    if (mu) {
+      if (!(mu[q] > 0) || !std::isfinite(mu[q])) return FDTD_ERR_INVALID_ARG;
+      if (mu[q] != m0) m_uniform = false;
+    }
+  }
+  if (!m_uniform) return FDTD_ERR_UNSUPPORTED;
+  for (int c = 0; c < 3; ++c)
+    if (h->eps_node[c]) { cudaFree(h->eps_node[c]); h->eps_node[c] = nullptr; }
+  h->mu_r = m0;
+  h->per_node = !e_uniform;
+  h->eps_r = e_uniform ? e0 : 1.0;
+  int rc = FDTD_OK;
+  if (h->per_node) {
+    for (int c = 0; c < 3; ++c) {
+      edge_eps(h, eps, c, h->eps_host[c]);
+      CK(cudaMalloc(&h->eps_node[c], sizeof(double) * h->eps_host[c].size()));
+      CK(cudaMemcpyAsync(h->eps_node[c], h->eps_host[c].data(), sizeof(double) * h->eps_host[c].size(),
+                         cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  rc = build_all_coefs(h);
+  for (int c = 0; c < 3; ++c) std::vector<double>().swap(h->eps_host[c]);
+  h->output_valid = false;
+  return rc;
+}
+
+int fdtd_set_field(fdtd_t* h, int comp, const void* data, int on_device) {
+  if (!h || !data || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc;
+  if ((h->scheme == FDTD_FADI || h->scheme == FDTD_FLOD2) && !h->pending_init) {
+    // back to the physical field, then re-initialise on the next step
+    if ((rc = physical_to_scratch(h))) return rc;
+    for (int c = 0; c < 6; ++c) std::swap(h->f[c], h->scratch[c]);
+    h->pending_init = true;
+  }
+  if ((rc = copy_in_component(h, comp, data, h->f[comp], on_device))) return rc;
+  if ((rc = zero_walls(h, comp, h->f[comp]))) return rc;
+  h->output_valid = false;
+  return FDTD_OK;
+}
+
+int fdtd_get_field(fdtd_t* h, int comp, void* out, int on_device) {
+  if (!h || !out || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->scheme == FDTD_FLOD || h->scheme == FDTD_FSS || h->pending_init)
+    return copy_component(h, comp, h->f[comp], out, on_device);
+  int rc = physical_to_scratch(h);
+  if (rc) return rc;
+  return copy_component(h, comp, h->scratch[comp], out, on_device);
+}
+
+int fdtd_get_state(fdtd_t* h, int comp, void* out, int on_device) {
+  if (!h || !out || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc = scheme_init(h);
+  if (rc) return rc;
+  return copy_component(h, comp, h->f[comp], out, on_device);
+}
+
+int fdtd_set_state(fdtd_t* h, int comp, const void* data, int on_device) {
+  if (!h || !data || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc = scheme_init(h);
+  if (rc) return rc;
+  if ((rc = copy_in_component(h, comp, data, h->f[comp], on_device))) return rc;
+  if ((rc = zero_walls(h, comp, h->f[comp]))) return rc;
+  h->output_valid = false;
+  return FDTD_OK;
+}
+
+int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* current, int64_t count) {
+  if (!h || count < 0 || (count > 0 && !current)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (count == 0) {
+    h->src_comp = -1;
+    h->src_current.clear();
+    h->output_valid = false;
+    return FDTD_OK;
+  }
+  if (comp < 0 || comp > 2) return FDTD_ERR_INVALID_ARG;
+  int sx, sy, sz;
+  comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  if (i < 0 || j < 0 || k < 0 || i >= sx || j >= sy || k >= sz) return FDTD_ERR_INVALID_ARG;
+  bool wall;
+  if (comp == EX) wall = (j == 0 || j == h->ny || k == 0 || k == h->nz);
+  else if (comp == EY) wall = (i == 0 || i == h->nx || k == 0 || k == h->nz);
+  else wall = (i == 0 || i == h->nx || j == 0 || j == h->ny);
+  if (wall) return FDTD_ERR_INVALID_ARG;
+  for (int64_t q = 0; q < count; ++q)
+    if (!std::isfinite(current[q])) return FDTD_ERR_INVALID_ARG;
+  h->src_comp = comp;
+  h->src_i = i; h->src_j = j; h->src_k = k;
+  h->src_current.assign(current, current + count);
+  h->output_valid = false;
+  return FDTD_OK;
+}
+
+int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id) {
+  if (!h || !id || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->nprobes >= fdtd::kMaxProbes) return FDTD_ERR_INVALID_ARG;
+  if (h->scheme == FDTD_FLOD2) return FDTD_ERR_UNSUPPORTED;
+  int sx, sy, sz;
+  comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  if (i < 0 || j < 0 || k < 0 || i >= sx || j >= sy || k >= sz) return FDTD_ERR_INVALID_ARG;
+  const int q = h->nprobes;
+  h->probe_comp[q] = comp;
+  h->probe_at[q] = elem_index(h, i, j, k);
+  h->probe_start[q] = h->steps;
+  h->nprobes++;
+  *id = q;
+  return FDTD_OK;
+}
+
+int fdtd_step(fdtd_t* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (nsteps == 0) return FDTD_OK;
+  int rc = scheme_init(h);
+  if (rc) return rc;
+  if ((rc = ensure_probe_capacity(h, h->steps + nsteps))) return rc;
+  if (h->src_comp >= 0) {
+    // f_E = -I / (A eps) at the source sample
+    double er = h->eps_r;
+    if (h->per_node)
+      CK(cudaMemcpy(&er, h->eps_node[h->src_comp] + elem_index(h, h->src_i, h->src_j, h->src_k),
+                    sizeof(double), cudaMemcpyDeviceToHost));
+    const double area = h->src_comp == EX ? h->dy * h->dz : (h->src_comp == EY ? h->dx * h->dz : h->dx * h->dy);
+    h->src_scale = -1.0 / (area * kEps0 * er);
+  }
+  for (int64_t q = 0; q < nsteps; ++q)
+    if ((rc = one_step(h))) return rc;
+  h->output_valid = false;
+  return FDTD_OK;
+}
+
+int fdtd_get_probe(fdtd_t* h, int id, double* out, int64_t n) {
+  if (!h || !out || id < 0 || id >= h->nprobes || n < 0) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->probe_start[id] + n > h->steps) return FDTD_ERR_INVALID_ARG;
+  if (n == 0) return FDTD_OK;
+  CK(cudaMemcpyAsync(out, h->d_probe + (size_t)id * h->probe_cap + h->probe_start[id], sizeof(double) * n,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int fdtd_energy(fdtd_t* h, double out[2]) {
+  if (!h || !out) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc = scheme_init(h);
+  if (rc) return rc;
+  if ((rc = energy(h, h->f, &out[1]))) return rc;
+  if (h->scheme == FDTD_FLOD || h->scheme == FDTD_FSS) {
+    out[0] = out[1];
+  } else {
+    if ((rc = physical_to_scratch(h))) return rc;
+    if ((rc = energy(h, h->scratch, &out[0]))) return rc;
+  }
+  if (!std::isfinite(out[0]) || !std::isfinite(out[1])) return FDTD_ERR_UNSTABLE;
+  return FDTD_OK;
+}
+
+int fdtd_set_timing(fdtd_t* h, int enable) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  h->timing = enable != 0;
+  return FDTD_OK;
+}
+
+int fdtd_get_stats(fdtd_t* h, fdtd_stats* out) {
+  if (!h || !out) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc = resolve_events(h);
+  if (rc) return rc;
+  out->launches = h->launches;
+  for (int c = 0; c < 3; ++c) {
+    out->timed_launches[c] = h->timed_launches[c];
+    out->timed_ms[c] = h->timed_ms[c];
+    out->bytes_per_launch[c] = h->bytes_per_launch[c];
+  }
+  return FDTD_OK;
+}
+
+int fdtd_reset_stats(fdtd_t* h) {
+  if (!h) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  int rc = resolve_events(h);
+  if (rc) return rc;
+  h->launches = 0;
+  for (int c = 0; c < 3; ++c) {
+    h->timed_launches[c] = 0;
+    h->timed_ms[c] = 0;
+  }
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Bars: relative error <= 1e-12 in FP64 mode and <= 1e-4
+in FP32 mode (energy norm over all six components and per component)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import grid as G
+from oracle import invariants as I
+from oracle import schemes as S
+
+from gpu_helpers import (energy_norm_rel, gpu_run, oracle_problem, per_comp_rel,
+                         random_fields)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-4}
+
+
+def check(a, b, prec):
+    e = energy_norm_rel(a, b)
+    assert e <= TOL[prec], e
+    for c, v in per_comp_rel(a, b).items():
+        assert v <= TOL[prec] * 10, (c, v)
+    return e
+
+
+def test_2d_gaussian_fadi_f64_vs_original_adi():
+    """64 x 64 TM (nz = 1), CFL 5, 200 steps, probe Ez(16,16) vs the original ADI."""
+    wl = W.workload_2d_gaussian(seed=1)
+    g = G.Grid(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz)
+    dt = wl.cfl * g.dt_cfl()
+    P = S.Problem(g, dt)
+    u = {c: wl.fields[c].copy() for c in G.COMPS}
+    probe = np.zeros(wl.steps)
+    for n in range(wl.steps):
+        u = S.orig_adi_step(P, u, n)
+        probe[n] = u["ez"][0, 16, 16]
+    out, series, en, _ = gpu_run(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, dt, "fadi", "f64",
+                                 wl.fields, wl.steps, probes=[("ez", 16, 16, 0)])
+    check(out, u, "f64")
+    assert np.max(np.abs(series[0] - probe)) <= 1e-12 * np.max(np.abs(probe))
+    assert en[0] == pytest.approx(I.energy(g, P.mat, u), rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["fadi", "flod", "fss", "flod2"])
+@pytest.mark.parametrize("dims", [(40, 37, 29), (33, 20, 70)])
+def test_3d_schemes_vs_oracle(scheme, prec, dims):
+    """Grids spanning several warps/segments with ragged tails on every axis."""
+    nx, ny, nz = dims
+    d = (1e-3, 0.9e-3, 1.1e-3)
+    g = G.Grid(nx, ny, nz, *d)
+    dt = 6.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=sum(dims))
+    steps = 12
+    P = S.Problem(g, dt)
+    ref, _, _ = S.run_fundamental(P, scheme, u0, steps)
+    out, _, _, _ = gpu_run(nx, ny, nz, *d, dt, scheme, prec, u0, steps)
+    check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["flod", "fss", "fadi"])
+def test_inhomogeneous_with_dipole_vs_oracle(scheme, prec):
+    """eps_r blocks in [1, 10] and a z-directed dipole (per-node coefficients)."""
+    nx, ny, nz = 36, 34, 30
+    d = 0.5e-3
+    g = G.Grid(nx, ny, nz, d, d, d)
+    dt = 8.0 * g.dt_cfl()
+    eps = W.eps_blocks(3, nx, ny, nz, 1.0, 10.0)
+    steps = 30
+    cur = W.dipole_current((np.arange(steps) + 0.5) * dt * 20)  # compressed pulse in time
+    src = ("ez", nx // 2, ny // 2, nz // 2, cur)
+    P = oracle_problem(nx, ny, nz, d, d, d, dt, eps=eps, source=src)
+    u0 = W.zero_fields(nx, ny, nz)
+    ref, _, _ = S.run_fundamental(P, scheme, u0, steps)
+    out, _, en, _ = gpu_run(nx, ny, nz, d, d, d, dt, scheme, prec, u0, steps, eps=eps, source=src)
+    check(out, ref, prec)
+    assert en[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec] * 10)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 1), (2, 2, 2), (3, 2, 2), (2, 3, 4), (5, 4, 1), (3, 3, 3)])
+@pytest.mark.parametrize("scheme", ["fadi", "flod"])
+def test_degenerate_tiny_grids(dims, scheme):
+    """Lines with zero or one unknown, a single layer, single-warp rows."""
+    nx, ny, nz = dims
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 3.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=nx * 100 + ny * 10 + nz)
+    P = S.Problem(g, dt)
+    ref, _, _ = S.run_fundamental(P, scheme, u0, 5)
+    out, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, scheme, "f64", u0, 5)
+    check(out, ref, "f64")
+
+
+@pytest.mark.parametrize("dims", [(300, 3, 3), (3, 300, 3), (3, 3, 300), (1000, 2, 2)])
+def test_long_lines(dims):
+    """Long lines along each axis (many segments; x rows up to 32 nodes/lane)."""
+    nx, ny, nz = dims
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 10.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=7)
+    P = S.Problem(g, dt)
+    ref, _, _ = S.run_fundamental(P, "fadi", u0, 4)
+    for prec in ("f64", "f32"):
+        out, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 4)
+        check(out, ref, prec)
+
+
+@pytest.mark.parametrize("L", [8, 16, 32])
+def test_segment_length_choices_agree(L):
+    """Every y/z segment length gives the oracle's answer (tuning override)."""
+    nx, ny, nz = 35, 70, 45
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 4.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=L)
+    P = S.Problem(g, dt)
+    ref, _, _ = S.run_fundamental(P, "fadi", u0, 3)
+    out, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", "f64", u0, 3, tune=(L, 0))
+    check(out, ref, "f64")
+
+
+def test_state_round_trip_and_restart():
+    """Checkpoint the raw FADI state, restore it in a new handle, continue: same as straight through."""
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 20, 18, 16
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 4.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=3)
+    a = Simulation(nx, ny, nz, 1e-3, scheme="fadi", precision="f64", dt=dt)
+    a.set_fields(u0)
+    a.step(5)
+    state = {c: a.get_state(c) for c in G.COMPS}
+    a.step(5)
+    b = Simulation(nx, ny, nz, 1e-3, scheme="fadi", precision="f64", dt=dt)
+    for c in G.COMPS:
+        b.set_state(c, state[c])
+    b.step(5)
+    fa = a.get_fields()
+    fb = b.get_fields()
+    assert energy_norm_rel(fb, fa) == 0.0
+
+
+def test_set_field_after_steps_reinitialises():
+    """Setting a field mid-run re-forms the FADI state from the physical field."""
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 16, 14, 12
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 4.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=5)
+    P = S.Problem(g, dt)
+    sim = Simulation(nx, ny, nz, 1e-3, scheme="fadi", precision="f64", dt=dt)
+    sim.set_fields(u0)
+    sim.step(3)
+    mid = sim.get_fields()
+    mid["ez"] = mid["ez"] * 0.5
+    sim.set_field("ez", mid["ez"])
+    sim.step(3)
+    ref, _, _ = S.run_fundamental(P, "fadi", mid, 3)
+    check(sim.get_fields(), ref, "f64")
+
+
+def test_device_buffers_path():
+    """set_field/get_field with torch CUDA tensors (on_device = 1)."""
+    import torch
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 24, 20, 18
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 4.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=9)
+    sim = Simulation(nx, ny, nz, 1e-3, scheme="flod", precision="f64", dt=dt)
+    for c in G.COMPS:
+        sim.set_field(c, torch.from_numpy(u0[c]).cuda())
+    sim.step(4)
+    out = {c: sim.get_field(c, device=True).cpu().numpy() for c in G.COMPS}
+    ref, _, _ = S.run_fundamental(S.Problem(g, dt), "flod", u0, 4)
+    check(out, ref, "f64")
