@@ -771,6 +771,21 @@ int physical_to_scratch(fdtd_t* h) {
 
 int check_comp(int c) { return (c >= 0 && c < 6) ? FDTD_OK : FDTD_ERR_INVALID_ARG; }
 
+// f_E = -I / (A eps) at the source sample (A = the sample's dual-face area).
+int refresh_src_scale(fdtd_t* h) {
+  if (h->src_comp < 0) {
+    h->src_scale = 0;
+    return FDTD_OK;
+  }
+  double er = h->eps_r;
+  if (h->per_node)
+    CK(cudaMemcpy(&er, h->eps_node[h->src_comp] + elem_index(h, h->src_i, h->src_j, h->src_k), sizeof(double),
+                  cudaMemcpyDeviceToHost));
+  const double area = h->src_comp == EX ? h->dy * h->dz : (h->src_comp == EY ? h->dx * h->dz : h->dx * h->dy);
+  h->src_scale = -1.0 / (area * kEps0 * er);
+  return FDTD_OK;
+}
+
 int copy_component(fdtd_t* h, int comp, const void* src_padded, void* dst, int on_device) {
   int sx, sy, sz;
   comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
@@ -1020,7 +1035,8 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   rc = build_all_coefs(h);
   for (int c = 0; c < 3; ++c) std::vector<double>().swap(h->eps_host[c]);
   h->output_valid = false;
-  return rc;
+  if (rc) return rc;
+  return refresh_src_scale(h);
 }
 
 int fdtd_set_field(fdtd_t* h, int comp, const void* data, int on_device) {
@@ -1092,7 +1108,7 @@ int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* curr
   h->src_i = i; h->src_j = j; h->src_k = k;
   h->src_current.assign(current, current + count);
   h->output_valid = false;
-  return FDTD_OK;
+  return refresh_src_scale(h);
 }
 
 int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id) {
@@ -1119,15 +1135,6 @@ int fdtd_step(fdtd_t* h, int64_t nsteps) {
   int rc = scheme_init(h);
   if (rc) return rc;
   if ((rc = ensure_probe_capacity(h, h->steps + nsteps))) return rc;
-  if (h->src_comp >= 0) {
-    // f_E = -I / (A eps) at the source sample
-    double er = h->eps_r;
-    if (h->per_node)
-      CK(cudaMemcpy(&er, h->eps_node[h->src_comp] + elem_index(h, h->src_i, h->src_j, h->src_k),
-                    sizeof(double), cudaMemcpyDeviceToHost));
-    const double area = h->src_comp == EX ? h->dy * h->dz : (h->src_comp == EY ? h->dx * h->dz : h->dx * h->dy);
-    h->src_scale = -1.0 / (area * kEps0 * er);
-  }
   for (int64_t q = 0; q < nsteps; ++q)
     if ((rc = one_step(h))) return rc;
   h->output_valid = false;
