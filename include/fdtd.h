@@ -168,6 +168,28 @@ int fdtd_get_stats(fdtd_t* h, fdtd_stats* out);
 /* Zero the counters and drop recorded events. */
 int fdtd_reset_stats(fdtd_t* h);
 
+/* Field energy 1/2 dV sum(eps E^2 + mu H^2) of six device field arrays,
+ * without allocating anything.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory where they need
+ * the energy (inside a framework whose caching allocator holds the device's
+ * memory, or in a loop that cannot take cudaMalloc's implicit device-wide
+ * synchronisation).  Its per-plane partial sums live in a fixed 192 KiB
+ * file-scope device array that every GPU loading the library holds until
+ * the process exits.
+ *   fields[6]: device pointers on the current device, compact Yee shapes
+ *     ([k][j][i], x fastest), element type double (FDTD_F64) or float
+ *     (FDTD_F32); uniform eps_r and mu_r.
+ *   out_device: device pointer to one double that receives the energy.
+ *   stream: cudaStream_t or NULL; the call is asynchronous on it.
+ * Limit: nz <= 4096 (nz + 1 planes per component); larger nz returns
+ * FDTD_ERR_INVALID_ARG with a message on stderr.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU (other
+ * streams or threads) race on it. */
+int fdtd_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, double eps_r, double mu_r,
+                        int precision, const void* const* fields, double* out_device, void* stream);
+
 /* Static description of an error code. */
 const char* fdtd_strerror(int code);
 

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import COMPS, PRECISIONS, SCHEMES, FdtdDesc, FdtdError, FdtdStats, check, lib
 
-__all__ = ["Simulation", "FdtdError", "comp_shape", "build"]
+__all__ = ["Simulation", "FdtdError", "comp_shape", "build", "energy_noalloc"]
 
 
 def comp_shape(comp: str, nx: int, ny: int, nz: int) -> tuple:
@@ -36,6 +36,32 @@ def build(force: bool = False, verbose: bool = False) -> str:
 def _torch():
     import torch
     return torch
+
+
+def energy_noalloc(fields: dict, nx, ny, nz, dx, dy, dz, eps_r=1.0, mu_r=1.0, out=None, stream=None):
+    """Field energy of six CUDA tensors (compact Yee shapes) through
+    ``fdtd_energy_noalloc``, which allocates no device memory: for callers
+    that cannot allocate where they need the number.  ``out`` is a one-element
+    float64 CUDA tensor (allocated here if omitted, by the caller's side);
+    the result is written there asynchronously on ``stream``."""
+    torch = _torch()
+    ts = [fields[c] for c in COMPS]
+    if len({t.dtype for t in ts}) != 1 or ts[0].dtype not in (torch.float32, torch.float64):
+        raise ValueError("fields must share one dtype, float32 or float64")
+    for c, t in zip(COMPS, ts):
+        if not (t.is_cuda and t.is_contiguous()) or tuple(t.shape) != comp_shape(c, nx, ny, nz):
+            raise ValueError(f"{c}: need a contiguous CUDA tensor of shape {comp_shape(c, nx, ny, nz)}")
+    prec = PRECISIONS["f64" if ts[0].dtype == torch.float64 else "f32"]
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=ts[0].device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ptrs = (ctypes.c_void_p * 6)(*[t.data_ptr() for t in ts])
+    check(lib().fdtd_energy_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), float(eps_r),
+                                    float(mu_r), prec, ptrs, ctypes.cast(ctypes.c_void_p(out.data_ptr()),
+                                                                         ctypes.POINTER(ctypes.c_double)),
+                                    ctypes.c_void_p(int(stream))), "fdtd_energy_noalloc")
+    return out
 
 
 class Simulation:

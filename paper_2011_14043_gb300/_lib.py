@@ -31,6 +31,7 @@ EXPORTS = (
     "fdtd_get_field", "fdtd_get_state", "fdtd_set_state", "fdtd_set_source", "fdtd_add_probe",
     "fdtd_step", "fdtd_get_probe", "fdtd_energy", "fdtd_steps_done", "fdtd_synchronize",
     "fdtd_strerror", "fdtd_set_timing", "fdtd_get_stats", "fdtd_reset_stats",
+    "fdtd_energy_noalloc",
 )
 
 
@@ -95,6 +96,9 @@ def lib() -> ctypes.CDLL:
         "fdtd_set_timing": (i32, [vp, i32]),
         "fdtd_get_stats": (i32, [vp, ctypes.POINTER(FdtdStats)]),
         "fdtd_reset_stats": (i32, [vp]),
+        "fdtd_energy_noalloc": (i32, [i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, i32, ctypes.POINTER(vp),
+                                      ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

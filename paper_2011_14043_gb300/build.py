@@ -1,6 +1,6 @@
 """Compile the CUDA library (sm_103a) in-tree: ``_build/libfdtd.so``.
 
-One translation unit, one ``-gencode``; takes about ten seconds.  The
+Two translation units, one ``-gencode``; takes about ten seconds.  The
 library links the CUDA runtime statically, so it only needs the driver at
 run time.
 """
@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfdtd.so")
-SOURCES = [os.path.join(HERE, "csrc", "fdtd.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "fdtd.cu"), os.path.join(HERE, "csrc", "energy_noalloc.cu")]
 DEPENDS = SOURCES + [
     os.path.join(HERE, "csrc", "line_kernels.cuh"),
     os.path.join(HERE, "csrc", "aux_kernels.cuh"),
