@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", type=int, nargs=2, default=(0, 0), help="kernel-shape overrides (fdtd_desc.tune)")
     return ap.parse_args()
 
 
@@ -126,7 +127,7 @@ def run_gpu(args, prec, fields, time_kernels=True):
     import torch
     from paper_2011_14043_gb300 import Simulation
     n = args.n
-    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl)
+    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl, tune=tuple(args.tune))
     sim.set_fields(fields)
     sim.step(args.warmup)            # includes the Eq. 10 initialization
     sim.synchronize()
@@ -163,7 +164,7 @@ def run_e2e(args, prec, fields):
         t.numpy()[...] = v.astype(np_dtype)
         host_in[c] = t
         host_out[c] = torch.empty(v.shape, dtype=t_dtype, pin_memory=True)
-    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl)
+    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl, tune=tuple(args.tune))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for c in fields:

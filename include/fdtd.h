@@ -64,7 +64,8 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * dt > 0 is used as given; otherwise dt = cfl * dt_CFL with
  * dt_CFL = 1 / (c0 * sqrt(1/dx^2 + 1/dy^2 [+ 1/dz^2 when nz > 1])),
  * c0 = 299792458 m/s.  tune[] are kernel-shape overrides (0 = automatic):
- * tune[0] nodes per thread of y/z-line solves, tune[1] unused. */
+ * tune[0] nodes per thread of the non-persistent y/z-line kernels (8, 16 or
+ * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel. */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis, each >= 1; nx, ny >= 2 */
   double dx, dy, dz;         /* cell sizes [m], > 0 */
@@ -143,7 +144,8 @@ int fdtd_energy(fdtd_t* h, double out[2]);
 /* Number of steps taken. */
 int fdtd_steps_done(const fdtd_t* h, int64_t* n);
 
-/* Wait for the handle's stream. */
+/* Wait for the handle's stream.  Returns FDTD_ERR_TIMEOUT if a kernel's
+ * bounded wait gave up (the context stays usable). */
 int fdtd_synchronize(fdtd_t* h);
 
 /* Launch accounting and per-kernel timing.  Launch classes of the

@@ -10,7 +10,9 @@
 //
 // The hot loop is in line_kernels.cuh; this file holds validation, FP64
 // coefficient precompute, the scheme schedules (Sec. II) and the launches.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -50,6 +52,8 @@ struct PairCoef {
   double dh = 0;          // |d|/(2 d_eta)
   void* tab = nullptr;    // uniform media: [3][tlen] (1/beta, m, c) in T
   int tlen = 0;
+  int jc = 1 << 30;       // uniform media: table constant (in T) for jc <= j <= N-1
+  double ib_inf = 0, m_inf = 0, c_inf = 0;
   void* nkb = nullptr;    // per-node media (field layout, T)
   void* nib = nullptr;
 };
@@ -80,6 +84,13 @@ struct fdtd_s {
   void* scratch[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   PairGeom geom[2][3];
   StridedCfg strided_cfg[2];  // y lines, z lines
+  int num_sms = 0;
+  int* d_err = nullptr;       // set by kernels whose bounded waits gave up
+  bool use_tma = true;
+  // TMA descriptors of the y/z line tiles, per component and box kind
+  CUtensorMap tmap[6][2];
+  const void* tmap_ptr[6][2] = {{nullptr}};
+  int tmap_bn[6][2] = {{0}};
   ProcCoef proc[3];  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing)
   bool per_node = false;
   double eps_r = 1.0, mu_r = 1.0;          // uniform media
@@ -281,6 +292,23 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
         tab[c.tlen + j] = (j >= 1) ? off * ib[j - 1] : 0.0;
         tab[2 * c.tlen + j] = off * ib[j];
       }
+      // limit values: the entries at the last interior node; jc = first node
+      // from which every entry (rounded to the field precision) equals them
+      c.jc = 1 << 30;
+      if (N >= 2) {
+        const int last = N - 1;
+        c.ib_inf = tab[last];
+        c.m_inf = tab[c.tlen + last];
+        c.c_inf = tab[2 * c.tlen + last];
+        auto same = [&](double a, double b) {
+          return h->prec == FDTD_F64 ? a == b : (float)a == (float)b;
+        };
+        int jc = last;
+        while (jc >= 1 && same(tab[jc], c.ib_inf) && same(tab[2 * c.tlen + jc], c.c_inf) &&
+               same(tab[c.tlen + jc + 1], c.m_inf))
+          --jc;
+        c.jc = jc + 1;
+      }
       int rc = upload_any(h, &c.tab, tab);
       if (rc) return rc;
     } else {
@@ -374,6 +402,11 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.beta = (T)beta;
   p.tab = (const T*)c.tab;
   p.tlen = c.tlen;
+  p.jc = c.jc;
+  p.ib_inf = (T)c.ib_inf;
+  p.m_inf = (T)c.m_inf;
+  p.c_inf = (T)c.c_inf;
+  p.err = h->d_err;
   p.nkb = (const T*)c.nkb;
   p.nib = (const T*)c.nib;
   p.kb_sign = (T)(sgn * c.kb);
@@ -486,6 +519,89 @@ StridedCfg choose_strided(int N, bool pn, int tune_L) {
   return best;
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed y/z line solves (homogeneous media, lines of at most 256 cells)
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+constexpr int kTmaL = 16;  // nodes per thread of the TMA kernel
+
+int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 16 : 32; }
+
+bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
+  return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 && tensor_map_encoder() != nullptr;
+}
+
+// Tensor map of component c for tiles of LANES lines x BN nodes along y
+// (kind 0) or z (kind 1).  Re-encoded when the array moved.
+int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
+  if (h->tmap_ptr[c][kind] != h->f[c] || h->tmap_bn[c][kind] != BN) {
+    const int lanes = tma_lanes(h);
+    cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->ny + 1), (cuuint64_t)(h->nz + 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->esize, (cuuint64_t)h->plane * h->esize};
+    cuuint32_t box[3] = {(cuuint32_t)lanes, kind == 0 ? (cuuint32_t)BN : 1u, kind == 0 ? 1u : (cuuint32_t)BN};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = tensor_map_encoder()(&h->tmap[c][kind],
+                                      h->prec == FDTD_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                      3, h->f[c], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      fprintf(stderr, "fdtd: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
+      return FDTD_ERR_CUDA;
+    }
+    h->tmap_ptr[c][kind] = h->f[c];
+    h->tmap_bn[c][kind] = BN;
+  }
+  *out = &h->tmap[c][kind];
+  return FDTD_OK;
+}
+
+template <typename T>
+size_t tma_smem_bytes(int lanes, int BN, int P) {
+  return 4 * (size_t)BN * lanes * sizeof(T) + 4 * (size_t)P * lanes * sizeof(T) + 2 * sizeof(uint64_t);
+}
+
+template <typename T, int LANES>
+int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
+  const int BN = ((g.N + 7) / 8) * 8;
+  const int P = (g.N + kTmaL - 1) / kTmaL;
+  const int kind = g.axis == AX_Y ? 0 : 1;
+  const CUtensorMap *tE, *tH;
+  int rc = get_tmap(h, g.ec, kind, BN, &tE);
+  if (rc) return rc;
+  if ((rc = get_tmap(h, g.hc, kind, BN, &tH))) return rc;
+  fdtd::TmaTiles q;
+  q.BN = BN;
+  q.zbox = kind;
+  q.tiles_x = (g.lane_hi + LANES - 1) / LANES;
+  q.n_tiles = q.tiles_x * g.n_o;
+  const size_t smem = tma_smem_bytes<T>(LANES, BN, P);
+  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, kTmaL>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  const int grid = std::min(q.n_tiles, h->num_sms);
+  kern<<<grid, P * LANES, smem, h->stream>>>(*tE, *tH, p, q);
+  return FDTD_OK;
+}
+
 int take_event(fdtd_t* h, int* idx) {
   cudaEvent_t e;
   CK(cudaEventCreate(&e));
@@ -534,6 +650,12 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
       case 32: launch_rows_L<T, 32>(h, g, p, pn); break;
       default: return FDTD_ERR_UNSUPPORTED;
     }
+  } else if (tma_eligible(h, g) && p.e_in == p.e_out && p.e_in == (const T*)h->f[g.ec] &&
+             p.h_in == (const T*)h->f[g.hc]) {
+    int rc;
+    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 16>(h, g, p);
+    else rc = launch_strided_tma<T, 32>(h, g, p);
+    if (rc) return rc;
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];
     if (!cfg.ok) return FDTD_ERR_UNSUPPORTED;
@@ -771,6 +893,14 @@ int physical_to_scratch(fdtd_t* h) {
 
 int check_comp(int c) { return (c >= 0 && c < 6) ? FDTD_OK : FDTD_ERR_INVALID_ARG; }
 
+// Did a kernel's bounded wait give up?  (Synchronises the stream.)
+int check_device_flag(fdtd_t* h) {
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return v ? FDTD_ERR_TIMEOUT : FDTD_OK;
+}
+
 // f_E = -I / (A eps) at the source sample (A = the sample's dual-face area).
 int refresh_src_scale(fdtd_t* h) {
   if (h->src_comp < 0) {
@@ -956,6 +1086,18 @@ int fdtd_create(const fdtd_desc* desc, void* stream, fdtd_t** out) {
     h->bytes_per_launch[cls] = 4.0 * (double)d.nx * d.ny * d.nz * (double)h->esize;
   cudaError_t e = cudaMalloc(&h->d_stash, sizeof(double) * fdtd::kMaxProbes);
   if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
+  e = cudaMalloc(&h->d_err, sizeof(int));
+  if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
+  if (cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_CUDA; }
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      fdtd_destroy(h);
+      return FDTD_ERR_CUDA;
+    }
+  }
+  h->use_tma = (d.tune[1] & 1) == 0;
   int rc = build_all_coefs(h);
   if (rc) { fdtd_destroy(h); return rc; }
   *out = h;
@@ -975,6 +1117,7 @@ int fdtd_destroy(fdtd_t* h) {
   if (h->d_probe) cudaFree(h->d_probe);
   if (h->d_stash) cudaFree(h->d_stash);
   if (h->d_partial) cudaFree(h->d_partial);
+  if (h->d_err) cudaFree(h->d_err);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return FDTD_OK;
@@ -996,7 +1139,7 @@ int fdtd_synchronize(fdtd_t* h) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
   CK(cudaStreamSynchronize(h->stream));
-  return FDTD_OK;
+  return check_device_flag(h);
 }
 
 int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
@@ -1058,6 +1201,7 @@ int fdtd_set_field(fdtd_t* h, int comp, const void* data, int on_device) {
 int fdtd_get_field(fdtd_t* h, int comp, void* out, int on_device) {
   if (!h || !out || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
+  if (int rc0 = check_device_flag(h)) return rc0;
   if (h->scheme == FDTD_FLOD || h->scheme == FDTD_FSS || h->pending_init)
     return copy_component(h, comp, h->f[comp], out, on_device);
   int rc = physical_to_scratch(h);
@@ -1155,6 +1299,7 @@ int fdtd_get_probe(fdtd_t* h, int id, double* out, int64_t n) {
 int fdtd_energy(fdtd_t* h, double out[2]) {
   if (!h || !out) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
+  if (int rc0 = check_device_flag(h)) return rc0;
   int rc = scheme_init(h);
   if (rc) return rc;
   if ((rc = energy(h, h->f, &out[1]))) return rc;

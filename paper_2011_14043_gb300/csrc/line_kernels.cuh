@@ -11,26 +11,35 @@
 //
 // Line solve: the Thomas algorithm with factors precomputed in FP64 on the
 // host (Sec. IV's "precomputed bidiagonally factorized elements"):
-//   forward   y_j = r_j - m_j y_{j-1},       m_j = l_j / beta_{j-1}
+//   forward   y_j = r_j - m_j y_{j-1},           m_j = l_j / beta_{j-1}
 //   backward  w_j = y_j / beta_j - c_j w_{j+1},  c_j = u_j / beta_j
 // with 1/beta = 0 on wall nodes and beyond the line, which pins w = 0 there.
 // Both recurrences are first-order linear, so a line is cut into segments:
 // each thread runs the recurrences over its own segment from a zero carry,
 // the segment carries are chained (a scan of affine maps x -> a + p x), and
 // each thread adds carry * (product of its -m or -c) to its values.  This is
-// exactly the sequential Thomas result, reassociated; nothing is stored
-// outside registers and a few words of shared memory.
+// the sequential Thomas result, reassociated; nothing is stored outside
+// registers and a few words of shared memory.
 //
-// Two layouts:
-//   proc_strided_kernel  lines along y or z (stride pitch or plane).  LANES
-//                        consecutive x lines form a coalesced row access;
-//                        P = blockDim.x / LANES segments of L nodes each
-//                        split every line; carries go through shared memory.
-//   proc_rows_kernel     lines along x (contiguous).  One warp per line, lane
-//                        l owns nodes/faces [l L, l L + L) loaded as 16-byte
-//                        vectors; carries go through warp shuffles.
+// Coefficient sources (MODE): 0 = position tables of a homogeneous medium;
+// 1 = the same tables' limit values, used on segments where the table is
+// constant (the LU pivots of a constant-coefficient line converge
+// geometrically, so past the first few nodes every entry equals its limit
+// in working precision); 2 = per-node arrays of an inhomogeneous medium.
+//
+// Kernels:
+//   proc_strided_kernel      lines along y or z, data loaded straight from HBM.
+//   proc_strided_tma_kernel  the same lines, persistent: each block walks a
+//                            list of tiles (LANES lines x all nodes) with the
+//                            next tile's E and H streamed into shared memory
+//                            by TMA (cp.async.bulk.tensor) while the current
+//                            tile is solved, so HBM never waits on compute.
+//   proc_rows_kernel         lines along x (contiguous): one warp per line,
+//                            lane l owns nodes/faces [l L, l L + L) loaded as
+//                            16-byte vectors; carries go through shuffles.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,16 +63,178 @@ struct PairParams {
   T alpha, beta;         // E_out = alpha*w + beta*E_in
   const T* tab;          // uniform: [3][tlen] = 1/beta, m, c (zero beyond N and at walls)
   int tlen;
+  int jc;                // uniform: 1/beta_j, c_j equal their limits for jc <= j <= N-1
+  T ib_inf, m_inf, c_inf;
   const T* nkb;          // per-node: |b_j|/d_eta at each E node (field layout)
   const T* nib;          // per-node: 1/beta_j at each E node (field layout)
   T kb_sign;             // per-node: RHS coupling = kb_sign * nkb_j
   T dh;                  // per-node: off-diagonal o_j = -nkb_j * dh, dh = |d|/(2 d_eta)
   int src_i, src_o, src_o2, src_j;  // source node on this pair (-1: none)
   T src_rhs, src_post;   // added to r_j and to E_out at the source node
+  int* err;              // set to 1 when a bounded device wait gives up
 };
 
 // ---------------------------------------------------------------------------
-// Lines along y or z
+// Segment arithmetic shared by all kernels
+// ---------------------------------------------------------------------------
+template <typename T, int L, int MODE>
+__device__ __forceinline__ T coef_m(const PairParams<T>& p, int j0, int t, const T (&kbn)[L], const T (&ibn)[L],
+                                    T ib_prev) {
+  if constexpr (MODE == 0) return p.tab[p.tlen + j0 + t];
+  else if constexpr (MODE == 1) return p.m_inf;
+  else return -kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]);
+}
+template <typename T, int L, int MODE>
+__device__ __forceinline__ T coef_c(const PairParams<T>& p, int j0, int t, const T (&kbn)[L], const T (&ibn)[L]) {
+  if constexpr (MODE == 0) return p.tab[2 * p.tlen + j0 + t];
+  else if constexpr (MODE == 1) return p.c_inf;
+  else return -kbn[t] * p.dh * ibn[t];
+}
+template <typename T, int L, int MODE>
+__device__ __forceinline__ T coef_ib(const PairParams<T>& p, int j0, int t, const T (&ibn)[L]) {
+  if constexpr (MODE == 0) return p.tab[j0 + t];
+  else if constexpr (MODE == 1) return p.ib_inf;
+  else return ibn[t];
+}
+
+// RHS and local forward sweep from a zero carry; returns prod(-m).
+template <typename T, int L, int MODE>
+__device__ __forceinline__ T phase_forward(const PairParams<T>& p, int j0, const T (&E)[L], const T (&H)[L], T hm1,
+                                           const T (&kbn)[L], const T (&ibn)[L], T ib_prev, int src_t, T (&y)[L]) {
+  T pf = T(1), hprev = hm1;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T kb = (MODE == 2) ? p.kb_sign * kbn[t] : p.kb;
+    T r = E[t] + kb * (H[t] - hprev);
+    hprev = H[t];
+    if (t == src_t) r += p.src_rhs;
+    const T m = coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
+    y[t] = (t == 0) ? r : r - m * y[t - 1];
+    pf *= -m;
+  }
+  return pf;
+}
+
+// Forward carry fix-up, then the local backward sweep from a zero carry;
+// returns prod(-c).
+template <typename T, int L, int MODE>
+__device__ __forceinline__ T phase_backward(const PairParams<T>& p, int j0, T yin, const T (&kbn)[L],
+                                            const T (&ibn)[L], T ib_prev, T (&y)[L]) {
+  T q = T(1);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    q *= -coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
+    y[t] += q * yin;
+  }
+  T pb = T(1), wn = T(0);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    const T c = coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
+    y[t] = y[t] * coef_ib<T, L, MODE>(p, j0, t, ibn) - c * wn;
+    wn = y[t];
+    pb *= -c;
+  }
+  return pb;
+}
+
+// Backward carry fix-up: y becomes w.
+template <typename T, int L, int MODE>
+__device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win, const T (&kbn)[L],
+                                          const T (&ibn)[L], T (&y)[L]) {
+  T q = T(1);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    q *= -coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
+    y[t] += q * win;
+  }
+}
+
+// Carry chains across the P segments of LANES lines (shared memory).
+template <typename T, int LANES>
+__device__ __forceinline__ T block_chain_forward(T* sh, int P, int s, int lane, T a, T pm) {
+  sh[(0 * P + s) * LANES + lane] = a;
+  sh[(1 * P + s) * LANES + lane] = pm;
+  __syncthreads();
+  if (s == 0) {
+    T c = T(0);
+    for (int q = 0; q < P; ++q) {
+      c = sh[(0 * P + q) * LANES + lane] + sh[(1 * P + q) * LANES + lane] * c;
+      sh[(0 * P + q) * LANES + lane] = c;
+    }
+  }
+  __syncthreads();
+  return (s > 0) ? sh[(0 * P + s - 1) * LANES + lane] : T(0);
+}
+
+template <typename T, int LANES>
+__device__ __forceinline__ T block_chain_backward(T* sh, int P, int s, int lane, T b, T pm) {
+  sh[(2 * P + s) * LANES + lane] = b;
+  sh[(3 * P + s) * LANES + lane] = pm;
+  __syncthreads();
+  if (s == 0) {
+    T c = T(0);
+    for (int q = P - 1; q >= 0; --q) {
+      c = sh[(2 * P + q) * LANES + lane] + sh[(3 * P + q) * LANES + lane] * c;
+      sh[(2 * P + q) * LANES + lane] = c;
+    }
+  }
+  __syncthreads();
+  return (s + 1 < P) ? sh[(2 * P + s + 1) * LANES + lane] : T(0);
+}
+
+// The whole segment solve of a block of LANES lines.  MODE may differ
+// between warps; every barrier sits outside the MODE branches.
+template <typename T, int LANES, int L, bool PER_NODE>
+__device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
+                                              const T (&E)[L], const T (&H)[L], T hm1, const T (&kbn)[L],
+                                              const T (&ibn)[L], T ib_prev, int src_t, T (&y)[L], T& win) {
+  const bool conv = (j0 >= p.jc + 1) && (j0 + L <= p.N);
+  T pf, pb;
+  if constexpr (PER_NODE) {
+    pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+  } else {
+    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+  }
+  const T yin = block_chain_forward<T, LANES>(sh, P, s, lane, y[L - 1], pf);
+  if constexpr (PER_NODE) {
+    pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
+  } else {
+    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
+    else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
+  }
+  win = block_chain_backward<T, LANES>(sh, P, s, lane, y[0], pb);
+  if constexpr (PER_NODE) {
+    phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
+  } else {
+    if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
+    else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
+  }
+}
+
+// H update, subtraction and store of one strided segment.
+template <typename T, int L>
+__device__ __forceinline__ void strided_store(const PairParams<T>& p, long long base, int j0, int src_t,
+                                              const T (&E)[L], const T (&H)[L], const T (&y)[L], T win) {
+  T* pe = p.e_out + base;
+  T* ph = p.h_out + base;
+  const long long ls = p.ls;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const int j = j0 + t;
+    if (j < p.N) {
+      const T wnext = (t + 1 < L) ? y[t + 1] : win;
+      const T hn = H[t] + p.kd * (wnext - y[t]);
+      T en = p.alpha * y[t] + p.beta * E[t];
+      if (t == src_t) en += p.src_post;
+      pe[(long long)j * ls] = en;
+      ph[(long long)j * ls] = hn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lines along y or z, loads straight from HBM
 // ---------------------------------------------------------------------------
 template <typename T, int LANES, int L, bool PER_NODE>
 __global__ void proc_strided_kernel(const PairParams<T> p) {
@@ -80,17 +251,16 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
   const int N = p.N;
   const long long ls = p.ls;
   const bool src_line = (i == p.src_i) && (o == p.src_o);
+  const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
 
-  T E[L], H[L], y[L];
-  T kbn[L];
-  T ibn[L];
-  T ib_prev = T(0);
-  T hm1 = T(0);
+  T E[L], H[L], y[L], kbn[L], ibn[L];
+  T ib_prev = T(0), hm1 = T(0);
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     E[t] = T(0);
     H[t] = T(0);
-    if (PER_NODE) { kbn[t] = T(0); ibn[t] = T(0); }
+    kbn[t] = T(0);
+    ibn[t] = T(0);
   }
   if (active) {
     const T* pe = p.e_in + base;
@@ -101,7 +271,7 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
       if (j < N) {
         E[t] = pe[(long long)j * ls];
         H[t] = ph[(long long)j * ls];
-        if (PER_NODE) {
+        if constexpr (PER_NODE) {
           kbn[t] = p.nkb[base + (long long)j * ls];
           ibn[t] = p.nib[base + (long long)j * ls];
         }
@@ -109,108 +279,170 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
     }
     if (j0 > 0 && j0 - 1 < N) {
       hm1 = ph[(long long)(j0 - 1) * ls];
-      if (PER_NODE) ib_prev = p.nib[base + (long long)(j0 - 1) * ls];
+      if constexpr (PER_NODE) ib_prev = p.nib[base + (long long)(j0 - 1) * ls];
     }
+  }
+  T win;
+  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, ib_prev, src_t, y, win);
+  if (active) strided_store<T, L>(p, base, j0, src_t, E, H, y, win);
+}
+
+// ---------------------------------------------------------------------------
+// Lines along y or z, persistent, TMA-fed (homogeneous media)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for an mbarrier phase for at most limit_ns; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+struct TmaTiles {
+  int BN;        // nodes per box (>= N, a multiple of 8, <= 256)
+  int zbox;      // 0: box {LANES, BN, 1} (lines along y); 1: box {LANES, 1, BN} (along z)
+  int tiles_x;   // ceil(lane_hi / LANES)
+  int n_tiles;   // tiles_x * n_o
+};
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [4][P][LANES] + 2 mbarriers.
+// At most 256 nodes per line, so at most 256 / L segments of LANES threads.
+template <typename T, int LANES, int L>
+__global__ void __launch_bounds__(LANES * (256 / L), 1)
+    proc_strided_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
+                            const PairParams<T> p, const TmaTiles q) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x % LANES;
+  const int s = threadIdx.x / LANES;
+  const int P = blockDim.x / LANES;
+  const int stage_elems = q.BN * LANES;
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* sh = buf + 4 * stage_elems;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 4 * P * LANES);
+  const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
+  const int j0 = s * L;
+  const int N = p.N;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int tile, int stage) {
+    const int x0 = (tile % q.tiles_x) * LANES;
+    const int o = p.o_lo + tile / q.tiles_x;
+    T* dE = buf + (2 * stage + 0) * stage_elems;
+    T* dH = buf + (2 * stage + 1) * stage_elems;
+    mbar_arrive_expect_tx(&bars[stage], stage_bytes);
+    if (q.zbox) {
+      tma_load_3d(dE, &tmE, &bars[stage], x0, o, 0);
+      tma_load_3d(dH, &tmH, &bars[stage], x0, o, 0);
+    } else {
+      tma_load_3d(dE, &tmE, &bars[stage], x0, 0, o);
+      tma_load_3d(dH, &tmH, &bars[stage], x0, 0, o);
+    }
+  };
+  if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < q.n_tiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < q.n_tiles) issue(blockIdx.x + gridDim.x, 1);
   }
 
-  // coefficient accessors
-  auto m_of = [&](int t) -> T {
-    if (PER_NODE) return -kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]);
-    return p.tab[p.tlen + j0 + t];
-  };
-  auto c_of = [&](int t) -> T {
-    if (PER_NODE) return -kbn[t] * p.dh * ibn[t];
-    return p.tab[2 * p.tlen + j0 + t];
-  };
-  auto ib_of = [&](int t) -> T {
-    if (PER_NODE) return ibn[t];
-    return p.tab[j0 + t];
-  };
+  uint32_t parity0 = 0, parity1 = 0;
+  int k = 0;
+  for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
+    const int stage = k & 1;
+    const uint32_t par = stage ? parity1 : parity0;
+    if (!mbar_wait_bounded(&bars[stage], par, kWaitLimitNs)) {
+      // Give up: flag it, let the other stage's copy (if any) land, return.
+      if (threadIdx.x == 0) atomicExch(p.err, 1);
+      const int other = tile + (int)gridDim.x;
+      if (other < q.n_tiles) mbar_wait_bounded(&bars[stage ^ 1], stage ? parity0 : parity1, kWaitLimitNs);
+      return;
+    }
+    if (stage) parity1 ^= 1u;
+    else parity0 ^= 1u;
 
-  // right-hand side and local forward sweep (zero carry-in)
-  T pf = T(1);
-  {
-    T hprev = hm1;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const T kb = PER_NODE ? p.kb_sign * kbn[t] : p.kb;
-      T r = E[t] + kb * (H[t] - hprev);
-      hprev = H[t];
-      if (src_line && (j0 + t) == p.src_j) r += p.src_rhs;
-      const T m = m_of(t);
-      y[t] = (t == 0) ? r : r - m * y[t - 1];
-      pf *= -m;
-    }
-  }
-  sh[(0 * P + s) * LANES + lane] = y[L - 1];
-  sh[(1 * P + s) * LANES + lane] = pf;
-  __syncthreads();
-  if (s == 0) {
-    T c = T(0);
-    for (int q = 0; q < P; ++q) {
-      c = sh[(0 * P + q) * LANES + lane] + sh[(1 * P + q) * LANES + lane] * c;
-      sh[(0 * P + q) * LANES + lane] = c;
-    }
-  }
-  __syncthreads();
-  const T yin = (s > 0) ? sh[(0 * P + s - 1) * LANES + lane] : T(0);
-  {
-    T q = T(1);
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      q *= -m_of(t);
-      y[t] += q * yin;
-    }
-  }
-  // local backward sweep (zero carry-in from the right)
-  T pb = T(1);
-  {
-    T wn = T(0);
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-      const T c = c_of(t);
-      y[t] = y[t] * ib_of(t) - c * wn;
-      wn = y[t];
-      pb *= -c;
-    }
-  }
-  sh[(2 * P + s) * LANES + lane] = y[0];
-  sh[(3 * P + s) * LANES + lane] = pb;
-  __syncthreads();
-  if (s == 0) {
-    T c = T(0);
-    for (int q = P - 1; q >= 0; --q) {
-      c = sh[(2 * P + q) * LANES + lane] + sh[(3 * P + q) * LANES + lane] * c;
-      sh[(2 * P + q) * LANES + lane] = c;
-    }
-  }
-  __syncthreads();
-  const T win = (s + 1 < P) ? sh[(2 * P + s + 1) * LANES + lane] : T(0);
-  {
-    T q = T(1);
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-      q *= -c_of(t);
-      y[t] += q * win;
-    }
-  }
+    const int x0 = (tile % q.tiles_x) * LANES;
+    const int o = p.o_lo + tile / q.tiles_x;
+    const int i = x0 + lane;
+    const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
+    const long long base = (long long)o * p.os + i;
+    const bool src_line = (i == p.src_i) && (o == p.src_o);
+    const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
 
-  // explicit H update, subtraction, store
-  if (active) {
-    T* pe = p.e_out + base;
-    T* ph = p.h_out + base;
+    const T* sE = buf + (2 * stage + 0) * stage_elems;
+    const T* sH = buf + (2 * stage + 1) * stage_elems;
+    T E[L], H[L], y[L], kbn[L], ibn[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const int j = j0 + t;
-      if (j < N) {
-        const T wnext = (t + 1 < L) ? y[t + 1] : win;
-        const T hn = H[t] + p.kd * (wnext - y[t]);
-        T en = p.alpha * y[t] + p.beta * E[t];
-        if (src_line && j == p.src_j) en += p.src_post;
-        pe[(long long)j * ls] = en;
-        ph[(long long)j * ls] = hn;
+      const bool in = j < N;
+      E[t] = in ? sE[j * LANES + lane] : T(0);
+      H[t] = in ? sH[j * LANES + lane] : T(0);
+      kbn[t] = T(0);
+      ibn[t] = T(0);
+    }
+    const T hm1 = (j0 > 0 && j0 - 1 < N) ? sH[(j0 - 1) * LANES + lane] : T(0);
+    __syncthreads();  // this stage's buffer is free again
+    if (threadIdx.x == 0) {
+      const int next = tile + 2 * (int)gridDim.x;
+      if (next < q.n_tiles) {
+        fence_proxy_async_smem();
+        issue(next, stage);
       }
     }
+    T win;
+    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, T(0), src_t, y, win);
+    if (active) strided_store<T, L>(p, base, j0, src_t, E, H, y, win);
   }
 }
 
@@ -267,12 +499,11 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   const int j0 = lane * L;
   const int N = p.N;
   const bool src_line = (jo == p.src_o) && (ko == p.src_o2);
+  const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
 
   // Segments never run past the padded row (the row pitch is >= 32*L);
   // values at nodes/faces >= N are forced to zero.
-  T E[L], H[L], y[L];
-  T kbn[L];
-  T ibn[L];
+  T E[L], H[L], y[L], kbn[L], ibn[L];
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     E[t] = T(0);
@@ -300,39 +531,17 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
   if (lane == 0) hm1 = T(0);
   T ib_prev = T(0);
-  if (PER_NODE) {
+  if constexpr (PER_NODE) {
     ib_prev = __shfl_up_sync(FULL, ibn[L - 1], 1);
     if (lane == 0) ib_prev = T(0);
   }
-  const T* tab = p.tab;
-  auto m_of = [&](int t) -> T {
-    if (PER_NODE) return -kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]);
-    return tab[p.tlen + j0 + t];
-  };
-  auto c_of = [&](int t) -> T {
-    if (PER_NODE) return -kbn[t] * p.dh * ibn[t];
-    return tab[2 * p.tlen + j0 + t];
-  };
-  auto ib_of = [&](int t) -> T {
-    if (PER_NODE) return ibn[t];
-    return tab[j0 + t];
-  };
+  const bool conv = (j0 >= p.jc + 1) && (j0 + L <= N);
 
-  // RHS and local forward sweep
-  T pf = T(1);
-  {
-    T hprev = hm1;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const T kb = PER_NODE ? p.kb_sign * kbn[t] : p.kb;
-      T r = E[t] + kb * (H[t] - hprev);
-      hprev = H[t];
-      if (src_line && (j0 + t) == p.src_j) r += p.src_rhs;
-      const T m = m_of(t);
-      y[t] = (t == 0) ? r : r - m * y[t - 1];
-      pf *= -m;
-    }
-  }
+  T pf;
+  if constexpr (PER_NODE) pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+  else if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+  else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+
   // inclusive scan over lanes of x -> a + p x (Kogge-Stone)
   T a = y[L - 1], pp = pf;
 #pragma unroll
@@ -346,26 +555,12 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   }
   T yin = __shfl_up_sync(FULL, a, 1);
   if (lane == 0) yin = T(0);
-  {
-    T q = T(1);
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      q *= -m_of(t);
-      y[t] += q * yin;
-    }
-  }
-  // local backward sweep
-  T pb = T(1);
-  {
-    T wn = T(0);
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-      const T c = c_of(t);
-      y[t] = y[t] * ib_of(t) - c * wn;
-      wn = y[t];
-      pb *= -c;
-    }
-  }
+
+  T pb;
+  if constexpr (PER_NODE) pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
+  else if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
+  else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
+
   T b = y[0], qq = pb;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -378,21 +573,18 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   }
   T win = __shfl_down_sync(FULL, b, 1);
   if (lane == 31) win = T(0);
-  {
-    T q = T(1);
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-      q *= -c_of(t);
-      y[t] += q * win;
-    }
-  }
+
+  if constexpr (PER_NODE) phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
+  else if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
+  else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
+
   // H update, subtraction, store (values beyond N are exactly zero)
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const T wnext = (t + 1 < L) ? y[t + 1] : win;
     H[t] = H[t] + p.kd * (wnext - y[t]);
     T en = p.alpha * y[t] + p.beta * E[t];
-    if (src_line && (j0 + t) == p.src_j) en += p.src_post;
+    if (t == src_t) en += p.src_post;
     E[t] = en;
   }
   if (j0 + L <= N) {
