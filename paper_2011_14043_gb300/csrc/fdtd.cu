@@ -280,7 +280,8 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       const double off = -b * d / (2.0 * de * de);
       const double diag = 0.5 + b * d / (de * de);
       const int N = std::max(g.N, 1);
-      c.tlen = ((std::max(N + 64, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
+      // covers every segment a kernel may form: P*L <= N + 4L - 1 with L <= 32
+      c.tlen = ((std::max(N + 160, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
       std::vector<double> ib(c.tlen, 0.0), tab(3 * (size_t)c.tlen, 0.0);
       double beta = 0;
       for (int j = 1; j <= N - 1; ++j) {
@@ -435,9 +436,18 @@ void set_src(const fdtd_t* h, const PairGeom& g, fdtd::PairParams<T>& p, double 
   p.src_post = (T)post;
 }
 
+// segments per line for a block of LANES-wide segments: ceil(N / L) rounded
+// up so that the block is a whole number of warps (extra segments lie past
+// the line end and hold zeros)
+int segments(int N, int L, int lanes) {
+  const int P = (N + L - 1) / L;
+  const int m = 32 / lanes;
+  return ((P + m - 1) / m) * m;
+}
+
 template <typename T, int LANES, int L>
 void launch_strided_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, bool per_node) {
-  const int P = (g.N + L - 1) / L;
+  const int P = segments(g.N, L, LANES);
   dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
   const int threads = P * LANES;
   const size_t smem = 4 * (size_t)P * LANES * sizeof(T);
@@ -504,7 +514,7 @@ StridedCfg choose_strided(int N, bool pn, int tune_L) {
     for (int q = 0; q < 5; ++q) {
       const int lanes = cand[q][0], L = cand[q][1];
       if (pass == 0 && tune_L && L != tune_L) continue;
-      const int P = (N + L - 1) / L;
+      const int P = segments(N, L, lanes);
       const void* fn = strided_fn_rt<T>(pn, lanes, L);
       if (!fn) continue;
       cudaFuncAttributes a;
@@ -539,7 +549,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 constexpr int kTmaL = 16;  // nodes per thread of the TMA kernel
 
-int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 16 : 32; }
+int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 8 : ((h->desc.tune[1] & 2) ? 32 : 16); }
 
 bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
   return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 && tensor_map_encoder() != nullptr;
@@ -558,7 +568,7 @@ int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
                                       h->prec == FDTD_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                                       3, h->f[c], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       fprintf(stderr, "fdtd: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
@@ -576,10 +586,10 @@ size_t tma_smem_bytes(int lanes, int BN, int P) {
   return 4 * (size_t)BN * lanes * sizeof(T) + 4 * (size_t)P * lanes * sizeof(T) + 2 * sizeof(uint64_t);
 }
 
-template <typename T, int LANES>
+template <typename T, int LANES, int MINB>
 int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   const int BN = ((g.N + 7) / 8) * 8;
-  const int P = (g.N + kTmaL - 1) / kTmaL;
+  const int P = segments(g.N, kTmaL, LANES);
   const int kind = g.axis == AX_Y ? 0 : 1;
   const CUtensorMap *tE, *tH;
   int rc = get_tmap(h, g.ec, kind, BN, &tE);
@@ -591,13 +601,13 @@ int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& 
   q.tiles_x = (g.lane_hi + LANES - 1) / LANES;
   q.n_tiles = q.tiles_x * g.n_o;
   const size_t smem = tma_smem_bytes<T>(LANES, BN, P);
-  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, kTmaL>;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
+  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, kTmaL, MINB>;
+  static bool attr_set = false;  // one flag per instantiation
+  if (!attr_set) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set[sizeof(T) == 8] = true;
+    attr_set = true;
   }
-  const int grid = std::min(q.n_tiles, h->num_sms);
+  const int grid = std::min(q.n_tiles, MINB * h->num_sms);
   kern<<<grid, P * LANES, smem, h->stream>>>(*tE, *tH, p, q);
   return FDTD_OK;
 }
@@ -653,8 +663,9 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   } else if (tma_eligible(h, g) && p.e_in == p.e_out && p.e_in == (const T*)h->f[g.ec] &&
              p.h_in == (const T*)h->f[g.hc]) {
     int rc;
-    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 16>(h, g, p);
-    else rc = launch_strided_tma<T, 32>(h, g, p);
+    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 8, 2>(h, g, p);
+    else if (h->desc.tune[1] & 2) rc = launch_strided_tma<T, 32, 1>(h, g, p);
+    else rc = launch_strided_tma<T, 16, 2>(h, g, p);
     if (rc) return rc;
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];

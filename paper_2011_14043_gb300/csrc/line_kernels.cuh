@@ -149,37 +149,66 @@ __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win,
   }
 }
 
-// Carry chains across the P segments of LANES lines (shared memory).
+// Carry chains across the P segments of LANES lines.  Each chain is an
+// inclusive scan over segments of the affine maps x -> a_q + p_q x, one scan
+// per lane.  The (lane, segment) items are spread over groups of PW = 2^k >= P
+// consecutive threads so the scan runs as a Kogge-Stone on warp shuffles with
+// every thread of the block taking part (uniform trip count; the block size
+// is a multiple of 32).  reverse = true scans from the last segment.
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_forward(T* sh, int P, int s, int lane, T a, T pm) {
-  sh[(0 * P + s) * LANES + lane] = a;
-  sh[(1 * P + s) * LANES + lane] = pm;
-  __syncthreads();
-  if (s == 0) {
-    T c = T(0);
-    for (int q = 0; q < P; ++q) {
-      c = sh[(0 * P + q) * LANES + lane] + sh[(1 * P + q) * LANES + lane] * c;
-      sh[(0 * P + q) * LANES + lane] = c;
+__device__ __forceinline__ void chain_scan(T* sa, const T* sp, int P, int PW, bool reverse) {
+  const unsigned FULL = 0xffffffffu;
+  const int items = LANES * PW;
+  for (int first = 0; first < items; first += blockDim.x) {
+    const int it = first + (int)threadIdx.x;
+    const int lane = it / PW;
+    const int q = it % PW;
+    const bool valid = (it < items) && (q < P);
+    const int qq = reverse ? (P - 1 - q) : q;
+    T a = valid ? sa[qq * LANES + lane] : T(0);
+    T pm = valid ? sp[qq * LANES + lane] : T(1);
+    for (int d = 1; d < PW; d <<= 1) {
+      const T au = __shfl_up_sync(FULL, a, d, PW);
+      const T pu = __shfl_up_sync(FULL, pm, d, PW);
+      if (q >= d) {
+        a = a + pm * au;
+        pm = pm * pu;
+      }
     }
+    if (valid) sa[qq * LANES + lane] = a;
   }
-  __syncthreads();
-  return (s > 0) ? sh[(0 * P + s - 1) * LANES + lane] : T(0);
 }
 
+// Forward chain: returns y at the last node of segment s-1 (0 for s = 0).
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_backward(T* sh, int P, int s, int lane, T b, T pm) {
-  sh[(2 * P + s) * LANES + lane] = b;
-  sh[(3 * P + s) * LANES + lane] = pm;
+__device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, T pm) {
+  T* sa = sh;
+  T* sp = sh + P * LANES;
+  sa[s * LANES + lane] = a;
+  sp[s * LANES + lane] = pm;
   __syncthreads();
-  if (s == 0) {
-    T c = T(0);
-    for (int q = P - 1; q >= 0; --q) {
-      c = sh[(2 * P + q) * LANES + lane] + sh[(3 * P + q) * LANES + lane] * c;
-      sh[(2 * P + q) * LANES + lane] = c;
-    }
-  }
+  chain_scan<T, LANES>(sa, sp, P, PW, false);
   __syncthreads();
-  return (s + 1 < P) ? sh[(2 * P + s + 1) * LANES + lane] : T(0);
+  return (s > 0) ? sa[(s - 1) * LANES + lane] : T(0);
+}
+
+// Backward chain: returns w at the first node of segment s+1 (0 for the last).
+template <typename T, int LANES>
+__device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, T pm) {
+  T* sa = sh + 2 * P * LANES;
+  T* sp = sh + 3 * P * LANES;
+  sa[s * LANES + lane] = b;
+  sp[s * LANES + lane] = pm;
+  __syncthreads();
+  chain_scan<T, LANES>(sa, sp, P, PW, true);
+  __syncthreads();
+  return (s + 1 < P) ? sa[(s + 1) * LANES + lane] : T(0);
+}
+
+__device__ __forceinline__ int pow2_at_least(int P) {
+  int w = 1;
+  while (w < P) w <<= 1;
+  return w;
 }
 
 // The whole segment solve of a block of LANES lines.  MODE may differ
@@ -196,14 +225,15 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
     if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
     else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
   }
-  const T yin = block_chain_forward<T, LANES>(sh, P, s, lane, y[L - 1], pf);
+  const int PW = pow2_at_least(P);
+  const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf);
   if constexpr (PER_NODE) {
     pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
   } else {
     if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
     else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
   }
-  win = block_chain_backward<T, LANES>(sh, P, s, lane, y[0], pb);
+  win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb);
   if constexpr (PER_NODE) {
     phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
   } else {
@@ -353,9 +383,10 @@ struct TmaTiles {
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 // Dynamic shared memory: [2 stages][E, H][BN][LANES] + [4][P][LANES] + 2 mbarriers.
-// At most 256 nodes per line, so at most 256 / L segments of LANES threads.
-template <typename T, int LANES, int L>
-__global__ void __launch_bounds__(LANES * (256 / L), 1)
+// At most 256 nodes per line, so at most 256 / L segments of LANES threads;
+// MINB blocks share an SM so that one block's barriers overlap another's work.
+template <typename T, int LANES, int L, int MINB>
+__global__ void __launch_bounds__(LANES * (256 / L), MINB)
     proc_strided_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
                             const PairParams<T> p, const TmaTiles q) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
