@@ -50,10 +50,12 @@ struct PairGeom {
 struct PairCoef {
   double kb = 0, kd = 0;  // signed s*b/d_eta, s*d/d_eta
   double dh = 0;          // |d|/(2 d_eta)
-  void* tab = nullptr;    // uniform media: [3][tlen] (1/beta, m, c) in T
+  void* tab = nullptr;    // uniform media: [10][tlen] hi/lo rows (1/beta, m, c, PF, PB) in T
   int tlen = 0;
-  int jc = 1 << 30;       // uniform media: table constant (in T) for jc <= j <= N-1
-  double ib_inf = 0, m_inf = 0, c_inf = 0;
+  int L = 16;             // segment length the carry-product rows are built for
+  int jc = 1 << 30;       // uniform media: first converged segment start
+  double cv[6] = {0, 0, 0, 0, 0, 0};  // converged (hi, lo) of 1/beta, m, c
+  double qf[2][32] = {{0}}, qb[2][32] = {{0}};
   void* nkb = nullptr;    // per-node media (field layout, T)
   void* nib = nullptr;
 };
@@ -277,38 +279,77 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
     if (!h->per_node) {
       const double b = hh / (2.0 * kEps0 * h->eps_r);
       c.kb = g.sign * b / de;
-      const double off = -b * d / (2.0 * de * de);
-      const double diag = 0.5 + b * d / (de * de);
+      // Factor the system the kernel actually applies: with FP32 couplings
+      // kb, kd the line operator is 1/2 - (kb kd / 2) (second difference), so
+      // form b d / d_eta^2 from the rounded couplings.  The procedure is then
+      // an exact Cayley transform of a (1e-8-perturbed) skew operator and
+      // keeps its energy invariant instead of drifting.
+      double bd = b * d / (de * de);
+      if (h->prec == FDTD_F32) {
+        c.kb = (double)(float)c.kb;
+        c.kd = (double)(float)c.kd;
+        bd = c.kb * c.kd;
+      }
+      const double off = -bd / 2.0;
+      const double diag = 0.5 + bd;
       const int N = std::max(g.N, 1);
+      const int L = g.rows ? std::max(1, pick_rows_L(N)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
+      c.L = L;
       // covers every segment a kernel may form: P*L <= N + 4L - 1 with L <= 32
       c.tlen = ((std::max(N + 160, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
-      std::vector<double> ib(c.tlen, 0.0), tab(3 * (size_t)c.tlen, 0.0);
-      double beta = 0;
+      const int tl = c.tlen;
+      std::vector<double> ib(tl, 0.0), m(tl, 0.0), cc(tl, 0.0), pf(tl, 0.0), pb(tl, 0.0);
       for (int j = 1; j <= N - 1; ++j) {
-        beta = (j == 1) ? diag : diag - off * off * ib[j - 1];
+        const double beta = (j == 1) ? diag : diag - off * off * ib[j - 1];
         ib[j] = 1.0 / beta;
       }
-      for (int j = 0; j < c.tlen; ++j) {
-        tab[j] = ib[j];
-        tab[c.tlen + j] = (j >= 1) ? off * ib[j - 1] : 0.0;
-        tab[2 * c.tlen + j] = off * ib[j];
+      for (int j = 0; j < tl; ++j) {
+        m[j] = (j >= 1) ? off * ib[j - 1] : 0.0;
+        cc[j] = off * ib[j];
       }
-      // limit values: the entries at the last interior node; jc = first node
-      // from which every entry (rounded to the field precision) equals them
+      // carry products within each segment [s L, s L + L)
+      for (int j0 = 0; j0 + L <= tl; j0 += L) {
+        double q = 1.0;
+        for (int t = 0; t < L; ++t) { q *= -m[j0 + t]; pf[j0 + t] = q; }
+        q = 1.0;
+        for (int t = L - 1; t >= 0; --t) { q *= -cc[j0 + t]; pb[j0 + t] = q; }
+      }
+      const bool f32 = h->prec == FDTD_F32;
+      auto hi = [&](double x) { return f32 ? (double)(float)x : x; };
+      auto lo = [&](double x) { return f32 ? (double)(float)(x - (double)(float)x) : 0.0; };
+      std::vector<double> tab((size_t)10 * tl, 0.0);
+      const std::vector<double>* rows[5] = {&ib, &m, &cc, &pf, &pb};
+      for (int r = 0; r < 5; ++r)
+        for (int j = 0; j < tl; ++j) {
+          tab[(size_t)(2 * r) * tl + j] = hi((*rows[r])[j]);
+          tab[(size_t)(2 * r + 1) * tl + j] = lo((*rows[r])[j]);
+        }
+      // converged constants: the entries of the last full segment inside the
+      // line; jc = first segment start from which every full segment's
+      // entries (hi and lo) equal them
       c.jc = 1 << 30;
-      if (N >= 2) {
-        const int last = N - 1;
-        c.ib_inf = tab[last];
-        c.m_inf = tab[c.tlen + last];
-        c.c_inf = tab[2 * c.tlen + last];
-        auto same = [&](double a, double b) {
-          return h->prec == FDTD_F64 ? a == b : (float)a == (float)b;
+      const int last_seg = ((N) / L - 1) * L;  // start of the last segment with j0 + L <= N
+      if (N >= 2 && last_seg >= 0) {
+        const int jr = last_seg + L - 1;
+        const double cvv[3] = {ib[jr], m[jr], cc[jr]};
+        for (int k = 0; k < 3; ++k) { c.cv[2 * k] = hi(cvv[k]); c.cv[2 * k + 1] = lo(cvv[k]); }
+        for (int t = 0; t < L; ++t) {
+          c.qf[0][t] = hi(pf[last_seg + t]); c.qf[1][t] = lo(pf[last_seg + t]);
+          c.qb[0][t] = hi(pb[last_seg + t]); c.qb[1][t] = lo(pb[last_seg + t]);
+        }
+        auto seg_ok = [&](int j0) {
+          for (int t = 0; t < L; ++t) {
+            const int j = j0 + t;
+            if (hi(ib[j]) != c.cv[0] || lo(ib[j]) != c.cv[1] || hi(m[j]) != c.cv[2] || lo(m[j]) != c.cv[3] ||
+                hi(cc[j]) != c.cv[4] || lo(cc[j]) != c.cv[5] || hi(pf[j]) != c.qf[0][t] || lo(pf[j]) != c.qf[1][t] ||
+                hi(pb[j]) != c.qb[0][t] || lo(pb[j]) != c.qb[1][t])
+              return false;
+          }
+          return true;
         };
-        int jc = last;
-        while (jc >= 1 && same(tab[jc], c.ib_inf) && same(tab[2 * c.tlen + jc], c.c_inf) &&
-               same(tab[c.tlen + jc + 1], c.m_inf))
-          --jc;
-        c.jc = jc + 1;
+        int jc = last_seg;
+        while (jc - L >= 0 && seg_ok(jc - L)) jc -= L;
+        c.jc = seg_ok(last_seg) ? jc : (1 << 30);
       }
       int rc = upload_any(h, &c.tab, tab);
       if (rc) return rc;
@@ -404,9 +445,13 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.tab = (const T*)c.tab;
   p.tlen = c.tlen;
   p.jc = c.jc;
-  p.ib_inf = (T)c.ib_inf;
-  p.m_inf = (T)c.m_inf;
-  p.c_inf = (T)c.c_inf;
+  for (int k = 0; k < 6; ++k) p.cv[k] = (T)c.cv[k];
+  for (int t = 0; t < 32; ++t) {
+    p.qf[0][t] = (T)c.qf[0][t];
+    p.qf[1][t] = (T)c.qf[1][t];
+    p.qb[0][t] = (T)c.qb[0][t];
+    p.qb[1][t] = (T)c.qb[1][t];
+  }
   p.err = h->d_err;
   p.nkb = (const T*)c.nkb;
   p.nib = (const T*)c.nib;
@@ -450,7 +495,7 @@ void launch_strided_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams
   const int P = segments(g.N, L, LANES);
   dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
   const int threads = P * LANES;
-  const size_t smem = 4 * (size_t)P * LANES * sizeof(T);
+  const size_t smem = 6 * (size_t)P * LANES * sizeof(T);
   if (per_node)
     fdtd::proc_strided_kernel<T, LANES, L, true><<<grid, threads, smem, h->stream>>>(p);
   else
@@ -552,7 +597,9 @@ constexpr int kTmaL = 16;  // nodes per thread of the TMA kernel
 int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 8 : ((h->desc.tune[1] & 2) ? 32 : 16); }
 
 bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
-  return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 && tensor_map_encoder() != nullptr;
+  // the coefficient tables' carry products are built for the strided L
+  return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 &&
+         h->strided_cfg[g.axis == AX_Y ? 0 : 1].L == kTmaL && tensor_map_encoder() != nullptr;
 }
 
 // Tensor map of component c for tiles of LANES lines x BN nodes along y
@@ -583,7 +630,7 @@ int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
 
 template <typename T>
 size_t tma_smem_bytes(int lanes, int BN, int P) {
-  return 4 * (size_t)BN * lanes * sizeof(T) + 4 * (size_t)P * lanes * sizeof(T) + 2 * sizeof(uint64_t);
+  return 4 * (size_t)BN * lanes * sizeof(T) + 6 * (size_t)P * lanes * sizeof(T) + 2 * sizeof(uint64_t);
 }
 
 template <typename T, int LANES, int MINB>

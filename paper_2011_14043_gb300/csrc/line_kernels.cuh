@@ -25,7 +25,8 @@
 // 1 = the same tables' limit values, used on segments where the table is
 // constant (the LU pivots of a constant-coefficient line converge
 // geometrically, so past the first few nodes every entry equals its limit
-// in working precision); 2 = per-node arrays of an inhomogeneous medium.
+// in working precision): kernel-parameter constants, no loads; 2 = per-node
+// arrays of an inhomogeneous medium.
 //
 // Kernels:
 //   proc_strided_kernel      lines along y or z, data loaded straight from HBM.
@@ -61,10 +62,14 @@ struct PairParams {
   T kb;                  // uniform: RHS coupling s*b/d_eta
   T kd;                  // H update coupling s*d/d_eta
   T alpha, beta;         // E_out = alpha*w + beta*E_in
-  const T* tab;          // uniform: [3][tlen] = 1/beta, m, c (zero beyond N and at walls)
+  const T* tab;          // uniform: [TB_ROWS][tlen] hi/lo rows of 1/beta, m, c and the
+                         // segment carry products PF, PB (zero beyond N and at walls)
   int tlen;
-  int jc;                // uniform: 1/beta_j, c_j equal their limits for jc <= j <= N-1
-  T ib_inf, m_inf, c_inf;
+  int jc;                // uniform: segments starting at j0 >= jc and ending by N are
+                         // "converged": their coefficients are the constants below
+  T cv[6];               // converged 1/beta, m, c as (hi, lo) pairs
+  T qf[2][32];           // converged PF_t = (-m)^(t+1), hi and lo
+  T qb[2][32];           // converged PB_t = (-c)^(L-t), hi and lo
   const T* nkb;          // per-node: |b_j|/d_eta at each E node (field layout)
   const T* nib;          // per-node: 1/beta_j at each E node (field layout)
   T kb_sign;             // per-node: RHS coupling = kb_sign * nkb_j
@@ -77,75 +82,141 @@ struct PairParams {
 // ---------------------------------------------------------------------------
 // Segment arithmetic shared by all kernels
 // ---------------------------------------------------------------------------
-template <typename T, int L, int MODE>
-__device__ __forceinline__ T coef_m(const PairParams<T>& p, int j0, int t, const T (&kbn)[L], const T (&ibn)[L],
-                                    T ib_prev) {
-  if constexpr (MODE == 0) return p.tab[p.tlen + j0 + t];
-  else if constexpr (MODE == 1) return p.m_inf;
-  else return -kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]);
-}
-template <typename T, int L, int MODE>
-__device__ __forceinline__ T coef_c(const PairParams<T>& p, int j0, int t, const T (&kbn)[L], const T (&ibn)[L]) {
-  if constexpr (MODE == 0) return p.tab[2 * p.tlen + j0 + t];
-  else if constexpr (MODE == 1) return p.c_inf;
-  else return -kbn[t] * p.dh * ibn[t];
-}
-template <typename T, int L, int MODE>
-__device__ __forceinline__ T coef_ib(const PairParams<T>& p, int j0, int t, const T (&ibn)[L]) {
-  if constexpr (MODE == 0) return p.tab[j0 + t];
-  else if constexpr (MODE == 1) return p.ib_inf;
-  else return ibn[t];
+// FP32 fields apply every FP64-formed coefficient as a pair hi + lo of FP32
+// numbers (hi = the FP64 value rounded, lo = the rounded remainder): the
+// solve then inverts the FP64-factored matrix to about 2^-48 instead of a
+// matrix perturbed by the rounding of its pivots.  Rounded pivots perturb
+// the diagonal of (1/2 I - h/4 O) identically at every step, which makes a
+// procedure slightly non-unitary and the field energy drift steadily; with
+// hi + lo the remaining error is the ordinary FP32 rounding of the fields.
+// FP64 fields use the coefficients as they are (lo terms compile away).
+template <typename T>
+struct HiLo {
+  T hi, lo;
+};
+
+template <typename T>
+__device__ __forceinline__ constexpr bool use_hilo() {
+  return sizeof(T) == 4;
 }
 
-// RHS and local forward sweep from a zero carry; returns prod(-m).
+// a * x + b with a = hi + lo
+template <typename T>
+__device__ __forceinline__ T fma2(HiLo<T> a, T x, T b) {
+  if constexpr (use_hilo<T>()) return fma(a.hi, x, fma(a.lo, x, b));
+  else return fma(a.hi, x, b);
+}
+
+// Table rows of a homogeneous medium, each [tlen] long.
+enum { TB_IBH = 0, TB_IBL, TB_MH, TB_ML, TB_CH, TB_CL, TB_PFH, TB_PFL, TB_PBH, TB_PBL, TB_ROWS };
+
+template <typename T, int MODE>
+__device__ __forceinline__ HiLo<T> tab2(const PairParams<T>& p, int row, int j, int t, const T* cv_hi,
+                                        const T* cv_lo) {
+  if constexpr (MODE == 0) return {p.tab[row * p.tlen + j], p.tab[(row + 1) * p.tlen + j]};
+  else return {cv_hi[t], cv_lo[t]};
+}
+
+// Forward multiplier m, backward coupling c, pivot 1/beta of node j0 + t.
 template <typename T, int L, int MODE>
-__device__ __forceinline__ T phase_forward(const PairParams<T>& p, int j0, const T (&E)[L], const T (&H)[L], T hm1,
-                                           const T (&kbn)[L], const T (&ibn)[L], T ib_prev, int src_t, T (&y)[L]) {
+__device__ __forceinline__ HiLo<T> coef_m(const PairParams<T>& p, int j0, int t, const T (&kbn)[L],
+                                          const T (&ibn)[L], T ib_prev) {
+  if constexpr (MODE == 0) return {p.tab[TB_MH * p.tlen + j0 + t], p.tab[TB_ML * p.tlen + j0 + t]};
+  else if constexpr (MODE == 1) return {p.cv[2], p.cv[3]};
+  else return {-kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]), T(0)};
+}
+template <typename T, int L, int MODE>
+__device__ __forceinline__ HiLo<T> coef_c(const PairParams<T>& p, int j0, int t, const T (&kbn)[L],
+                                          const T (&ibn)[L]) {
+  if constexpr (MODE == 0) return {p.tab[TB_CH * p.tlen + j0 + t], p.tab[TB_CL * p.tlen + j0 + t]};
+  else if constexpr (MODE == 1) return {p.cv[4], p.cv[5]};
+  else return {-kbn[t] * p.dh * ibn[t], T(0)};
+}
+template <typename T, int L, int MODE>
+__device__ __forceinline__ HiLo<T> coef_ib(const PairParams<T>& p, int j0, int t, const T (&ibn)[L]) {
+  if constexpr (MODE == 0) return {p.tab[TB_IBH * p.tlen + j0 + t], p.tab[TB_IBL * p.tlen + j0 + t]};
+  else if constexpr (MODE == 1) return {p.cv[0], p.cv[1]};
+  else return {ibn[t], T(0)};
+}
+// Carry products within the segment: PF_t = prod_{u<=t} (-m_u), PB_t = prod_{u>=t} (-c_u).
+template <typename T, int MODE>
+__device__ __forceinline__ HiLo<T> coef_pf(const PairParams<T>& p, int j0, int t) {
+  if constexpr (MODE == 0) return {p.tab[TB_PFH * p.tlen + j0 + t], p.tab[TB_PFL * p.tlen + j0 + t]};
+  else return {p.qf[0][t], p.qf[1][t]};
+}
+template <typename T, int MODE>
+__device__ __forceinline__ HiLo<T> coef_pb(const PairParams<T>& p, int j0, int t) {
+  if constexpr (MODE == 0) return {p.tab[TB_PBH * p.tlen + j0 + t], p.tab[TB_PBL * p.tlen + j0 + t]};
+  else return {p.qb[0][t], p.qb[1][t]};
+}
+
+// RHS and local forward sweep from a zero carry; returns the segment's carry
+// coefficient prod(-m).
+template <typename T, int L, int MODE>
+__device__ __forceinline__ HiLo<T> phase_forward(const PairParams<T>& p, int j0, const T (&E)[L], const T (&H)[L],
+                                                 T hm1, const T (&kbn)[L], const T (&ibn)[L], T ib_prev,
+                                                 int src_t, T (&y)[L]) {
   T pf = T(1), hprev = hm1;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const T kb = (MODE == 2) ? p.kb_sign * kbn[t] : p.kb;
-    T r = E[t] + kb * (H[t] - hprev);
+    T r = fma(kb, H[t] - hprev, E[t]);
     hprev = H[t];
     if (t == src_t) r += p.src_rhs;
-    const T m = coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
-    y[t] = (t == 0) ? r : r - m * y[t - 1];
-    pf *= -m;
+    const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
+    y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
+    if constexpr (MODE == 2) pf *= -m.hi;
   }
-  return pf;
+  if constexpr (MODE == 2) return {pf, T(0)};
+  else return coef_pf<T, MODE>(p, j0, L - 1);
 }
 
 // Forward carry fix-up, then the local backward sweep from a zero carry;
-// returns prod(-c).
+// returns the segment's carry coefficient prod(-c).
 template <typename T, int L, int MODE>
-__device__ __forceinline__ T phase_backward(const PairParams<T>& p, int j0, T yin, const T (&kbn)[L],
-                                            const T (&ibn)[L], T ib_prev, T (&y)[L]) {
-  T q = T(1);
+__device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0, T yin, const T (&kbn)[L],
+                                                  const T (&ibn)[L], T ib_prev, T (&y)[L]) {
+  if constexpr (MODE == 2) {
+    T q = T(1);
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    q *= -coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
-    y[t] += q * yin;
+    for (int t = 0; t < L; ++t) {
+      q *= -coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev).hi;
+      y[t] = fma(q, yin, y[t]);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) y[t] = fma2(coef_pf<T, MODE>(p, j0, t), yin, y[t]);
   }
   T pb = T(1), wn = T(0);
 #pragma unroll
   for (int t = L - 1; t >= 0; --t) {
-    const T c = coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
-    y[t] = y[t] * coef_ib<T, L, MODE>(p, j0, t, ibn) - c * wn;
+    const HiLo<T> c = coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
+    const HiLo<T> ib = coef_ib<T, L, MODE>(p, j0, t, ibn);
+    T u;
+    if constexpr (use_hilo<T>() && MODE != 2) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
+    else u = -c.hi * wn;
+    y[t] = fma(y[t], ib.hi, u);
     wn = y[t];
-    pb *= -c;
+    if constexpr (MODE == 2) pb *= -c.hi;
   }
-  return pb;
+  if constexpr (MODE == 2) return {pb, T(0)};
+  else return coef_pb<T, MODE>(p, j0, 0);
 }
 
 // Backward carry fix-up: y becomes w.
 template <typename T, int L, int MODE>
 __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win, const T (&kbn)[L],
                                           const T (&ibn)[L], T (&y)[L]) {
-  T q = T(1);
+  if constexpr (MODE == 2) {
+    T q = T(1);
 #pragma unroll
-  for (int t = L - 1; t >= 0; --t) {
-    q *= -coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
-    y[t] += q * win;
+    for (int t = L - 1; t >= 0; --t) {
+      q *= -coef_c<T, L, MODE>(p, j0, t, kbn, ibn).hi;
+      y[t] = fma(q, win, y[t]);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) y[t] = fma2(coef_pb<T, MODE>(p, j0, t), win, y[t]);
   }
 }
 
@@ -154,9 +225,12 @@ __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win,
 // per lane.  The (lane, segment) items are spread over groups of PW = 2^k >= P
 // consecutive threads so the scan runs as a Kogge-Stone on warp shuffles with
 // every thread of the block taking part (uniform trip count; the block size
-// is a multiple of 32).  reverse = true scans from the last segment.
+// is a multiple of 32).  reverse = true scans from the last segment.  The
+// first combine (a neighbour's carry) uses p as hi + lo; longer-range
+// products are FP32 (their weight is already below prod(-m)^2 over a
+// segment, far under the rounding of the result).
 template <typename T, int LANES>
-__device__ __forceinline__ void chain_scan(T* sa, const T* sp, int P, int PW, bool reverse) {
+__device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, int P, int PW, bool reverse) {
   const unsigned FULL = 0xffffffffu;
   const int items = LANES * PW;
   for (int first = 0; first < items; first += blockDim.x) {
@@ -166,13 +240,14 @@ __device__ __forceinline__ void chain_scan(T* sa, const T* sp, int P, int PW, bo
     const bool valid = (it < items) && (q < P);
     const int qq = reverse ? (P - 1 - q) : q;
     T a = valid ? sa[qq * LANES + lane] : T(0);
-    T pm = valid ? sp[qq * LANES + lane] : T(1);
+    T ph = valid ? sph[qq * LANES + lane] : T(1);
+    const T pl = valid ? spl[qq * LANES + lane] : T(0);
     for (int d = 1; d < PW; d <<= 1) {
       const T au = __shfl_up_sync(FULL, a, d, PW);
-      const T pu = __shfl_up_sync(FULL, pm, d, PW);
+      const T pu = __shfl_up_sync(FULL, ph, d, PW);
       if (q >= d) {
-        a = a + pm * au;
-        pm = pm * pu;
+        a = (d == 1) ? fma2(HiLo<T>{ph, pl}, au, a) : fma(ph, au, a);
+        ph = ph * pu;
       }
     }
     if (valid) sa[qq * LANES + lane] = a;
@@ -180,27 +255,32 @@ __device__ __forceinline__ void chain_scan(T* sa, const T* sp, int P, int PW, bo
 }
 
 // Forward chain: returns y at the last node of segment s-1 (0 for s = 0).
+// sh holds [6][P][LANES]: forward a, p_hi, p_lo, backward a, p_hi, p_lo.
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, T pm) {
+__device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, HiLo<T> pm) {
   T* sa = sh;
-  T* sp = sh + P * LANES;
+  T* sph = sh + P * LANES;
+  T* spl = sh + 2 * P * LANES;
   sa[s * LANES + lane] = a;
-  sp[s * LANES + lane] = pm;
+  sph[s * LANES + lane] = pm.hi;
+  spl[s * LANES + lane] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sp, P, PW, false);
+  chain_scan<T, LANES>(sa, sph, spl, P, PW, false);
   __syncthreads();
   return (s > 0) ? sa[(s - 1) * LANES + lane] : T(0);
 }
 
 // Backward chain: returns w at the first node of segment s+1 (0 for the last).
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, T pm) {
-  T* sa = sh + 2 * P * LANES;
-  T* sp = sh + 3 * P * LANES;
+__device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, HiLo<T> pm) {
+  T* sa = sh + 3 * P * LANES;
+  T* sph = sh + 4 * P * LANES;
+  T* spl = sh + 5 * P * LANES;
   sa[s * LANES + lane] = b;
-  sp[s * LANES + lane] = pm;
+  sph[s * LANES + lane] = pm.hi;
+  spl[s * LANES + lane] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sp, P, PW, true);
+  chain_scan<T, LANES>(sa, sph, spl, P, PW, true);
   __syncthreads();
   return (s + 1 < P) ? sa[(s + 1) * LANES + lane] : T(0);
 }
@@ -217,8 +297,8 @@ template <typename T, int LANES, int L, bool PER_NODE>
 __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
                                               const T (&E)[L], const T (&H)[L], T hm1, const T (&kbn)[L],
                                               const T (&ibn)[L], T ib_prev, int src_t, T (&y)[L], T& win) {
-  const bool conv = (j0 >= p.jc + 1) && (j0 + L <= p.N);
-  T pf, pb;
+  const bool conv = (j0 >= p.jc) && (j0 + L <= p.N);
+  HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
     pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
   } else {
@@ -269,7 +349,7 @@ __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long 
 template <typename T, int LANES, int L, bool PER_NODE>
 __global__ void proc_strided_kernel(const PairParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sh = reinterpret_cast<T*>(smem_raw);  // [4][P][LANES]
+  T* sh = reinterpret_cast<T*>(smem_raw);  // [6][P][LANES]
   const int lane = threadIdx.x % LANES;
   const int s = threadIdx.x / LANES;
   const int P = blockDim.x / LANES;
@@ -382,7 +462,7 @@ struct TmaTiles {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
-// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [4][P][LANES] + 2 mbarriers.
+// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [6][P][LANES] + 2 mbarriers.
 // At most 256 nodes per line, so at most 256 / L segments of LANES threads;
 // MINB blocks share an SM so that one block's barriers overlap another's work.
 template <typename T, int LANES, int L, int MINB>
@@ -396,7 +476,7 @@ __global__ void __launch_bounds__(LANES * (256 / L), MINB)
   const int stage_elems = q.BN * LANES;
   T* buf = reinterpret_cast<T*>(smem_raw);
   T* sh = buf + 4 * stage_elems;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 4 * P * LANES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 6 * P * LANES);
   const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
   const int j0 = s * L;
   const int N = p.N;
@@ -517,13 +597,13 @@ __device__ __forceinline__ void store_seg(T* dst, const T (&v)[L]) {
   }
 }
 
+// One x line (a warp): solve and store.  E, H (and per-node kbn, ibn) hold
+// the line's segment of this lane, zero past the line end.
 template <typename T, int L, bool PER_NODE>
-__global__ void proc_rows_kernel(const PairParams<T> p) {
+__device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
+                                                const T (&kbn)[L], const T (&ibn)[L]) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
   const int jo = p.o_lo + (int)(line % p.n_o);
   const int ko = p.o2_lo + (int)(line / p.n_o);
   const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
@@ -531,34 +611,8 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   const int N = p.N;
   const bool src_line = (jo == p.src_o) && (ko == p.src_o2);
   const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
+  T y[L];
 
-  // Segments never run past the padded row (the row pitch is >= 32*L);
-  // values at nodes/faces >= N are forced to zero.
-  T E[L], H[L], y[L], kbn[L], ibn[L];
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    E[t] = T(0);
-    H[t] = T(0);
-    kbn[t] = T(0);
-    ibn[t] = T(0);
-  }
-  if (j0 < N) {  // lanes wholly past the line end touch no memory
-    load_seg<T, L>(p.e_in + base + j0, E);
-    load_seg<T, L>(p.h_in + base + j0, H);
-    if constexpr (PER_NODE) {
-      load_seg<T, L>(p.nkb + base + j0, kbn);
-      load_seg<T, L>(p.nib + base + j0, ibn);
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    if (j0 + t >= N) {
-      E[t] = T(0);
-      H[t] = T(0);
-      kbn[t] = T(0);
-      ibn[t] = T(0);
-    }
-  }
   T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
   if (lane == 0) hm1 = T(0);
   T ib_prev = T(0);
@@ -566,39 +620,40 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
     ib_prev = __shfl_up_sync(FULL, ibn[L - 1], 1);
     if (lane == 0) ib_prev = T(0);
   }
-  const bool conv = (j0 >= p.jc + 1) && (j0 + L <= N);
+  const bool conv = (j0 >= p.jc) && (j0 + L <= N);
 
-  T pf;
+  HiLo<T> pf;
   if constexpr (PER_NODE) pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
   else if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
   else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
 
-  // inclusive scan over lanes of x -> a + p x (Kogge-Stone)
-  T a = y[L - 1], pp = pf;
+  // inclusive scan over lanes of x -> a + p x (Kogge-Stone); the first
+  // combine uses the neighbour's coefficient as hi + lo
+  T a = y[L - 1], pp = pf.hi;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const T a_up = __shfl_up_sync(FULL, a, d);
     const T p_up = __shfl_up_sync(FULL, pp, d);
     if (lane >= d) {
-      a = a + pp * a_up;
+      a = (d == 1) ? fma2(HiLo<T>{pp, pf.lo}, a_up, a) : fma(pp, a_up, a);
       pp = pp * p_up;
     }
   }
   T yin = __shfl_up_sync(FULL, a, 1);
   if (lane == 0) yin = T(0);
 
-  T pb;
+  HiLo<T> pb;
   if constexpr (PER_NODE) pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
   else if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
   else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
 
-  T b = y[0], qq = pb;
+  T b = y[0], qq = pb.hi;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const T b_dn = __shfl_down_sync(FULL, b, d);
     const T q_dn = __shfl_down_sync(FULL, qq, d);
     if (lane + d < 32) {
-      b = b + qq * b_dn;
+      b = (d == 1) ? fma2(HiLo<T>{qq, pb.lo}, b_dn, b) : fma(qq, b_dn, b);
       qq = qq * q_dn;
     }
   }
@@ -630,6 +685,52 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
       }
     }
   }
+}
+
+// Load this lane's segment of x line `line` (zeros past the line end).
+// Segments never run past the padded row (the row pitch is >= 32*L).
+template <typename T, int L, bool PER_NODE>
+__device__ __forceinline__ void row_load(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
+                                         T (&kbn)[L], T (&ibn)[L]) {
+  const int lane = threadIdx.x & 31;
+  const int jo = p.o_lo + (int)(line % p.n_o);
+  const int ko = p.o2_lo + (int)(line / p.n_o);
+  const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const int j0 = lane * L;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = T(0);
+    H[t] = T(0);
+    kbn[t] = T(0);
+    ibn[t] = T(0);
+  }
+  if (j0 < p.N) {  // lanes wholly past the line end touch no memory
+    load_seg<T, L>(p.e_in + base + j0, E);
+    load_seg<T, L>(p.h_in + base + j0, H);
+    if constexpr (PER_NODE) {
+      load_seg<T, L>(p.nkb + base + j0, kbn);
+      load_seg<T, L>(p.nib + base + j0, ibn);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    if (j0 + t >= p.N) {
+      E[t] = T(0);
+      H[t] = T(0);
+      kbn[t] = T(0);
+      ibn[t] = T(0);
+    }
+  }
+}
+
+// One warp per x line.
+template <typename T, int L, bool PER_NODE>
+__global__ void proc_rows_kernel(const PairParams<T> p) {
+  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
+  T E[L], H[L], kbn[L], ibn[L];
+  row_load<T, L, PER_NODE>(p, line, E, H, kbn, ibn);
+  row_solve_store<T, L, PER_NODE>(p, line, E, H, kbn, ibn);
 }
 
 }  // namespace fdtd

@@ -1,0 +1,74 @@
+"""Full-size parity: cavity-mode workloads at their real sizes and step counts
+against the exact closed-form modal evolution of the oracle (oracle/modal.py,
+pinned to the stepper in test_oracle_modal.py), element by element.
+
+Also checks the exactly conserved FADI invariant W(v) at full size."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import grid as G
+from oracle import modal as M
+
+from gpu_helpers import energy_norm_rel, per_comp_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-4}
+
+
+def report(name, **kw):
+    print(f"\nFULLSIZE {name} " + json.dumps(kw))
+
+
+def run_cavity(n, steps, prec, cfl=4.0, seed=2, scheme="fadi"):
+    from paper_2011_14043_gb300 import Simulation
+    d = 1e-3
+    g = G.Grid(n, n, n, d, d, d)
+    dt = cfl * g.dt_cfl()
+    modes = W.random_modes(seed, n, n, n, d, d, d, count=8)
+    u0 = W.mode_sum_fields(modes, n, n, n)
+    sim = Simulation(n, n, n, d, scheme=scheme, precision=prec, dt=dt)
+    sim.set_fields(u0)
+    e_init = sim.energy()            # (physical, state invariant) after initialization
+    sim.step(steps)
+    e_end = sim.energy()
+    out = {c: sim.get_field(c) for c in G.COMPS}
+    sim.close()
+    ref = M.field_after(g, dt, scheme, modes, steps)
+    return out, ref, e_init, e_end
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_cavity_128_fadi_1000_steps(prec):
+    """Workload 2: 128^3 PEC cavity, 1 mm, CFL 4, 8 seeded modes, 1000 FADI steps."""
+    out, ref, e0, e1 = run_cavity(128, 1000, prec)
+    err = energy_norm_rel(out, ref)
+    drift = abs(e1[1] / e0[1] - 1.0)
+    report(f"cavity128_fadi_{prec}", rel_err=err, invariant_drift=drift,
+           per_comp=per_comp_rel(out, ref))
+    assert err <= TOL[prec]
+    assert drift <= (1e-12 if prec == "f64" else 1e-4)
+
+
+def test_cavity_256_fadi_1000_steps_f32():
+    """The benchmark workload: 256^3, 1000 FADI steps in FP32 vs the exact field."""
+    out, ref, e0, e1 = run_cavity(256, 1000, "f32")
+    err = energy_norm_rel(out, ref)
+    drift = abs(e1[1] / e0[1] - 1.0)
+    report("cavity256_fadi_f32", rel_err=err, invariant_drift=drift, per_comp=per_comp_rel(out, ref))
+    assert err <= TOL["f32"]
+    assert drift <= 1e-4
+
+
+@pytest.mark.parametrize("scheme", ["flod", "fss"])
+def test_cavity_128_flod_fss_f32(scheme):
+    out, ref, e0, e1 = run_cavity(128, 300, "f32", cfl=8.0, scheme=scheme)
+    err = energy_norm_rel(out, ref)
+    drift = abs(e1[0] / e0[0] - 1.0)
+    report(f"cavity128_{scheme}_f32", rel_err=err, energy_drift=drift)
+    assert err <= TOL["f32"]
+    assert drift <= 1e-4
