@@ -211,6 +211,15 @@ int pick_rows_L(int N) {
   return -1;
 }
 
+// segments per line for a block of LANES-wide segments: ceil(N / L) rounded
+// up so that the block is a whole number of warps (extra segments lie past
+// the line end and hold zeros)
+int segments(int N, int L, int lanes) {
+  const int P = (N + L - 1) / L;
+  const int m = 32 / lanes;
+  return ((P + m - 1) / m) * m;
+}
+
 double spacing(const fdtd_t* h, int axis) { return axis == AX_X ? h->dx : (axis == AX_Y ? h->dy : h->dz); }
 
 template <typename T>
@@ -457,37 +466,8 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.nib = (const T*)c.nib;
   p.kb_sign = (T)(sgn * c.kb);
   p.dh = (T)c.dh;
-  p.src_i = p.src_o = p.src_o2 = p.src_j = -1;
-  p.src_rhs = T(0);
-  p.src_post = T(0);
   (void)h;
   return p;
-}
-
-// Place a point value at sample (i, j, k) of component comp on the pair's
-// line coordinates, if that component is the pair's E component.
-template <typename T>
-void set_src(const fdtd_t* h, const PairGeom& g, fdtd::PairParams<T>& p, double rhs, double post) {
-  if (h->src_comp != g.ec) return;
-  const int si = h->src_i, sj = h->src_j, sk = h->src_k;
-  if (g.axis == AX_X) {
-    p.src_o = sj; p.src_o2 = sk; p.src_j = si;
-  } else if (g.axis == AX_Y) {
-    p.src_i = si; p.src_o = sk; p.src_j = sj;
-  } else {
-    p.src_i = si; p.src_o = sj; p.src_j = sk;
-  }
-  p.src_rhs = (T)rhs;
-  p.src_post = (T)post;
-}
-
-// segments per line for a block of LANES-wide segments: ceil(N / L) rounded
-// up so that the block is a whole number of warps (extra segments lie past
-// the line end and hold zeros)
-int segments(int N, int L, int lanes) {
-  const int P = (N + L - 1) / L;
-  const int m = 32 / lanes;
-  return ((P + m - 1) / m) * m;
 }
 
 template <typename T, int LANES, int L>
@@ -495,7 +475,7 @@ void launch_strided_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams
   const int P = segments(g.N, L, LANES);
   dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
   const int threads = P * LANES;
-  const size_t smem = 6 * (size_t)P * LANES * sizeof(T);
+  const size_t smem = 6 * (size_t)(P | 1) * LANES * sizeof(T);
   if (per_node)
     fdtd::proc_strided_kernel<T, LANES, L, true><<<grid, threads, smem, h->stream>>>(p);
   else
@@ -527,6 +507,7 @@ const void* strided_fn_rt(bool pn, int lanes, int L) {
   if (lanes == 32 && L == 8) return strided_fn<T, 32, 8>(pn);
   if (lanes == 32 && L == 16) return strided_fn<T, 32, 16>(pn);
   if (lanes == 32 && L == 32) return strided_fn<T, 32, 32>(pn);
+  if (lanes == 16 && L == 17) return strided_fn<T, 16, 17>(pn);
   if (lanes == 16 && L == 8) return strided_fn<T, 16, 8>(pn);
   if (lanes == 16 && L == 16) return strided_fn<T, 16, 16>(pn);
   if (lanes == 16 && L == 32) return strided_fn<T, 16, 32>(pn);
@@ -540,6 +521,7 @@ void launch_strided(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T
   if (lanes == 32 && L == 8) launch_strided_L<T, 32, 8>(h, g, p, pn);
   else if (lanes == 32 && L == 16) launch_strided_L<T, 32, 16>(h, g, p, pn);
   else if (lanes == 32 && L == 32) launch_strided_L<T, 32, 32>(h, g, p, pn);
+  else if (lanes == 16 && L == 17) launch_strided_L<T, 16, 17>(h, g, p, pn);
   else if (lanes == 16 && L == 8) launch_strided_L<T, 16, 8>(h, g, p, pn);
   else if (lanes == 16 && L == 16) launch_strided_L<T, 16, 16>(h, g, p, pn);
   else if (lanes == 16 && L == 32) launch_strided_L<T, 16, 32>(h, g, p, pn);
@@ -551,12 +533,12 @@ template <typename T>
 StridedCfg choose_strided(int N, bool pn, int tune_L) {
   // preference order: widest rows first (coalescing), then the L that keeps
   // registers low enough for two or more resident blocks.
-  static const int cand32[][2] = {{32, 16}, {32, 8}, {32, 32}, {16, 32}, {8, 32}};
-  static const int cand64[][2] = {{16, 16}, {16, 8}, {16, 32}, {8, 16}, {8, 32}};
+  static const int cand32[][2] = {{32, 16}, {32, 8}, {32, 32}, {16, 32}, {8, 32}, {8, 32}};
+  static const int cand64[][2] = {{16, 16}, {16, 8}, {16, 32}, {8, 16}, {8, 32}, {8, 32}};
   const int(*cand)[2] = sizeof(T) == 8 ? cand64 : cand32;
   StridedCfg best;
   for (int pass = 0; pass < 2; ++pass) {
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
       const int lanes = cand[q][0], L = cand[q][1];
       if (pass == 0 && tune_L && L != tune_L) continue;
       const int P = segments(N, L, lanes);
@@ -592,14 +574,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-constexpr int kTmaL = 16;  // nodes per thread of the TMA kernel
+// nodes per thread of the TMA kernel (the coefficient tables' carry
+// products are built for the strided L, which must match)
+template <typename T>
+constexpr int tma_L() { return 16; }
+int tma_L_rt(const fdtd_t*) { return 16; }
 
-int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 8 : ((h->desc.tune[1] & 2) ? 32 : 16); }
+int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 8 : 16; }
 
 bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
   // the coefficient tables' carry products are built for the strided L
   return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 &&
-         h->strided_cfg[g.axis == AX_Y ? 0 : 1].L == kTmaL && tensor_map_encoder() != nullptr;
+         h->strided_cfg[g.axis == AX_Y ? 0 : 1].L == tma_L_rt(h) && tensor_map_encoder() != nullptr;
 }
 
 // Tensor map of component c for tiles of LANES lines x BN nodes along y
@@ -630,13 +616,14 @@ int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
 
 template <typename T>
 size_t tma_smem_bytes(int lanes, int BN, int P) {
-  return 4 * (size_t)BN * lanes * sizeof(T) + 6 * (size_t)P * lanes * sizeof(T) + 2 * sizeof(uint64_t);
+  return 4 * (size_t)BN * lanes * sizeof(T) + 6 * (size_t)(P | 1) * lanes * sizeof(T) + 2 * sizeof(uint64_t);
 }
 
 template <typename T, int LANES, int MINB>
 int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
+  constexpr int L = tma_L<T>();
   const int BN = ((g.N + 7) / 8) * 8;
-  const int P = segments(g.N, kTmaL, LANES);
+  const int P = segments(g.N, L, LANES);
   const int kind = g.axis == AX_Y ? 0 : 1;
   const CUtensorMap *tE, *tH;
   int rc = get_tmap(h, g.ec, kind, BN, &tE);
@@ -648,7 +635,7 @@ int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& 
   q.tiles_x = (g.lane_hi + LANES - 1) / LANES;
   q.n_tiles = q.tiles_x * g.n_o;
   const size_t smem = tma_smem_bytes<T>(LANES, BN, P);
-  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, kTmaL, MINB>;
+  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, L, MINB>;
   static bool attr_set = false;  // one flag per instantiation
   if (!attr_set) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -711,7 +698,6 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
              p.h_in == (const T*)h->f[g.hc]) {
     int rc;
     if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 8, 2>(h, g, p);
-    else if (h->desc.tune[1] & 2) rc = launch_strided_tma<T, 32, 1>(h, g, p);
     else rc = launch_strided_tma<T, 16, 2>(h, g, p);
     if (rc) return rc;
   } else {
@@ -734,33 +720,57 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
 
 // One updating procedure.  sgn = -1 runs the inverse procedure (length -h),
 // whose tridiagonal matrices are the same and whose couplings flip sign.
-// rhs_src / post_src: values at the source sample (E component only).
 template <typename T>
 int run_procedure(fdtd_t* h, int slot, double sgn, double alpha, double beta, double kd_mul,
-                  void* const* in, void* const* out, double rhs_src, double post_src) {
+                  void* const* in, void* const* out) {
   const ProcCoef& P = h->proc[slot];
   for (int q = 0; q < 3; ++q) {
     const PairGeom& g = h->geom[P.op][q];
     fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], sgn, alpha, beta, kd_mul, in, out);
-    if (rhs_src != 0.0 || post_src != 0.0) set_src<T>(h, g, p, rhs_src, post_src);
     int rc = launch_pair<T>(h, g, p);
     if (rc) return rc;
   }
   return FDTD_OK;
 }
 
-// The forward procedure: E <- w - E, H <- H + kd dw, in place.
+long long elem_index(const fdtd_t* h, int i, int j, int k) {
+  return (long long)k * h->plane + (long long)j * h->pitch + i;
+}
+
+// value added to one sample of an array (a point source)
+int add_point(fdtd_t* h, void* arr, double value) {
+  if (value == 0.0 || h->src_comp < 0) return FDTD_OK;
+  const long long at = elem_index(h, h->src_i, h->src_j, h->src_k);
+  h->launches++;
+  if (h->prec == FDTD_F64)
+    fdtd::add_point_kernel<double><<<1, 32, 0, h->stream>>>((double*)arr, at, value);
+  else
+    fdtd::add_point_kernel<float><<<1, 32, 0, h->stream>>>((float*)arr, at, value);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+// The forward procedure, in place: E <- w - E, H <- H + kd dw.  A point
+// source enters as rhs_src added to the implicit right-hand side (applied by
+// adding it to E before the solve and once more to the new E, since the new
+// E subtracts the E the solve saw) and post_src added to the new E.
 int procedure(fdtd_t* h, int slot, double rhs_src, double post_src) {
-  return h->prec == FDTD_F64
-             ? run_procedure<double>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f, rhs_src, post_src)
-             : run_procedure<float>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f, rhs_src, post_src);
+  int rc;
+  if (h->src_comp >= 0 && rhs_src != 0.0) {
+    if ((rc = add_point(h, h->f[h->src_comp], rhs_src))) return rc;
+  }
+  rc = h->prec == FDTD_F64 ? run_procedure<double>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f)
+                           : run_procedure<float>(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f);
+  if (rc) return rc;
+  if (h->src_comp >= 0 && (rhs_src != 0.0 || post_src != 0.0))
+    return add_point(h, h->f[h->src_comp], rhs_src + post_src);
+  return FDTD_OK;
 }
 
 int procedure_ex(fdtd_t* h, int slot, double sgn, double alpha, double beta, double kd_mul,
-                 void* const* in, void* const* out, double rhs_src) {
-  return h->prec == FDTD_F64
-             ? run_procedure<double>(h, slot, sgn, alpha, beta, kd_mul, in, out, rhs_src, 0.0)
-             : run_procedure<float>(h, slot, sgn, alpha, beta, kd_mul, in, out, rhs_src, 0.0);
+                 void* const* in, void* const* out) {
+  return h->prec == FDTD_F64 ? run_procedure<double>(h, slot, sgn, alpha, beta, kd_mul, in, out)
+                             : run_procedure<float>(h, slot, sgn, alpha, beta, kd_mul, in, out);
 }
 
 int ensure_scratch(fdtd_t* h) {
@@ -786,10 +796,6 @@ double source_value(const fdtd_t* h, long long n) {
   // f_E at the source sample for step n: -I(t_n + dt/2)/(A eps)
   if (h->src_comp < 0 || n < 0 || n >= (long long)h->src_current.size()) return 0.0;
   return h->src_scale * h->src_current[(size_t)n];
-}
-
-long long elem_index(const fdtd_t* h, int i, int j, int k) {
-  return (long long)k * h->plane + (long long)j * h->pitch + i;
 }
 
 // FADI input initialization (Eq. 10 with Eqs. 7, 8a): v^0 = (I + dt/2 B) u^0
@@ -937,11 +943,12 @@ int physical_to_scratch(fdtd_t* h) {
       // the B pairs' line systems with the couplings of a procedure of length
       // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
       const double fp = source_value(h, h->steps);
-      rc = procedure_ex(h, 1, -1.0, 0.5, 0.0, 0.5, h->f, h->scratch, -0.5 * h->dt * fp);
+      if ((rc = add_point(h, h->scratch[h->src_comp < 0 ? 0 : h->src_comp], -0.5 * h->dt * fp))) return rc;
+      rc = procedure_ex(h, 1, -1.0, 0.5, 0.0, 0.5, h->scratch, h->scratch);
       if (rc) return rc;
     } else if (h->scheme == FDTD_FLOD2) {
       // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4}, u^{n+1} = v - u^{n+5/4}
-      rc = procedure_ex(h, 2, -1.0, 1.0, -1.0, 1.0, h->f, h->scratch, 0.0);
+      rc = procedure_ex(h, 2, -1.0, 1.0, -1.0, 1.0, h->scratch, h->scratch);
       if (rc) return rc;
     }
   }

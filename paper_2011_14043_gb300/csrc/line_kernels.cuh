@@ -74,8 +74,6 @@ struct PairParams {
   const T* nib;          // per-node: 1/beta_j at each E node (field layout)
   T kb_sign;             // per-node: RHS coupling = kb_sign * nkb_j
   T dh;                  // per-node: off-diagonal o_j = -nkb_j * dh, dh = |d|/(2 d_eta)
-  int src_i, src_o, src_o2, src_j;  // source node on this pair (-1: none)
-  T src_rhs, src_post;   // added to r_j and to E_out at the source node
   int* err;              // set to 1 when a bounded device wait gives up
 };
 
@@ -155,14 +153,13 @@ __device__ __forceinline__ HiLo<T> coef_pb(const PairParams<T>& p, int j0, int t
 template <typename T, int L, int MODE>
 __device__ __forceinline__ HiLo<T> phase_forward(const PairParams<T>& p, int j0, const T (&E)[L], const T (&H)[L],
                                                  T hm1, const T (&kbn)[L], const T (&ibn)[L], T ib_prev,
-                                                 int src_t, T (&y)[L]) {
+                                                 T (&y)[L]) {
   T pf = T(1), hprev = hm1;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const T kb = (MODE == 2) ? p.kb_sign * kbn[t] : p.kb;
-    T r = fma(kb, H[t] - hprev, E[t]);
+    const T r = fma(kb, H[t] - hprev, E[t]);
     hprev = H[t];
-    if (t == src_t) r += p.src_rhs;
     const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
     y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
     if constexpr (MODE == 2) pf *= -m.hi;
@@ -230,7 +227,7 @@ __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win,
 // products are FP32 (their weight is already below prod(-m)^2 over a
 // segment, far under the rounding of the result).
 template <typename T, int LANES>
-__device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, int P, int PW, bool reverse) {
+__device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, int P, int PS, int PW, bool reverse) {
   const unsigned FULL = 0xffffffffu;
   const int items = LANES * PW;
   for (int first = 0; first < items; first += blockDim.x) {
@@ -239,9 +236,10 @@ __device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, in
     const int q = it % PW;
     const bool valid = (it < items) && (q < P);
     const int qq = reverse ? (P - 1 - q) : q;
-    T a = valid ? sa[qq * LANES + lane] : T(0);
-    T ph = valid ? sph[qq * LANES + lane] : T(1);
-    const T pl = valid ? spl[qq * LANES + lane] : T(0);
+    const int at = lane * PS + qq;
+    T a = valid ? sa[at] : T(0);
+    T ph = valid ? sph[at] : T(1);
+    const T pl = valid ? spl[at] : T(0);
     for (int d = 1; d < PW; d <<= 1) {
       const T au = __shfl_up_sync(FULL, a, d, PW);
       const T pu = __shfl_up_sync(FULL, ph, d, PW);
@@ -250,39 +248,45 @@ __device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, in
         ph = ph * pu;
       }
     }
-    if (valid) sa[qq * LANES + lane] = a;
+    if (valid) sa[at] = a;
   }
 }
 
+// Chain buffers: [6][LANES][PS], PS = P rounded up to odd so that both the
+// per-segment writes (lanes across a warp) and the scan reads (segments
+// across a warp) are free of bank conflicts.
+__device__ __forceinline__ int chain_stride(int P) { return P | 1; }
+
 // Forward chain: returns y at the last node of segment s-1 (0 for s = 0).
-// sh holds [6][P][LANES]: forward a, p_hi, p_lo, backward a, p_hi, p_lo.
 template <typename T, int LANES>
 __device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, HiLo<T> pm) {
+  const int PS = chain_stride(P);
   T* sa = sh;
-  T* sph = sh + P * LANES;
-  T* spl = sh + 2 * P * LANES;
-  sa[s * LANES + lane] = a;
-  sph[s * LANES + lane] = pm.hi;
-  spl[s * LANES + lane] = pm.lo;
+  T* sph = sh + PS * LANES;
+  T* spl = sh + 2 * PS * LANES;
+  sa[lane * PS + s] = a;
+  sph[lane * PS + s] = pm.hi;
+  spl[lane * PS + s] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sph, spl, P, PW, false);
+  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, false);
   __syncthreads();
-  return (s > 0) ? sa[(s - 1) * LANES + lane] : T(0);
+  return (s > 0) ? sa[lane * PS + s - 1] : T(0);
 }
 
 // Backward chain: returns w at the first node of segment s+1 (0 for the last).
 template <typename T, int LANES>
 __device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, HiLo<T> pm) {
-  T* sa = sh + 3 * P * LANES;
-  T* sph = sh + 4 * P * LANES;
-  T* spl = sh + 5 * P * LANES;
-  sa[s * LANES + lane] = b;
-  sph[s * LANES + lane] = pm.hi;
-  spl[s * LANES + lane] = pm.lo;
+  const int PS = chain_stride(P);
+  T* sa = sh + 3 * PS * LANES;
+  T* sph = sh + 4 * PS * LANES;
+  T* spl = sh + 5 * PS * LANES;
+  sa[lane * PS + s] = b;
+  sph[lane * PS + s] = pm.hi;
+  spl[lane * PS + s] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sph, spl, P, PW, true);
+  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, true);
   __syncthreads();
-  return (s + 1 < P) ? sa[(s + 1) * LANES + lane] : T(0);
+  return (s + 1 < P) ? sa[lane * PS + s + 1] : T(0);
 }
 
 __device__ __forceinline__ int pow2_at_least(int P) {
@@ -296,14 +300,14 @@ __device__ __forceinline__ int pow2_at_least(int P) {
 template <typename T, int LANES, int L, bool PER_NODE>
 __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
                                               const T (&E)[L], const T (&H)[L], T hm1, const T (&kbn)[L],
-                                              const T (&ibn)[L], T ib_prev, int src_t, T (&y)[L], T& win) {
+                                              const T (&ibn)[L], T ib_prev, T (&y)[L], T& win) {
   const bool conv = (j0 >= p.jc) && (j0 + L <= p.N);
   HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
-    pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+    pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
   } else {
-    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
-    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
+    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
   }
   const int PW = pow2_at_least(P);
   const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf);
@@ -324,21 +328,26 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
 
 // H update, subtraction and store of one strided segment.
 template <typename T, int L>
-__device__ __forceinline__ void strided_store(const PairParams<T>& p, long long base, int j0, int src_t,
-                                              const T (&E)[L], const T (&H)[L], const T (&y)[L], T win) {
-  T* pe = p.e_out + base;
-  T* ph = p.h_out + base;
+__device__ __forceinline__ void strided_store(const PairParams<T>& p, long long base, int j0, const T (&E)[L],
+                                              const T (&H)[L], const T (&y)[L], T win) {
+  T* pe = p.e_out + base + (long long)j0 * p.ls;
+  T* ph = p.h_out + base + (long long)j0 * p.ls;
   const long long ls = p.ls;
+  if (j0 + L <= p.N) {
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const int j = j0 + t;
-    if (j < p.N) {
+    for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
-      const T hn = H[t] + p.kd * (wnext - y[t]);
-      T en = p.alpha * y[t] + p.beta * E[t];
-      if (t == src_t) en += p.src_post;
-      pe[(long long)j * ls] = en;
-      ph[(long long)j * ls] = hn;
+      pe[t * ls] = fma(p.alpha, y[t], p.beta * E[t]);
+      ph[t * ls] = fma(p.kd, wnext - y[t], H[t]);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t < p.N) {
+        const T wnext = (t + 1 < L) ? y[t + 1] : win;
+        pe[t * ls] = fma(p.alpha, y[t], p.beta * E[t]);
+        ph[t * ls] = fma(p.kd, wnext - y[t], H[t]);
+      }
     }
   }
 }
@@ -349,7 +358,7 @@ __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long 
 template <typename T, int LANES, int L, bool PER_NODE>
 __global__ void proc_strided_kernel(const PairParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sh = reinterpret_cast<T*>(smem_raw);  // [6][P][LANES]
+  T* sh = reinterpret_cast<T*>(smem_raw);  // [6][LANES][P|1]
   const int lane = threadIdx.x % LANES;
   const int s = threadIdx.x / LANES;
   const int P = blockDim.x / LANES;
@@ -360,8 +369,6 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
   const int j0 = s * L;
   const int N = p.N;
   const long long ls = p.ls;
-  const bool src_line = (i == p.src_i) && (o == p.src_o);
-  const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
 
   T E[L], H[L], y[L], kbn[L], ibn[L];
   T ib_prev = T(0), hm1 = T(0);
@@ -393,8 +400,8 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
     }
   }
   T win;
-  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, ib_prev, src_t, y, win);
-  if (active) strided_store<T, L>(p, base, j0, src_t, E, H, y, win);
+  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, ib_prev, y, win);
+  if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,11 +469,11 @@ struct TmaTiles {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
-// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [6][P][LANES] + 2 mbarriers.
-// At most 256 nodes per line, so at most 256 / L segments of LANES threads;
+// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [6][LANES][P|1] + 2 mbarriers.
+// At most 256 nodes per line, so at most ceil(256 / L) segments of LANES threads;
 // MINB blocks share an SM so that one block's barriers overlap another's work.
 template <typename T, int LANES, int L, int MINB>
-__global__ void __launch_bounds__(LANES * (256 / L), MINB)
+__global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     proc_strided_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
                             const PairParams<T> p, const TmaTiles q) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(LANES * (256 / L), MINB)
   const int stage_elems = q.BN * LANES;
   T* buf = reinterpret_cast<T*>(smem_raw);
   T* sh = buf + 4 * stage_elems;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 6 * P * LANES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 6 * chain_stride(P) * LANES);
   const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
   const int j0 = s * L;
   const int N = p.N;
@@ -527,20 +534,28 @@ __global__ void __launch_bounds__(LANES * (256 / L), MINB)
     const int i = x0 + lane;
     const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
     const long long base = (long long)o * p.os + i;
-    const bool src_line = (i == p.src_i) && (o == p.src_o);
-    const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
 
     const T* sE = buf + (2 * stage + 0) * stage_elems;
     const T* sH = buf + (2 * stage + 1) * stage_elems;
     T E[L], H[L], y[L], kbn[L], ibn[L];
+    if (j0 + L <= N) {
 #pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const int j = j0 + t;
-      const bool in = j < N;
-      E[t] = in ? sE[j * LANES + lane] : T(0);
-      H[t] = in ? sH[j * LANES + lane] : T(0);
-      kbn[t] = T(0);
-      ibn[t] = T(0);
+      for (int t = 0; t < L; ++t) {
+        E[t] = sE[(j0 + t) * LANES + lane];
+        H[t] = sH[(j0 + t) * LANES + lane];
+        kbn[t] = T(0);
+        ibn[t] = T(0);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        const int j = j0 + t;
+        const bool in = j < N;
+        E[t] = in ? sE[j * LANES + lane] : T(0);
+        H[t] = in ? sH[j * LANES + lane] : T(0);
+        kbn[t] = T(0);
+        ibn[t] = T(0);
+      }
     }
     const T hm1 = (j0 > 0 && j0 - 1 < N) ? sH[(j0 - 1) * LANES + lane] : T(0);
     __syncthreads();  // this stage's buffer is free again
@@ -552,8 +567,8 @@ __global__ void __launch_bounds__(LANES * (256 / L), MINB)
       }
     }
     T win;
-    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, T(0), src_t, y, win);
-    if (active) strided_store<T, L>(p, base, j0, src_t, E, H, y, win);
+    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, T(0), y, win);
+    if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
   }
 }
 
@@ -597,6 +612,44 @@ __device__ __forceinline__ void store_seg(T* dst, const T (&v)[L]) {
   }
 }
 
+// Segment carry chain across the 32 lanes of a warp (x lines): inclusive
+// scan of x -> a + p x; the first combine uses the neighbour's p as hi + lo.
+template <typename T>
+__device__ __forceinline__ T warp_chain_forward(T a, HiLo<T> pm) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  T pp = pm.hi;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T a_up = __shfl_up_sync(FULL, a, d);
+    const T p_up = __shfl_up_sync(FULL, pp, d);
+    if (lane >= d) {
+      a = (d == 1) ? fma2(HiLo<T>{pp, pm.lo}, a_up, a) : fma(pp, a_up, a);
+      pp = pp * p_up;
+    }
+  }
+  T yin = __shfl_up_sync(FULL, a, 1);
+  return lane == 0 ? T(0) : yin;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_chain_backward(T b, HiLo<T> pm) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  T qq = pm.hi;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T b_dn = __shfl_down_sync(FULL, b, d);
+    const T q_dn = __shfl_down_sync(FULL, qq, d);
+    if (lane + d < 32) {
+      b = (d == 1) ? fma2(HiLo<T>{qq, pm.lo}, b_dn, b) : fma(qq, b_dn, b);
+      qq = qq * q_dn;
+    }
+  }
+  T win = __shfl_down_sync(FULL, b, 1);
+  return lane == 31 ? T(0) : win;
+}
+
 // One x line (a warp): solve and store.  E, H (and per-node kbn, ibn) hold
 // the line's segment of this lane, zero past the line end.
 template <typename T, int L, bool PER_NODE>
@@ -609,8 +662,6 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
   const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
   const int j0 = lane * L;
   const int N = p.N;
-  const bool src_line = (jo == p.src_o) && (ko == p.src_o2);
-  const int src_t = (src_line && p.src_j >= j0 && p.src_j < j0 + L) ? p.src_j - j0 : -1;
   T y[L];
 
   T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
@@ -620,63 +671,46 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     ib_prev = __shfl_up_sync(FULL, ibn[L - 1], 1);
     if (lane == 0) ib_prev = T(0);
   }
-  const bool conv = (j0 >= p.jc) && (j0 + L <= N);
 
-  HiLo<T> pf;
-  if constexpr (PER_NODE) pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
-  else if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
-  else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, src_t, y);
-
-  // inclusive scan over lanes of x -> a + p x (Kogge-Stone); the first
-  // combine uses the neighbour's coefficient as hi + lo
-  T a = y[L - 1], pp = pf.hi;
+  if constexpr (PER_NODE) {
+    const HiLo<T> pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    const T yin = warp_chain_forward<T>(y[L - 1], pf);
+    const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
+    const T win = warp_chain_backward<T>(y[0], pb);
+    phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
+    // H update and subtraction below use y (= w) and win
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const T a_up = __shfl_up_sync(FULL, a, d);
-    const T p_up = __shfl_up_sync(FULL, pp, d);
-    if (lane >= d) {
-      a = (d == 1) ? fma2(HiLo<T>{pp, pf.lo}, a_up, a) : fma(pp, a_up, a);
-      pp = pp * p_up;
+    for (int t = 0; t < L; ++t) {
+      const T wnext = (t + 1 < L) ? y[t + 1] : win;
+      H[t] = fma(p.kd, wnext - y[t], H[t]);
+      E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+    }
+  } else {
+    // homogeneous media: lanes in the converged interior use the limit
+    // constants, lanes near the walls read the tables
+    const bool conv = (j0 >= p.jc) && (j0 + L <= N);
+    HiLo<T> pf, pb;
+    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    const T yin = warp_chain_forward<T>(y[L - 1], pf);
+    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
+    else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
+    const T win = warp_chain_backward<T>(y[0], pb);
+    if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
+    else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const T wnext = (t + 1 < L) ? y[t + 1] : win;
+      H[t] = fma(p.kd, wnext - y[t], H[t]);
+      E[t] = fma(p.alpha, y[t], p.beta * E[t]);
     }
   }
-  T yin = __shfl_up_sync(FULL, a, 1);
-  if (lane == 0) yin = T(0);
-
-  HiLo<T> pb;
-  if constexpr (PER_NODE) pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
-  else if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
-  else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
-
-  T b = y[0], qq = pb.hi;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const T b_dn = __shfl_down_sync(FULL, b, d);
-    const T q_dn = __shfl_down_sync(FULL, qq, d);
-    if (lane + d < 32) {
-      b = (d == 1) ? fma2(HiLo<T>{qq, pb.lo}, b_dn, b) : fma(qq, b_dn, b);
-      qq = qq * q_dn;
-    }
-  }
-  T win = __shfl_down_sync(FULL, b, 1);
-  if (lane == 31) win = T(0);
-
-  if constexpr (PER_NODE) phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
-  else if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
-  else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
-
-  // H update, subtraction, store (values beyond N are exactly zero)
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const T wnext = (t + 1 < L) ? y[t + 1] : win;
-    H[t] = H[t] + p.kd * (wnext - y[t]);
-    T en = p.alpha * y[t] + p.beta * E[t];
-    if (t == src_t) en += p.src_post;
-    E[t] = en;
-  }
+  // values beyond N are exactly zero, so whole segments inside the padded
+  // row are stored as vectors; the segment holding the line end element-wise
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
     store_seg<T, L>(p.h_out + base + j0, H);
-  } else {
+  } else if (j0 < N) {
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       if (j0 + t < N) {
