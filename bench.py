@@ -61,6 +61,23 @@ def workload_fields(n):
     return W.mode_sum_fields(modes, n, n, n)
 
 
+def recorded_traffic(kernel_class: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture (profiles/dram_traffic.json), or None when the kernels changed
+    since that capture or the capture is of another kernel."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        src = os.path.join(ROOT, "paper_2011_14043_gb300", "csrc", "line_kernels.cuh")
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["line_kernels_sha1"]:
+            return None
+        if kernel_class not in ("y-lines", "z-lines"):
+            return None
+        return rec["traffic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -276,7 +293,7 @@ def main():
                  for c in range(3)}
     step_bytes = 96.0 * cells  # 2 procedures x 6 arrays x (4 B read + 4 B write)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(cls_names[dom]),
                 "kernel": f"proc line solve, {cls_names[dom]}", "peak_kind": peak_kind,
                 "step_achieved": step_bytes * args.steps / (r32["ms"] / 1e3) / 1e9,
                 "step_frac": step_bytes * args.steps / (r32["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
