@@ -67,7 +67,10 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * tune[0] nodes per thread of the non-persistent y/z-line kernels (8, 16 or
  * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel. */
 typedef struct {
-  int32_t nx, ny, nz;        /* cells per axis, each >= 1; nx, ny >= 2 */
+  int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
+                                along y and z are solved with at most 32 segments of
+                                at most 32 nodes, so ny, nz <= 1024 (else
+                                FDTD_ERR_UNSUPPORTED) */
   double dx, dy, dz;         /* cell sizes [m], > 0 */
   double dt;                 /* time step [s] */
   double cfl;                /* CFL number, used when dt <= 0 */

@@ -36,7 +36,7 @@ __global__ void explicit_pair_kernel(const PairParams<T> p, int rows) {
     const long long at = base + (long long)j * p.ls;
     const T hf = p.h_in[at];
     if (j >= 1) {
-      const T kb = PER_NODE ? p.kb_sign * p.nkb[at] : p.kb;
+      const T kb = PER_NODE ? p.ks / p.nq[at] : p.kb;   // s b_j / d_eta (h > 0)
       p.e_out[at] = p.e_in[at] + kb * (hf - p.h_in[at - p.ls]);
     } else {
       p.e_out[at] = p.e_in[at];

@@ -49,15 +49,16 @@ struct PairGeom {
 // Coefficients of one pair for one procedure length h.
 struct PairCoef {
   double kb = 0, kd = 0;  // signed s*b/d_eta, s*d/d_eta
-  double dh = 0;          // |d|/(2 d_eta)
   void* tab = nullptr;    // uniform media: [10][tlen] hi/lo rows (1/beta, m, c, PF, PB) in T
   int tlen = 0;
   int L = 16;             // segment length the carry-product rows are built for
   int jc = 1 << 30;       // uniform media: first converged segment start
   double cv[6] = {0, 0, 0, 0, 0, 0};  // converged (hi, lo) of 1/beta, m, c
   double qf[2][32] = {{0}}, qb[2][32] = {{0}};
-  void* nkb = nullptr;    // per-node media (field layout, T)
-  void* nib = nullptr;
+  void* nq = nullptr;     // per-node media (field layout, T): 1/|b_j|
+  void* nib = nullptr;    //   1/beta_j (hi)
+  void* nibl = nullptr;   //   1/beta_j (lo, FP32 only)
+  double ks = 0, offh = 0, offl = 0;  // per-node: scaled-row coupling, off-diagonal
 };
 
 struct StridedCfg {
@@ -239,8 +240,9 @@ int upload_any(fdtd_t* h, void** dst, const std::vector<double>& src) {
 void free_coef(ProcCoef& pc) {
   for (auto& c : pc.pc) {
     if (c.tab) cudaFree(c.tab);
-    if (c.nkb) cudaFree(c.nkb);
+    if (c.nq) cudaFree(c.nq);
     if (c.nib) cudaFree(c.nib);
+    if (c.nibl) cudaFree(c.nibl);
     c = PairCoef();
   }
   pc.valid = false;
@@ -284,7 +286,6 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
     const double de = spacing(h, g.axis);
     const double d = hh / (2.0 * kMu0 * h->mu_r);
     c.kd = g.sign * d / de;
-    c.dh = std::fabs(d) / (2.0 * de);
     if (!h->per_node) {
       const double b = hh / (2.0 * kEps0 * h->eps_r);
       c.kb = g.sign * b / de;
@@ -363,10 +364,23 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       int rc = upload_any(h, &c.tab, tab);
       if (rc) return rc;
     } else {
-      // per-node: |b_j|/d_eta and 1/beta_j at every E node of the pair's lines
-      std::vector<double> nkb((size_t)h->count, 0.0), nib((size_t)h->count, 0.0);
+      // Per-node media: rows scaled by 1/b_j (symmetric form),
+      //   q_j w_j / 2 - (|ks| |kd| / 2) (w_{j+1} - 2 w_j + w_{j-1}) = q_j E_j + ks (H_j - H_{j-1}),
+      // q_j = 1/|b_j|, ks = s sign(h) / d_eta.  Every line is factored in FP64
+      // from exactly the q_j, ks, kd the kernel uses (rounded to the field
+      // precision first), so each procedure is an exact Cayley transform of
+      // the medium those rounded values describe.
+      const bool f32 = h->prec == FDTD_F32;
+      auto rnd = [&](double x) { return f32 ? (double)(float)x : x; };
+      c.kd = rnd(c.kd);
+      c.ks = rnd(g.sign * (hh >= 0 ? 1.0 : -1.0) / de);
+      const double kk = std::fabs(c.ks) * std::fabs(c.kd);
+      const double off = -kk / 2.0;
+      c.offh = rnd(off);
+      c.offl = f32 ? (double)(float)(off - c.offh) : 0.0;
+      std::vector<double> nq((size_t)h->count, 0.0), nib((size_t)h->count, 0.0), nibl;
+      if (f32) nibl.assign((size_t)h->count, 0.0);
       const double* er = h->eps_host[g.ec].data();
-      const double s2 = de * de;
       const long long nl = g.n_lines();
       for (long long line = 0; line < nl; ++line) {
         long long base;
@@ -380,25 +394,24 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
           const int o = g.o_lo + (int)(line / nlx);
           base = (long long)o * g.os + i;
         }
-        double ibm = 0, om = 0;
+        double ibm = 0;
         for (int j = 1; j <= g.N - 1; ++j) {
           const long long at = base + (long long)j * g.ls;
-          const double b = hh / (2.0 * kEps0 * er[at]);
-          const double o = -b * d / (2.0 * s2);
-          const double diag = 0.5 + b * d / s2;
-          const double beta = diag - o * om * ibm;
+          const double b = std::fabs(hh) / (2.0 * kEps0 * er[at]);
+          const double q = rnd(1.0 / b);
+          const double diag = q / 2.0 + kk;
+          const double beta = diag - off * off * ibm;
           const double ib = 1.0 / beta;
-          nkb[at] = std::fabs(b) / de;
-          nib[at] = ib;
+          nq[at] = q;
+          nib[at] = rnd(ib);
+          if (f32) nibl[at] = (double)(float)(ib - nib[at]);
           ibm = ib;
-          om = o;
         }
       }
-      c.kb = g.sign * (hh >= 0 ? 1.0 : -1.0);  // kb_sign
-      int rc = upload_any(h, &c.nkb, nkb);
+      int rc = upload_any(h, &c.nq, nq);
       if (rc) return rc;
-      rc = upload_any(h, &c.nib, nib);
-      if (rc) return rc;
+      if ((rc = upload_any(h, &c.nib, nib))) return rc;
+      if (f32 && (rc = upload_any(h, &c.nibl, nibl))) return rc;
     }
   }
   P.valid = true;
@@ -462,10 +475,12 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
     p.qb[1][t] = (T)c.qb[1][t];
   }
   p.err = h->d_err;
-  p.nkb = (const T*)c.nkb;
+  p.nq = (const T*)c.nq;
   p.nib = (const T*)c.nib;
-  p.kb_sign = (T)(sgn * c.kb);
-  p.dh = (T)c.dh;
+  p.nibl = (const T*)c.nibl;
+  p.ks = (T)(sgn * c.ks);
+  p.offh = (T)c.offh;
+  p.offl = (T)c.offl;
   (void)h;
   return p;
 }
@@ -542,6 +557,7 @@ StridedCfg choose_strided(int N, bool pn, int tune_L) {
       const int lanes = cand[q][0], L = cand[q][1];
       if (pass == 0 && tune_L && L != tune_L) continue;
       const int P = segments(N, L, lanes);
+      if (P > 32) continue;  // the carry chains scan at most 32 segments (one warp)
       const void* fn = strided_fn_rt<T>(pn, lanes, L);
       if (!fn) continue;
       cudaFuncAttributes a;

@@ -70,10 +70,13 @@ struct PairParams {
   T cv[6];               // converged 1/beta, m, c as (hi, lo) pairs
   T qf[2][32];           // converged PF_t = (-m)^(t+1), hi and lo
   T qb[2][32];           // converged PB_t = (-c)^(L-t), hi and lo
-  const T* nkb;          // per-node: |b_j|/d_eta at each E node (field layout)
-  const T* nib;          // per-node: 1/beta_j at each E node (field layout)
-  T kb_sign;             // per-node: RHS coupling = kb_sign * nkb_j
-  T dh;                  // per-node: off-diagonal o_j = -nkb_j * dh, dh = |d|/(2 d_eta)
+  // per-node media, rows scaled by 1/b_j (symmetric form): r'_j = q_j E_j +
+  // ks (H_j - H_{j-1}), constant off-diagonal off, pivots 1/beta_j (hi + lo)
+  const T* nq;           // per-node: q_j = 1/|b_j| at each E node (field layout)
+  const T* nib;          // per-node: 1/beta_j, hi part (field layout)
+  const T* nibl;         // per-node: 1/beta_j, lo part (FP32 fields only)
+  T ks;                  // per-node: RHS coupling of the scaled rows, s sign(h) / d_eta
+  T offh, offl;          // per-node: off-diagonal -|ks| |kd| / 2 as hi + lo
   int* err;              // set to 1 when a bounded device wait gives up
 };
 
@@ -115,26 +118,42 @@ __device__ __forceinline__ HiLo<T> tab2(const PairParams<T>& p, int row, int j, 
   else return {cv_hi[t], cv_lo[t]};
 }
 
+// a * b for a, b given as hi + lo (FP32 fields: error-free product of the
+// hi parts plus the cross terms; FP64 fields: the plain product)
+template <typename T>
+__device__ __forceinline__ HiLo<T> dd_mul(HiLo<T> a, HiLo<T> b) {
+  const T ph = a.hi * b.hi;
+  if constexpr (use_hilo<T>()) {
+    const T e = fma(a.hi, b.hi, -ph);
+    return {ph, fma(a.hi, b.lo, fma(a.lo, b.hi, e))};
+  } else {
+    return {ph, T(0)};
+  }
+}
+
 // Forward multiplier m, backward coupling c, pivot 1/beta of node j0 + t.
+// Per-node media (MODE 2): ibn / ibl hold this segment's pivots (hi, lo),
+// ib_prev the previous node's; m_j = off / beta_{j-1}, c_j = off / beta_j.
 template <typename T, int L, int MODE>
-__device__ __forceinline__ HiLo<T> coef_m(const PairParams<T>& p, int j0, int t, const T (&kbn)[L],
-                                          const T (&ibn)[L], T ib_prev) {
+__device__ __forceinline__ HiLo<T> coef_m(const PairParams<T>& p, int j0, int t, const T (&ibl)[L],
+                                          const T (&ibn)[L], HiLo<T> ib_prev) {
   if constexpr (MODE == 0) return {p.tab[TB_MH * p.tlen + j0 + t], p.tab[TB_ML * p.tlen + j0 + t]};
   else if constexpr (MODE == 1) return {p.cv[2], p.cv[3]};
-  else return {-kbn[t] * p.dh * (t == 0 ? ib_prev : ibn[t - 1]), T(0)};
+  else return dd_mul(HiLo<T>{p.offh, p.offl}, t == 0 ? ib_prev : HiLo<T>{ibn[t - 1], ibl[t - 1]});
 }
 template <typename T, int L, int MODE>
-__device__ __forceinline__ HiLo<T> coef_c(const PairParams<T>& p, int j0, int t, const T (&kbn)[L],
+__device__ __forceinline__ HiLo<T> coef_c(const PairParams<T>& p, int j0, int t, const T (&ibl)[L],
                                           const T (&ibn)[L]) {
   if constexpr (MODE == 0) return {p.tab[TB_CH * p.tlen + j0 + t], p.tab[TB_CL * p.tlen + j0 + t]};
   else if constexpr (MODE == 1) return {p.cv[4], p.cv[5]};
-  else return {-kbn[t] * p.dh * ibn[t], T(0)};
+  else return dd_mul(HiLo<T>{p.offh, p.offl}, HiLo<T>{ibn[t], ibl[t]});
 }
 template <typename T, int L, int MODE>
-__device__ __forceinline__ HiLo<T> coef_ib(const PairParams<T>& p, int j0, int t, const T (&ibn)[L]) {
+__device__ __forceinline__ HiLo<T> coef_ib(const PairParams<T>& p, int j0, int t, const T (&ibl)[L],
+                                           const T (&ibn)[L]) {
   if constexpr (MODE == 0) return {p.tab[TB_IBH * p.tlen + j0 + t], p.tab[TB_IBL * p.tlen + j0 + t]};
   else if constexpr (MODE == 1) return {p.cv[0], p.cv[1]};
-  else return {ibn[t], T(0)};
+  else return {ibn[t], ibl[t]};
 }
 // Carry products within the segment: PF_t = prod_{u<=t} (-m_u), PB_t = prod_{u>=t} (-c_u).
 template <typename T, int MODE>
@@ -150,17 +169,19 @@ __device__ __forceinline__ HiLo<T> coef_pb(const PairParams<T>& p, int j0, int t
 
 // RHS and local forward sweep from a zero carry; returns the segment's carry
 // coefficient prod(-m).
+// qn: per-node q_j (MODE 2); ibn, ibl: per-node pivots (MODE 2).
 template <typename T, int L, int MODE>
 __device__ __forceinline__ HiLo<T> phase_forward(const PairParams<T>& p, int j0, const T (&E)[L], const T (&H)[L],
-                                                 T hm1, const T (&kbn)[L], const T (&ibn)[L], T ib_prev,
-                                                 T (&y)[L]) {
+                                                 T hm1, const T (&qn)[L], const T (&ibn)[L], const T (&ibl)[L],
+                                                 HiLo<T> ib_prev, T (&y)[L]) {
   T pf = T(1), hprev = hm1;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const T kb = (MODE == 2) ? p.kb_sign * kbn[t] : p.kb;
-    const T r = fma(kb, H[t] - hprev, E[t]);
+    T r;
+    if constexpr (MODE == 2) r = fma(qn[t], E[t], p.ks * (H[t] - hprev));
+    else r = fma(p.kb, H[t] - hprev, E[t]);
     hprev = H[t];
-    const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev);
+    const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev);
     y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
     if constexpr (MODE == 2) pf *= -m.hi;
   }
@@ -171,13 +192,13 @@ __device__ __forceinline__ HiLo<T> phase_forward(const PairParams<T>& p, int j0,
 // Forward carry fix-up, then the local backward sweep from a zero carry;
 // returns the segment's carry coefficient prod(-c).
 template <typename T, int L, int MODE>
-__device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0, T yin, const T (&kbn)[L],
-                                                  const T (&ibn)[L], T ib_prev, T (&y)[L]) {
+__device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0, T yin, const T (&ibn)[L],
+                                                  const T (&ibl)[L], HiLo<T> ib_prev, T (&y)[L]) {
   if constexpr (MODE == 2) {
     T q = T(1);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
-      q *= -coef_m<T, L, MODE>(p, j0, t, kbn, ibn, ib_prev).hi;
+      q *= -coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev).hi;
       y[t] = fma(q, yin, y[t]);
     }
   } else {
@@ -187,10 +208,10 @@ __device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0
   T pb = T(1), wn = T(0);
 #pragma unroll
   for (int t = L - 1; t >= 0; --t) {
-    const HiLo<T> c = coef_c<T, L, MODE>(p, j0, t, kbn, ibn);
-    const HiLo<T> ib = coef_ib<T, L, MODE>(p, j0, t, ibn);
+    const HiLo<T> c = coef_c<T, L, MODE>(p, j0, t, ibl, ibn);
+    const HiLo<T> ib = coef_ib<T, L, MODE>(p, j0, t, ibl, ibn);
     T u;
-    if constexpr (use_hilo<T>() && MODE != 2) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
+    if constexpr (use_hilo<T>()) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
     else u = -c.hi * wn;
     y[t] = fma(y[t], ib.hi, u);
     wn = y[t];
@@ -202,13 +223,13 @@ __device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0
 
 // Backward carry fix-up: y becomes w.
 template <typename T, int L, int MODE>
-__device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win, const T (&kbn)[L],
-                                          const T (&ibn)[L], T (&y)[L]) {
+__device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win, const T (&ibn)[L],
+                                          const T (&ibl)[L], T (&y)[L]) {
   if constexpr (MODE == 2) {
     T q = T(1);
 #pragma unroll
     for (int t = L - 1; t >= 0; --t) {
-      q *= -coef_c<T, L, MODE>(p, j0, t, kbn, ibn).hi;
+      q *= -coef_c<T, L, MODE>(p, j0, t, ibl, ibn).hi;
       y[t] = fma(q, win, y[t]);
     }
   } else {
@@ -299,30 +320,31 @@ __device__ __forceinline__ int pow2_at_least(int P) {
 // between warps; every barrier sits outside the MODE branches.
 template <typename T, int LANES, int L, bool PER_NODE>
 __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
-                                              const T (&E)[L], const T (&H)[L], T hm1, const T (&kbn)[L],
-                                              const T (&ibn)[L], T ib_prev, T (&y)[L], T& win) {
+                                              const T (&E)[L], const T (&H)[L], T hm1, const T (&qn)[L],
+                                              const T (&ibn)[L], const T (&ibl)[L], HiLo<T> ib_prev, T (&y)[L],
+                                              T& win) {
   const bool conv = (j0 >= p.jc) && (j0 + L <= p.N);
   HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
-    pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
   } else {
-    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
-    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
+    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
   }
   const int PW = pow2_at_least(P);
   const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf);
   if constexpr (PER_NODE) {
-    pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
+    pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
   } else {
-    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
-    else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
+    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, ibn, ibl, ib_prev, y);
+    else pb = phase_backward<T, L, 0>(p, j0, yin, ibn, ibl, ib_prev, y);
   }
   win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb);
   if constexpr (PER_NODE) {
-    phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
+    phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
   } else {
-    if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
-    else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
+    if (conv) phase_fix<T, L, 1>(p, j0, win, ibn, ibl, y);
+    else phase_fix<T, L, 0>(p, j0, win, ibn, ibl, y);
   }
 }
 
@@ -370,14 +392,16 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
   const int N = p.N;
   const long long ls = p.ls;
 
-  T E[L], H[L], y[L], kbn[L], ibn[L];
-  T ib_prev = T(0), hm1 = T(0);
+  T E[L], H[L], y[L], qn[L], ibn[L], ibl[L];
+  HiLo<T> ib_prev = {T(0), T(0)};
+  T hm1 = T(0);
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     E[t] = T(0);
     H[t] = T(0);
-    kbn[t] = T(0);
+    qn[t] = T(0);
     ibn[t] = T(0);
+    ibl[t] = T(0);
   }
   if (active) {
     const T* pe = p.e_in + base;
@@ -389,18 +413,22 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
         E[t] = pe[(long long)j * ls];
         H[t] = ph[(long long)j * ls];
         if constexpr (PER_NODE) {
-          kbn[t] = p.nkb[base + (long long)j * ls];
+          qn[t] = p.nq[base + (long long)j * ls];
           ibn[t] = p.nib[base + (long long)j * ls];
+          if constexpr (use_hilo<T>()) ibl[t] = p.nibl[base + (long long)j * ls];
         }
       }
     }
     if (j0 > 0 && j0 - 1 < N) {
       hm1 = ph[(long long)(j0 - 1) * ls];
-      if constexpr (PER_NODE) ib_prev = p.nib[base + (long long)(j0 - 1) * ls];
+      if constexpr (PER_NODE) {
+        ib_prev.hi = p.nib[base + (long long)(j0 - 1) * ls];
+        if constexpr (use_hilo<T>()) ib_prev.lo = p.nibl[base + (long long)(j0 - 1) * ls];
+      }
     }
   }
   T win;
-  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, ib_prev, y, win);
+  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
 }
 
@@ -537,14 +565,18 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
 
     const T* sE = buf + (2 * stage + 0) * stage_elems;
     const T* sH = buf + (2 * stage + 1) * stage_elems;
-    T E[L], H[L], y[L], kbn[L], ibn[L];
+    T E[L], H[L], y[L], qn[L], ibn[L], ibl[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      qn[t] = T(0);
+      ibn[t] = T(0);
+      ibl[t] = T(0);
+    }
     if (j0 + L <= N) {
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         E[t] = sE[(j0 + t) * LANES + lane];
         H[t] = sH[(j0 + t) * LANES + lane];
-        kbn[t] = T(0);
-        ibn[t] = T(0);
       }
     } else {
 #pragma unroll
@@ -553,8 +585,6 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
         const bool in = j < N;
         E[t] = in ? sE[j * LANES + lane] : T(0);
         H[t] = in ? sH[j * LANES + lane] : T(0);
-        kbn[t] = T(0);
-        ibn[t] = T(0);
       }
     }
     const T hm1 = (j0 > 0 && j0 - 1 < N) ? sH[(j0 - 1) * LANES + lane] : T(0);
@@ -567,7 +597,8 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
       }
     }
     T win;
-    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, kbn, ibn, T(0), y, win);
+    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
+                                      win);
     if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
   }
 }
@@ -650,11 +681,11 @@ __device__ __forceinline__ T warp_chain_backward(T b, HiLo<T> pm) {
   return lane == 31 ? T(0) : win;
 }
 
-// One x line (a warp): solve and store.  E, H (and per-node kbn, ibn) hold
-// the line's segment of this lane, zero past the line end.
+// One x line (a warp): solve and store.  E, H (and per-node qn, ibn, ibl)
+// hold the line's segment of this lane, zero past the line end.
 template <typename T, int L, bool PER_NODE>
 __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
-                                                const T (&kbn)[L], const T (&ibn)[L]) {
+                                                const T (&qn)[L], const T (&ibn)[L], const T (&ibl)[L]) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int jo = p.o_lo + (int)(line % p.n_o);
@@ -666,18 +697,19 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
 
   T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
   if (lane == 0) hm1 = T(0);
-  T ib_prev = T(0);
+  HiLo<T> ib_prev = {T(0), T(0)};
   if constexpr (PER_NODE) {
-    ib_prev = __shfl_up_sync(FULL, ibn[L - 1], 1);
-    if (lane == 0) ib_prev = T(0);
+    ib_prev.hi = __shfl_up_sync(FULL, ibn[L - 1], 1);
+    if constexpr (use_hilo<T>()) ib_prev.lo = __shfl_up_sync(FULL, ibl[L - 1], 1);
+    if (lane == 0) ib_prev = {T(0), T(0)};
   }
 
   if constexpr (PER_NODE) {
-    const HiLo<T> pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    const HiLo<T> pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
     const T yin = warp_chain_forward<T>(y[L - 1], pf);
-    const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, kbn, ibn, ib_prev, y);
+    const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
     const T win = warp_chain_backward<T>(y[0], pb);
-    phase_fix<T, L, 2>(p, j0, win, kbn, ibn, y);
+    phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
     // H update and subtraction below use y (= w) and win
 #pragma unroll
     for (int t = 0; t < L; ++t) {
@@ -690,14 +722,14 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     // constants, lanes near the walls read the tables
     const bool conv = (j0 >= p.jc) && (j0 + L <= N);
     HiLo<T> pf, pb;
-    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
-    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, kbn, ibn, ib_prev, y);
+    if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
+    else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
     const T yin = warp_chain_forward<T>(y[L - 1], pf);
-    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, kbn, ibn, ib_prev, y);
-    else pb = phase_backward<T, L, 0>(p, j0, yin, kbn, ibn, ib_prev, y);
+    if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, ibn, ibl, ib_prev, y);
+    else pb = phase_backward<T, L, 0>(p, j0, yin, ibn, ibl, ib_prev, y);
     const T win = warp_chain_backward<T>(y[0], pb);
-    if (conv) phase_fix<T, L, 1>(p, j0, win, kbn, ibn, y);
-    else phase_fix<T, L, 0>(p, j0, win, kbn, ibn, y);
+    if (conv) phase_fix<T, L, 1>(p, j0, win, ibn, ibl, y);
+    else phase_fix<T, L, 0>(p, j0, win, ibn, ibl, y);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
@@ -725,7 +757,7 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
 // Segments never run past the padded row (the row pitch is >= 32*L).
 template <typename T, int L, bool PER_NODE>
 __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
-                                         T (&kbn)[L], T (&ibn)[L]) {
+                                         T (&qn)[L], T (&ibn)[L], T (&ibl)[L]) {
   const int lane = threadIdx.x & 31;
   const int jo = p.o_lo + (int)(line % p.n_o);
   const int ko = p.o2_lo + (int)(line / p.n_o);
@@ -735,15 +767,17 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
   for (int t = 0; t < L; ++t) {
     E[t] = T(0);
     H[t] = T(0);
-    kbn[t] = T(0);
+    qn[t] = T(0);
     ibn[t] = T(0);
+    ibl[t] = T(0);
   }
   if (j0 < p.N) {  // lanes wholly past the line end touch no memory
     load_seg<T, L>(p.e_in + base + j0, E);
     load_seg<T, L>(p.h_in + base + j0, H);
     if constexpr (PER_NODE) {
-      load_seg<T, L>(p.nkb + base + j0, kbn);
+      load_seg<T, L>(p.nq + base + j0, qn);
       load_seg<T, L>(p.nib + base + j0, ibn);
+      if constexpr (use_hilo<T>()) load_seg<T, L>(p.nibl + base + j0, ibl);
     }
   }
 #pragma unroll
@@ -751,8 +785,9 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
     if (j0 + t >= p.N) {
       E[t] = T(0);
       H[t] = T(0);
-      kbn[t] = T(0);
+      qn[t] = T(0);
       ibn[t] = T(0);
+      ibl[t] = T(0);
     }
   }
 }
@@ -762,9 +797,9 @@ template <typename T, int L, bool PER_NODE>
 __global__ void proc_rows_kernel(const PairParams<T> p) {
   const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
-  T E[L], H[L], kbn[L], ibn[L];
-  row_load<T, L, PER_NODE>(p, line, E, H, kbn, ibn);
-  row_solve_store<T, L, PER_NODE>(p, line, E, H, kbn, ibn);
+  T E[L], H[L], qn[L], ibn[L], ibl[L];
+  row_load<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
+  row_solve_store<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
 }
 
 }  // namespace fdtd

@@ -72,3 +72,32 @@ def test_cavity_128_flod_fss_f32(scheme):
     report(f"cavity128_{scheme}_f32", rel_err=err, energy_drift=drift)
     assert err <= TOL["f32"]
     assert drift <= 1e-4
+
+
+def run_blocks(n, steps, prec, scheme, seed=3):
+    """Workload 3: eps_r blocks in [1, 10], 0.5 mm cells, CFL 8, z dipole at the centre."""
+    from paper_2011_14043_gb300 import Simulation
+    d = 0.5e-3
+    g = G.Grid(n, n, n, d, d, d)
+    dt = 8.0 * g.dt_cfl()
+    eps = W.eps_blocks(seed, n, n, n, 1.0, 10.0)
+    cur = W.dipole_current((np.arange(steps) + 0.5) * dt)
+    sim = Simulation(n, n, n, d, scheme=scheme, precision=prec, dt=dt)
+    sim.set_material(eps)
+    sim.set_source("ez", n // 2, n // 2, n // 2, cur)
+    sim.step(steps)
+    out = {c: sim.get_field(c).astype(np.float64) for c in G.COMPS}
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["flod", "fss"])
+def test_blocks_256_f32_vs_f64(scheme):
+    """FP32 precision statement at the full workload-3 size: FP32 fields vs the
+    FP64 path (itself pinned to the oracle to 1e-12 on the same recipe at
+    reduced size in test_gpu_parity.py)."""
+    f64 = run_blocks(256, 1000, "f64", scheme)
+    f32 = run_blocks(256, 1000, "f32", scheme)
+    err = energy_norm_rel(f32, f64)
+    report(f"blocks256_{scheme}_f32_vs_f64", rel_err=err)
+    assert err <= 1e-4
