@@ -195,6 +195,22 @@ int fdtd_reset_stats(fdtd_t* h);
 int fdtd_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, double eps_r, double mu_r,
                         int precision, const void* const* fields, double* out_device, void* stream);
 
+/* Batches (workload 4: many independent cavities).  A batch steps a set of
+ * handles together: each procedure of the scheme runs as one launch per
+ * (line direction, segment length) group covering every grid of the batch,
+ * and one step of the whole batch is captured once as a CUDA graph and
+ * replayed.  Every grid runs exactly the arithmetic of its own handle's
+ * fdtd_step.  Handles must share scheme, precision and stream, be distinct,
+ * and have no source or probe (FDTD_ERR_UNSUPPORTED); they stay owned by
+ * the caller, stay usable for set/get/energy, and must outlive the batch.
+ * stream: the handles' stream.  Errors as for fdtd_step. */
+typedef struct fdtd_batch_s fdtd_batch_t;
+int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batch_t** out);
+int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps);
+int fdtd_batch_destroy(fdtd_batch_t* b);
+/* Kernel launches per batch step (for accounting); valid after a step. */
+int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
+
 /* Static description of an error code. */
 const char* fdtd_strerror(int code);
 

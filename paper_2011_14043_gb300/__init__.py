@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import COMPS, PRECISIONS, SCHEMES, FdtdDesc, FdtdError, FdtdStats, check, lib
 
-__all__ = ["Simulation", "FdtdError", "comp_shape", "build", "energy_noalloc"]
+__all__ = ["Simulation", "Batch", "FdtdError", "comp_shape", "build", "energy_noalloc"]
 
 
 def comp_shape(comp: str, nx: int, ny: int, nz: int) -> tuple:
@@ -232,3 +232,42 @@ class Simulation:
         out = (ctypes.c_double * 2)()
         check(lib().fdtd_energy(self._h, out), "fdtd_energy")
         return out[0], out[1]
+
+
+class Batch:
+    """Many independent grids stepped together (one launch per line direction
+    and procedure for the whole batch, one CUDA graph per batch step).  The
+    Simulation objects stay usable for set/get/energy and must share scheme,
+    precision and stream; they must outlive the batch."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        if not self.sims:
+            raise ValueError("empty batch")
+        arr = (ctypes.c_void_p * len(self.sims))(*[s_._h.value for s_ in self.sims])
+        h = ctypes.c_void_p()
+        check(lib().fdtd_batch_create(arr, len(self.sims), self.sims[0]._stream, ctypes.byref(h)),
+              "fdtd_batch_create")
+        self._h = h
+
+    def step(self, n: int = 1):
+        check(lib().fdtd_batch_step(self._h, int(n)), "fdtd_batch_step")
+
+    def launches_per_step(self) -> int:
+        v = ctypes.c_int64()
+        check(lib().fdtd_batch_launches(self._h, ctypes.byref(v)), "fdtd_batch_launches")
+        return v.value
+
+    def synchronize(self):
+        self.sims[0].synchronize()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fdtd_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

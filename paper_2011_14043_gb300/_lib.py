@@ -31,7 +31,8 @@ EXPORTS = (
     "fdtd_get_field", "fdtd_get_state", "fdtd_set_state", "fdtd_set_source", "fdtd_add_probe",
     "fdtd_step", "fdtd_get_probe", "fdtd_energy", "fdtd_steps_done", "fdtd_synchronize",
     "fdtd_strerror", "fdtd_set_timing", "fdtd_get_stats", "fdtd_reset_stats",
-    "fdtd_energy_noalloc",
+    "fdtd_energy_noalloc", "fdtd_batch_create", "fdtd_batch_step", "fdtd_batch_destroy",
+    "fdtd_batch_launches",
 )
 
 
@@ -96,6 +97,10 @@ def lib() -> ctypes.CDLL:
         "fdtd_set_timing": (i32, [vp, i32]),
         "fdtd_get_stats": (i32, [vp, ctypes.POINTER(FdtdStats)]),
         "fdtd_reset_stats": (i32, [vp]),
+        "fdtd_batch_create": (i32, [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]),
+        "fdtd_batch_step": (i32, [vp, i64]),
+        "fdtd_batch_destroy": (i32, [vp]),
+        "fdtd_batch_launches": (i32, [vp, ctypes.POINTER(i64)]),
         "fdtd_energy_noalloc": (i32, [i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, i32, ctypes.POINTER(vp),
                                       ctypes.POINTER(ctypes.c_double), vp]),

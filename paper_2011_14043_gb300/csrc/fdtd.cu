@@ -1429,3 +1429,293 @@ int fdtd_reset_stats(fdtd_t* h) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batches: many independent grids stepped together
+// ===========================================================================
+namespace {
+
+constexpr int kBatchLanes = 16;
+
+struct BatchGroup {
+  int kind = 0;             // 0 lines along y, 1 along z, 2 along x
+  int L = 16, P = 1;        // segment length; segments per block (strided)
+  int ngrids = 0;
+  long long nitems = 0;     // tiles (strided) or lines (x)
+  void* d_params = nullptr; // PairParams<T>[ngrids]
+  void* d_index = nullptr;  // BatchTile[nitems] or long long line_start[ngrids + 1]
+};
+
+}  // namespace
+
+struct fdtd_batch_s {
+  std::vector<fdtd_t*> h;
+  int prec = 0, scheme = 0;
+  cudaStream_t stream = nullptr;       // the handles' stream
+  cudaStream_t run = nullptr;          // capture/replay stream (never the legacy default)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<BatchGroup> groups[2];           // per procedure slot
+  std::vector<const void*> bound;              // state pointers the tables were built for
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+void free_groups(fdtd_batch_t* b) {
+  for (auto& gs : b->groups)
+    for (auto& g : gs) {
+      if (g.d_params) cudaFree(g.d_params);
+      if (g.d_index) cudaFree(g.d_index);
+    }
+  b->groups[0].clear();
+  b->groups[1].clear();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+#define BCK(call)                                                          \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) {                                               \
+      fprintf(stderr, "fdtd batch: CUDA error: %s\n", cudaGetErrorString(_e)); \
+      return FDTD_ERR_CUDA;                                                \
+    }                                                                      \
+  } while (0)
+
+template <typename T>
+int build_groups_t(fdtd_batch_t* b) {
+  free_groups(b);
+  for (int slot = 0; slot < 2; ++slot) {
+    // key: (kind, L) -> grids in the group
+    std::vector<std::pair<std::pair<int, int>, std::vector<std::pair<int, int>>>> keys;  // (kind,L) -> (grid, q)
+    for (int gi = 0; gi < (int)b->h.size(); ++gi) {
+      fdtd_t* h = b->h[gi];
+      const ProcCoef& P = h->proc[slot];
+      for (int q = 0; q < 3; ++q) {
+        const PairGeom& g = h->geom[P.op][q];
+        if (g.empty()) continue;
+        const int kind = g.rows ? 2 : (g.axis == AX_Y ? 0 : 1);
+        const int L = g.rows ? pick_rows_L(g.N) : h->strided_cfg[kind].L;
+        bool found = false;
+        for (auto& k : keys)
+          if (k.first.first == kind && k.first.second == L) {
+            k.second.push_back({gi, q});
+            found = true;
+          }
+        if (!found) keys.push_back({{kind, L}, {{gi, q}}});
+      }
+    }
+    for (auto& k : keys) {
+      BatchGroup bg;
+      bg.kind = k.first.first;
+      bg.L = k.first.second;
+      bg.ngrids = (int)k.second.size();
+      std::vector<fdtd::PairParams<T>> params;
+      std::vector<fdtd::BatchTile> tiles;
+      std::vector<long long> starts(1, 0);
+      int Pmax = 1;
+      for (int m = 0; m < bg.ngrids; ++m) {
+        fdtd_t* h = b->h[k.second[m].first];
+        const int q = k.second[m].second;
+        const ProcCoef& P = h->proc[slot];
+        const PairGeom& g = h->geom[P.op][q];
+        params.push_back(make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, h->f));
+        if (bg.kind == 2) {
+          starts.push_back(starts.back() + g.n_lines());
+        } else {
+          Pmax = std::max(Pmax, segments(g.N, bg.L, kBatchLanes));
+          const int tx = (g.lane_hi + kBatchLanes - 1) / kBatchLanes;
+          for (int o = 0; o < g.n_o; ++o)
+            for (int bx = 0; bx < tx; ++bx) tiles.push_back({m, bx * kBatchLanes, g.o_lo + o, 0});
+        }
+      }
+      bg.P = Pmax;
+      if (Pmax > 32) return FDTD_ERR_UNSUPPORTED;
+      BCK(cudaMalloc(&bg.d_params, sizeof(fdtd::PairParams<T>) * params.size()));
+      BCK(cudaMemcpy(bg.d_params, params.data(), sizeof(fdtd::PairParams<T>) * params.size(),
+                     cudaMemcpyHostToDevice));
+      if (bg.kind == 2) {
+        bg.nitems = starts.back();
+        BCK(cudaMalloc(&bg.d_index, sizeof(long long) * starts.size()));
+        BCK(cudaMemcpy(bg.d_index, starts.data(), sizeof(long long) * starts.size(), cudaMemcpyHostToDevice));
+      } else {
+        bg.nitems = (long long)tiles.size();
+        BCK(cudaMalloc(&bg.d_index, sizeof(fdtd::BatchTile) * tiles.size()));
+        BCK(cudaMemcpy(bg.d_index, tiles.data(), sizeof(fdtd::BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
+      }
+      b->groups[slot].push_back(bg);
+    }
+  }
+  return FDTD_OK;
+}
+
+template <typename T, int L>
+void launch_batch_strided_L(fdtd_batch_t* b, const BatchGroup& g) {
+  const int threads = g.P * kBatchLanes;
+  const size_t smem = 6 * (size_t)(g.P | 1) * kBatchLanes * sizeof(T);
+  fdtd::proc_strided_batch_kernel<T, kBatchLanes, L><<<(unsigned)g.nitems, threads, smem, b->run>>>(
+      (const fdtd::PairParams<T>*)g.d_params, (const fdtd::BatchTile*)g.d_index);
+}
+
+template <typename T, int L>
+void launch_batch_rows_L(fdtd_batch_t* b, const BatchGroup& g) {
+  const int wpb = 8;
+  fdtd::proc_rows_batch_kernel<T, L><<<(unsigned)((g.nitems + wpb - 1) / wpb), wpb * 32, 0, b->run>>>(
+      (const fdtd::PairParams<T>*)g.d_params, (const long long*)g.d_index, g.ngrids);
+}
+
+template <typename T>
+int launch_batch_group(fdtd_batch_t* b, const BatchGroup& g) {
+  b->launches++;
+  if (g.kind == 2) {
+    switch (g.L) {
+      case 1: launch_batch_rows_L<T, 1>(b, g); break;
+      case 2: launch_batch_rows_L<T, 2>(b, g); break;
+      case 4: launch_batch_rows_L<T, 4>(b, g); break;
+      case 8: launch_batch_rows_L<T, 8>(b, g); break;
+      case 12: launch_batch_rows_L<T, 12>(b, g); break;
+      case 16: launch_batch_rows_L<T, 16>(b, g); break;
+      case 24: launch_batch_rows_L<T, 24>(b, g); break;
+      case 32: launch_batch_rows_L<T, 32>(b, g); break;
+      default: return FDTD_ERR_UNSUPPORTED;
+    }
+  } else {
+    switch (g.L) {
+      case 8: launch_batch_strided_L<T, 8>(b, g); break;
+      case 16: launch_batch_strided_L<T, 16>(b, g); break;
+      case 32: launch_batch_strided_L<T, 32>(b, g); break;
+      default: return FDTD_ERR_UNSUPPORTED;
+    }
+  }
+  BCK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+// One time step of every grid: the scheme's procedure sequence, each
+// procedure one launch per group.
+template <typename T>
+int batch_one_step(fdtd_batch_t* b) {
+  static const int seq_fss[3] = {0, 1, 0};
+  static const int seq_two[2] = {0, 1};
+  const int* seq = b->scheme == FDTD_FSS ? seq_fss : seq_two;
+  const int n = b->scheme == FDTD_FSS ? 3 : 2;
+  for (int k = 0; k < n; ++k)
+    for (const auto& g : b->groups[seq[k]]) {
+      int rc = launch_batch_group<T>(b, g);
+      if (rc) return rc;
+    }
+  return FDTD_OK;
+}
+
+int batch_prepare(fdtd_batch_t* b) {
+  for (fdtd_t* h : b->h) {
+    int rc = scheme_init(h);
+    if (rc) return rc;
+  }
+  std::vector<const void*> ptrs;
+  for (fdtd_t* h : b->h)
+    for (int c = 0; c < 6; ++c) ptrs.push_back(h->f[c]);
+  if (ptrs == b->bound && !b->groups[0].empty()) return FDTD_OK;
+  int rc = b->prec == FDTD_F64 ? build_groups_t<double>(b) : build_groups_t<float>(b);
+  if (rc) return rc;
+  b->bound = ptrs;
+  return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batch_t** out) {
+  if (!handles || count < 1 || !out) return FDTD_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    fdtd_t* h = handles[i];
+    if (!h) return FDTD_ERR_INVALID_ARG;
+    if (h->poisoned) return FDTD_ERR_STATE;
+    if (h->scheme != handles[0]->scheme || h->prec != handles[0]->prec) return FDTD_ERR_INVALID_ARG;
+    if (h->stream != (cudaStream_t)stream) return FDTD_ERR_INVALID_ARG;
+    if (h->src_comp >= 0 || h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h) return FDTD_ERR_INVALID_ARG;
+  }
+  fdtd_batch_t* b = new (std::nothrow) fdtd_batch_s();
+  if (!b) return FDTD_ERR_OOM;
+  b->h.assign(handles, handles + count);
+  b->prec = handles[0]->prec;
+  b->scheme = handles[0]->scheme;
+  b->stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&b->run, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    fdtd_batch_destroy(b);
+    return FDTD_ERR_CUDA;
+  }
+  *out = b;
+  return FDTD_OK;
+}
+
+int fdtd_batch_destroy(fdtd_batch_t* b) {
+  if (!b) return FDTD_OK;
+  if (b->run) cudaStreamSynchronize(b->run);
+  cudaStreamSynchronize(b->stream);
+  free_groups(b);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->run) cudaStreamDestroy(b->run);
+  delete b;
+  return FDTD_OK;
+}
+
+int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return FDTD_ERR_INVALID_ARG;
+  for (fdtd_t* h : b->h) {
+    if (h->poisoned) return FDTD_ERR_STATE;
+    if (h->src_comp >= 0 || h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
+  }
+  if (nsteps == 0) return FDTD_OK;
+  int rc = batch_prepare(b);
+  if (rc) return rc;
+  if (!b->exec) {
+    // one step of every grid, captured once as a CUDA graph and replayed
+    BCK(cudaStreamBeginCapture(b->run, cudaStreamCaptureModeThreadLocal));
+    rc = b->prec == FDTD_F64 ? batch_one_step<double>(b) : batch_one_step<float>(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->run, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    BCK(e);
+    b->graph = g;
+    BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  }
+  // order after the handles' earlier work, and their later work after this
+  BCK(cudaEventRecord(b->ev_in, b->stream));
+  BCK(cudaStreamWaitEvent(b->run, b->ev_in, 0));
+  for (int64_t k = 0; k < nsteps; ++k) BCK(cudaGraphLaunch(b->exec, b->run));
+  BCK(cudaEventRecord(b->ev_out, b->run));
+  BCK(cudaStreamWaitEvent(b->stream, b->ev_out, 0));
+  for (fdtd_t* h : b->h) {
+    h->steps += nsteps;
+    h->output_valid = false;
+    h->launches += (long long)nsteps * (long long)b->groups[0].size();  // approximate share
+  }
+  return FDTD_OK;
+}
+
+int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step) {
+  if (!b || !per_step) return FDTD_ERR_INVALID_ARG;
+  const int n = b->scheme == FDTD_FSS ? 3 : 2;
+  const int seq[3] = {0, 1, 0};
+  long long c = 0;
+  for (int k = 0; k < n; ++k) c += (long long)b->groups[seq[k]].size();
+  *per_step = c;
+  return FDTD_OK;
+}
+
+}  // extern "C"

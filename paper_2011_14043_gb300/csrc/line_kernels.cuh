@@ -802,4 +802,111 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
   row_solve_store<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
 }
 
+// ---------------------------------------------------------------------------
+// Batched lines: many independent grids in one launch
+// ---------------------------------------------------------------------------
+// One launch covers the same pair of every grid of a batch.  y/z lines: one
+// block per tile of LANES lines of one grid, tile table entry =
+// (grid, x0, outer index); the block reads its grid's parameters once into
+// shared memory.  Blocks hold P = blockDim / LANES segments, enough for the
+// longest line of the batch; shorter lines leave their upper segments empty.
+struct BatchTile {
+  int grid, x0, o, pad;
+};
+
+template <typename T, int LANES, int L>
+__global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ params,
+                                          const BatchTile* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) PairParams<T> ps;
+  const BatchTile tile = tiles[blockIdx.x];
+  {
+    // cooperative word copy of this grid's parameters
+    static_assert(sizeof(PairParams<T>) % 4 == 0, "word copy");
+    const int* src = reinterpret_cast<const int*>(params + tile.grid);
+    int* dst = reinterpret_cast<int*>(&ps);
+    for (int k = threadIdx.x; k < (int)(sizeof(PairParams<T>) / 4); k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
+  const PairParams<T>& p = ps;
+  T* sh = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x % LANES;
+  const int s = threadIdx.x / LANES;
+  const int P = blockDim.x / LANES;
+  const int i = tile.x0 + lane;
+  const int o = tile.o;
+  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
+  const long long base = (long long)o * p.os + i;
+  const int j0 = s * L;
+  const int N = p.N;
+  const long long ls = p.ls;
+  const bool pn = p.nq != nullptr;
+
+  T E[L], H[L], y[L], qn[L], ibn[L], ibl[L];
+  HiLo<T> ib_prev = {T(0), T(0)};
+  T hm1 = T(0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = T(0);
+    H[t] = T(0);
+    qn[t] = T(0);
+    ibn[t] = T(0);
+    ibl[t] = T(0);
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int j = j0 + t;
+      if (j < N) {
+        const long long at = base + (long long)j * ls;
+        E[t] = p.e_in[at];
+        H[t] = p.h_in[at];
+        if (pn) {
+          qn[t] = p.nq[at];
+          ibn[t] = p.nib[at];
+          if constexpr (use_hilo<T>()) ibl[t] = p.nibl[at];
+        }
+      }
+    }
+    if (j0 > 0 && j0 - 1 < N) {
+      const long long at = base + (long long)(j0 - 1) * ls;
+      hm1 = p.h_in[at];
+      if (pn) {
+        ib_prev.hi = p.nib[at];
+        if constexpr (use_hilo<T>()) ib_prev.lo = p.nibl[at];
+      }
+    }
+  }
+  T win;
+  if (pn) strided_solve<T, LANES, L, true>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
+}
+
+// x lines of every grid of a group: one warp per line; line_start[g] is the
+// first global line of the group's grid g (ascending, line_start[ngrids] =
+// total).  All grids of a group share the segment length L of their tables.
+template <typename T, int L>
+__global__ void proc_rows_batch_kernel(const PairParams<T>* __restrict__ params,
+                                       const long long* __restrict__ line_start, int ngrids) {
+  const long long gline = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gline >= line_start[ngrids]) return;  // whole warp leaves together
+  int lo = 0, hi = ngrids;                  // line_start[lo] <= gline < line_start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (line_start[mid] <= gline) lo = mid;
+    else hi = mid;
+  }
+  const PairParams<T>& p = params[lo];
+  const long long line = gline - line_start[lo];
+  T E[L], H[L], qn[L], ibn[L], ibl[L];
+  if (p.nq != nullptr) {
+    row_load<T, L, true>(p, line, E, H, qn, ibn, ibl);
+    row_solve_store<T, L, true>(p, line, E, H, qn, ibn, ibl);
+  } else {
+    row_load<T, L, false>(p, line, E, H, qn, ibn, ibl);
+    row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+  }
+}
+
 }  // namespace fdtd
