@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", type=int, nargs=2, default=(0, 0), help="kernel-shape overrides (fdtd_desc.tune)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the many-cavity batch measurement")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -196,6 +199,75 @@ def run_e2e(args, prec, fields):
     return {"s": t1 - t0, "h2d": nbytes, "d2h": nbytes}
 
 
+def batch_rel_err(a: dict, b: dict) -> float:
+    """Relative L2 in the vacuum energy norm (E weighted by eps0, H by mu0)."""
+    import numpy as np
+    eps0 = 1.0 / (1.25663706212e-6 * 299792458.0 ** 2)
+    num = den = 0.0
+    for c in a:
+        w = eps0 if c.startswith("e") else 1.25663706212e-6
+        num += w * float(np.sum((a[c].astype(np.float64) - b[c]) ** 2))
+        den += w * float(np.sum(b[c].astype(np.float64) ** 2))
+    return math.sqrt(num / den)
+
+
+def run_batch(wls, prec, steps, warmup, want_fields):
+    """Many cavities stepped as one batch (one CUDA graph per step); CUDA
+    events on the handles' stream around ``steps`` steps."""
+    import torch
+    from paper_2011_14043_gb300 import Batch, Simulation
+    sims = []
+    for w in wls:
+        s = Simulation(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, scheme="fadi", precision=prec, cfl=w.cfl)
+        s.set_material(w.eps_r)
+        s.set_fields(w.fields)
+        sims.append(s)
+    b = Batch(sims)
+    b.step(warmup)
+    b.synchronize()
+    stream = torch.cuda.ExternalStream(sims[0]._stream.value) if sims[0]._stream.value \
+        else torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    per_step = b.launches_per_step()
+    fields = [s.get_fields() for s in sims] if want_fields else None
+    b.close()
+    for s in sims:
+        s.close()
+    return {"ms": ms, "launches_per_step": per_step, "fields": fields}
+
+
+def batch_section(args):
+    """64 seeded PEC cavities (32..160 x 32..96 x 32..128 cells, CFL in [2, 10],
+    eps_r blocks in [1, 4], 8-mode initial field), FADI FP32, stepped together;
+    per-instance error against the FP64 path after the same steps."""
+    import workloads as W
+    wls = W.workload_batch(seed=4, count=args.batch_count, steps=args.batch_steps)
+    cells = sum(w.nx * w.ny * w.nz for w in wls)
+    r32 = run_batch(wls, "f32", args.batch_steps, args.warmup, want_fields=not args.no_fp64)
+    out = {"value": cells * args.batch_steps / (r32["ms"] / 1e3), "unit": UNIT,
+           "ms_per_step": r32["ms"] / args.batch_steps, "steps": args.batch_steps, "warmup": args.warmup,
+           "instances": len(wls), "cells": cells, "dtype": "f32",
+           "workload": f"{len(wls)} seeded PEC cavities, 1 mm cells, sizes 32..160 x 32..96 x 32..128, "
+                       f"CFL U[2,10], eps_r blocks U[1,4], 8 seeded modes, FADI",
+           "gpu_launches": r32["launches_per_step"] * args.batch_steps,
+           "hbm_frac_step": 96.0 * cells * args.batch_steps / (r32["ms"] / 1e3) / 1e9
+           / measured_peaks()[0]["hbm_gbs"]}
+    if not args.no_fp64:
+        r64 = run_batch(wls, "f64", args.batch_steps, args.warmup, want_fields=True)
+        errs = [batch_rel_err(a, b) for a, b in zip(r32["fields"], r64["fields"])]
+        out["fp64_value"] = cells * args.batch_steps / (r64["ms"] / 1e3)
+        out["max_rel_err_vs_fp64"] = max(errs)
+        out["median_rel_err_vs_fp64"] = statistics.median(errs)
+        out["error_norm"] = "per-instance relative L2, vacuum energy weights, FP32 vs FP64 path after the same steps"
+    return out
+
+
 def cpu_baseline(n, steps=1):
     """The FP64 numpy oracle timed on this host on a bounded sample."""
     import oracle.grid as G
@@ -322,6 +394,8 @@ def main():
         ev = ws * cells * args.steps / e["s"]
         line["e2e"] = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": e["h2d"] / args.steps,
                        "d2h_bytes_per_step": e["d2h"] / args.steps}
+    if not args.no_batch:
+        line["batch"] = batch_section(args)
     if rank == 0 and not args.no_cpu_baseline:
         v, s = cpu_baseline(n, steps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -1703,7 +1703,6 @@ int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps) {
   for (fdtd_t* h : b->h) {
     h->steps += nsteps;
     h->output_valid = false;
-    h->launches += (long long)nsteps * (long long)b->groups[0].size();  // approximate share
   }
   return FDTD_OK;
 }

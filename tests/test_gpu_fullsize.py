@@ -101,3 +101,43 @@ def test_blocks_256_f32_vs_f64(scheme):
     err = energy_norm_rel(f32, f64)
     report(f"blocks256_{scheme}_f32_vs_f64", rel_err=err)
     assert err <= 1e-4
+
+
+def run_batch(wls, prec, steps):
+    from paper_2011_14043_gb300 import Batch, Simulation
+    sims = []
+    for w in wls:
+        s = Simulation(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, scheme="fadi", precision=prec, cfl=w.cfl)
+        s.set_material(w.eps_r)
+        s.set_fields(w.fields)
+        sims.append(s)
+    b = Batch(sims)
+    b.step(steps)
+    out = [{c: s.get_field(c).astype(np.float64) for c in G.COMPS} for s in sims]
+    dts = [s.dt for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    return out, dts
+
+
+def test_batch_64_cavities_500_steps():
+    """Workload 4 at full size: 64 seeded cavities of uneven sizes, CFL numbers
+    and eps_r blocks, 500 FADI steps as one batch.  Every FP32 instance within
+    1e-4 of the FP64 batch; the FP64 batch against the FP64 oracle (structured
+    stepper) on the smallest instance over all 500 steps, to 1e-12."""
+    from oracle import schemes as S
+    wls = W.workload_batch(seed=4, count=64, steps=500)
+    f64, dts = run_batch(wls, "f64", 500)
+    f32, _ = run_batch(wls, "f32", 500)
+    errs = [energy_norm_rel(a, b) for a, b in zip(f32, f64)]
+    small = min(range(len(wls)), key=lambda i: wls[i].nx * wls[i].ny * wls[i].nz)
+    w = wls[small]
+    g = G.Grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    P = S.Problem(g, dts[small], eps_r_cell=w.eps_r)
+    ref, _, _ = S.run_fundamental(P, "fadi", w.fields, 500)
+    err_oracle = energy_norm_rel(f64[small], ref)
+    report("batch64_fadi", max_rel_err_f32_vs_f64=max(errs), median=float(np.median(errs)),
+           smallest=[w.nx, w.ny, w.nz], f64_vs_oracle=err_oracle)
+    assert max(errs) <= 1e-4
+    assert err_oracle <= 1e-12
