@@ -65,7 +65,9 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * dt_CFL = 1 / (c0 * sqrt(1/dx^2 + 1/dy^2 [+ 1/dz^2 when nz > 1])),
  * c0 = 299792458 m/s.  tune[] are kernel-shape overrides (0 = automatic):
  * tune[0] nodes per thread of the non-persistent y/z-line kernels (8, 16 or
- * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel. */
+ * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel;
+ * tune[1] bit 1 set: per-node (inhomogeneous-media) coefficients even when
+ * fdtd_set_material receives a uniform eps (needed by fdtd_adj_create). */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of
@@ -195,7 +197,7 @@ int fdtd_reset_stats(fdtd_t* h);
 int fdtd_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, double eps_r, double mu_r,
                         int precision, const void* const* fields, double* out_device, void* stream);
 
-/* Batches (workload 4: many independent cavities).  A batch steps a set of
+/* Batches of many independent cavities.  A batch steps a set of
  * handles together: each procedure of the scheme runs as one launch per
  * (line direction, segment length) group covering every grid of the batch,
  * and one step of the whole batch is captured once as a CUDA graph and
@@ -210,6 +212,41 @@ int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps);
 int fdtd_batch_destroy(fdtd_batch_t* b);
 /* Kernel launches per batch step (for accounting); valid after a step. */
 int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
+
+/* Reverse mode: gradient of a probe-energy objective of FADI with respect to
+ * the per-cell permittivity.
+ *
+ * Objective: J = sum over steps n = 1..nsteps and over the probe samples of
+ * (E^n)^2, where E^n is the FADI output field after step n (w_B/2, Eq. 9 with
+ * Eqs. 8c-8d) and the probe samples are every interior Ex, Ey and Ez sample
+ * whose array index (i, j, k) lies in the cell block
+ * block = {i0, i1, j0, j1, k0, k1} (half-open ranges).  The gradient is the
+ * exact discrete adjoint of the stepper: each procedure's transpose runs in
+ * reverse order (transposed line solves with the procedure's own pivots,
+ * transposed stencil), and dJ/d eps is collected per E sample, then carried
+ * through the edge averaging of eps to the cells.  Checkpoints of the state
+ * are kept every checkpoint_every steps; the backward pass recomputes each
+ * segment from its checkpoint before running it in reverse.
+ *
+ * fdtd_adj_create: h must be a FADI handle with per-node media (eps set by
+ *   fdtd_set_material, non-uniform or tune[1] bit 1), fields and source set,
+ *   no probes, and not yet stepped (FDTD_ERR_UNSUPPORTED / FDTD_ERR_STATE
+ *   otherwise).  Device memory: about (6 nsteps/checkpoint_every +
+ *   6 checkpoint_every + 21) state arrays (fdtd_adj_memory gives the bytes);
+ *   FDTD_ERR_OOM when it does not fit.  The context borrows h, which must
+ *   outlive it.
+ * fdtd_adj_forward: runs the nsteps steps on h (h advances; its fields are
+ *   afterwards those of step nsteps) and returns J (FP64 sum).  Once only.
+ * fdtd_adj_backward: grad_eps_r[nz][ny][nx] (double; host or device) =
+ *   jbar * dJ/d eps_r per cell.  Requires the forward pass; may be repeated.
+ *   h's own state is not touched. */
+typedef struct fdtd_adj_s fdtd_adj_t;
+int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t checkpoint_every,
+                    fdtd_adj_t** out);
+int fdtd_adj_forward(fdtd_adj_t* a, double* objective);
+int fdtd_adj_backward(fdtd_adj_t* a, double jbar, double* grad_eps_r, int on_device);
+int fdtd_adj_memory(const fdtd_adj_t* a, int64_t* bytes);
+int fdtd_adj_destroy(fdtd_adj_t* a);
 
 /* Static description of an error code. */
 const char* fdtd_strerror(int code);

@@ -58,10 +58,11 @@ template <typename T>
 struct ProbeParams {
   const T* arr[kMaxProbes];
   long long at[kMaxProbes];
+  double sub[kMaxProbes];  // mode 1: subtracted from value (a source added after the solve)
   int n;
 };
 
-// mode 0: stash[p] = value;  mode 1: out[p][col] = (stash[p] + value)/2;
+// mode 0: stash[p] = value;  mode 1: out[p][col] = (stash[p] + value - sub[p])/2;
 // mode 2: out[p][col] = value.
 template <typename T>
 __global__ void probe_kernel(const ProbeParams<T> pp, double* stash, double* out, long long ld,
@@ -72,7 +73,7 @@ __global__ void probe_kernel(const ProbeParams<T> pp, double* stash, double* out
   if (mode == 0) {
     stash[q] = v;
   } else if (mode == 1) {
-    out[(long long)q * ld + col] = 0.5 * (stash[q] + v);
+    out[(long long)q * ld + col] = 0.5 * (stash[q] + v - pp.sub[q]);
   } else {
     out[(long long)q * ld + col] = v;
   }

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/fdtd.h"
+#include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "line_kernels.cuh"
 
@@ -862,13 +863,15 @@ int scheme_init(fdtd_t* h) {
 }
 
 template <typename T>
-int record_probes(fdtd_t* h, int mode) {
+int record_probes(fdtd_t* h, int mode, double post) {
   if (h->nprobes == 0) return FDTD_OK;
   fdtd::ProbeParams<T> pp;
   pp.n = h->nprobes;
+  const long long src_at = h->src_comp >= 0 ? elem_index(h, h->src_i, h->src_j, h->src_k) : -1;
   for (int q = 0; q < h->nprobes; ++q) {
     pp.arr[q] = (const T*)h->f[h->probe_comp[q]];
     pp.at[q] = h->probe_at[q];
+    pp.sub[q] = (h->probe_comp[q] == h->src_comp && h->probe_at[q] == src_at) ? post : 0.0;
   }
   h->launches++;
   fdtd::probe_kernel<T><<<1, 32, 0, h->stream>>>(pp, h->d_stash, h->d_probe, h->probe_cap, h->steps, mode);
@@ -876,8 +879,10 @@ int record_probes(fdtd_t* h, int mode) {
   return FDTD_OK;
 }
 
-int probes(fdtd_t* h, int mode) {
-  return h->prec == FDTD_F64 ? record_probes<double>(h, mode) : record_probes<float>(h, mode);
+// mode 1 (FADI, after B): post = the source just added after the B
+// subtraction, which the output w_B/2 does not contain
+int probes(fdtd_t* h, int mode, double post = 0.0) {
+  return h->prec == FDTD_F64 ? record_probes<double>(h, mode, post) : record_probes<float>(h, mode, post);
 }
 
 int ensure_probe_capacity(fdtd_t* h, long long need) {
@@ -916,7 +921,7 @@ int one_step(fdtd_t* h) {
       if ((rc = procedure(h, 0, 0.0, 0.5 * dt * f))) return rc;
       if ((rc = probes(h, 0))) return rc;
       if ((rc = procedure(h, 1, 0.0, 0.5 * dt * fn))) return rc;
-      if ((rc = probes(h, 1))) return rc;
+      if ((rc = probes(h, 1, 0.5 * dt * fn))) return rc;
       break;
     }
     case FDTD_FLOD:
@@ -1244,8 +1249,9 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   for (int c = 0; c < 3; ++c)
     if (h->eps_node[c]) { cudaFree(h->eps_node[c]); h->eps_node[c] = nullptr; }
   h->mu_r = m0;
-  h->per_node = !e_uniform;
-  h->eps_r = e_uniform ? e0 : 1.0;
+  // tune[1] bit 1 keeps per-node coefficients even for a uniform eps
+  h->per_node = !e_uniform || (h->desc.tune[1] & 2) != 0;
+  h->eps_r = h->per_node ? 1.0 : e0;
   int rc = FDTD_OK;
   if (h->per_node) {
     for (int c = 0; c < 3; ++c) {
@@ -1714,6 +1720,462 @@ int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step) {
   long long c = 0;
   for (int k = 0; k < n; ++k) c += (long long)b->groups[seq[k]].size();
   *per_step = c;
+  return FDTD_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Reverse mode: gradient of a probe-energy objective with respect to eps
+// ===========================================================================
+namespace {
+
+struct AdjCfg {
+  bool ok = false;
+  int lanes = 16, L = 16;
+};
+
+template <typename T>
+const void* adj_strided_fn(int lanes, int L) {
+  if (lanes == 32 && L == 8) return (const void*)fdtd::adj_strided_kernel<T, 32, 8>;
+  if (lanes == 32 && L == 16) return (const void*)fdtd::adj_strided_kernel<T, 32, 16>;
+  if (lanes == 16 && L == 8) return (const void*)fdtd::adj_strided_kernel<T, 16, 8>;
+  if (lanes == 16 && L == 16) return (const void*)fdtd::adj_strided_kernel<T, 16, 16>;
+  if (lanes == 16 && L == 32) return (const void*)fdtd::adj_strided_kernel<T, 16, 32>;
+  if (lanes == 8 && L == 32) return (const void*)fdtd::adj_strided_kernel<T, 8, 32>;
+  return nullptr;
+}
+
+// Segment layout of the adjoint y/z kernel for lines of N cells (the
+// per-node solve builds its carries on the fly, so any L works).
+template <typename T>
+AdjCfg adj_strided_cfg(int N) {
+  static const int c32[][2] = {{32, 16}, {32, 8}, {16, 16}, {16, 32}, {8, 32}};
+  static const int c64[][2] = {{16, 16}, {16, 8}, {16, 32}, {8, 32}, {8, 32}};
+  const int(*cand)[2] = sizeof(T) == 8 ? c64 : c32;
+  AdjCfg best;
+  for (int q = 0; q < 5; ++q) {
+    const int lanes = cand[q][0], L = cand[q][1];
+    const int P = segments(N, L, lanes);
+    if (P > 32) continue;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, adj_strided_fn<T>(lanes, L)) != cudaSuccess) continue;
+    if (P * lanes > a.maxThreadsPerBlock) continue;
+    best.ok = true;
+    best.lanes = lanes;
+    best.L = L;
+    return best;
+  }
+  return best;
+}
+
+template <typename T, int LANES, int L>
+void launch_adj_strided_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p,
+                          const fdtd::AdjExtra<T>& x) {
+  const int P = segments(g.N, L, LANES);
+  dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
+  const size_t smem = 6 * (size_t)(P | 1) * LANES * sizeof(T);
+  fdtd::adj_strided_kernel<T, LANES, L><<<grid, P * LANES, smem, h->stream>>>(p, x);
+}
+
+template <typename T, int L>
+void launch_adj_rows_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p,
+                       const fdtd::AdjExtra<T>& x) {
+  const int wpb = 8;
+  const unsigned blocks = (unsigned)((g.n_lines() + wpb - 1) / wpb);
+  fdtd::adj_rows_kernel<T, L><<<blocks, wpb * 32, 0, h->stream>>>(p, x);
+}
+
+}  // namespace
+
+struct fdtd_adj_s {
+  fdtd_t* h = nullptr;
+  long long nsteps = 0;
+  int every = 1, nseg = 0;
+  int nprobe = 0;
+  long long* d_probe_at = nullptr;
+  int* d_probe_comp = nullptr;
+  double* d_stash = nullptr;
+  double* d_acc = nullptr;
+  double* d_cell = nullptr;
+  void* ckpt = nullptr;     // nseg x 6 state arrays
+  void* tape = nullptr;     // (2 every + 1) x 3 E arrays of one segment
+  void* work[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* lam[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* grad[3] = {nullptr, nullptr, nullptr};
+  void* u0h[3] = {nullptr, nullptr, nullptr};   // initial physical H
+  AdjCfg cfg[2];
+  long long src_at = -1;
+  double eps_src = 0;
+  bool forward_done = false;
+  double objective = 0;
+  long long bytes = 0;
+};
+
+namespace {
+
+void* arr_at(void* base, long long idx, const fdtd_t* h) {
+  return (char*)base + (size_t)idx * (size_t)h->count * h->esize;
+}
+
+template <typename T>
+fdtd::ProbeSet<T> probe_set(const fdtd_adj_t* a) {
+  fdtd::ProbeSet<T> ps;
+  ps.at = a->d_probe_at;
+  ps.comp = a->d_probe_comp;
+  ps.n = a->nprobe;
+  ps.src_at = a->src_at;
+  ps.src_comp = a->h->src_comp;
+  return ps;
+}
+
+int copy_arrays(fdtd_t* h, void* const* dst, void* const* src, int first, int n) {
+  for (int c = first; c < first + n; ++c)
+    CK(cudaMemcpyAsync(dst[c], src[c], (size_t)h->count * h->esize, cudaMemcpyDeviceToDevice, h->stream));
+  return FDTD_OK;
+}
+
+// One FADI step of the forward model on `st` (in place), optionally with the
+// objective's probe accumulation; E states after A and after B copied to
+// tape slots ta, tb when given.
+template <typename T>
+int adj_forward_step(fdtd_adj_t* a, void* const* st, long long n, bool objective, void* const* ta,
+                     void* const* tb) {
+  fdtd_t* h = a->h;
+  const double post_a = 0.5 * h->dt * source_value(h, n);
+  const double post_b = 0.5 * h->dt * source_value(h, n + 1);
+  int rc = run_procedure<T>(h, 0, 1.0, 1.0, -1.0, 1.0, st, st);
+  if (rc) return rc;
+  if (h->src_comp >= 0 && (rc = add_point(h, st[h->src_comp], post_a))) return rc;
+  if (ta && (rc = copy_arrays(h, ta, st, 0, 3))) return rc;
+  if (objective && a->nprobe) {
+    fdtd::probe_energy_kernel<T><<<1, 256, 0, h->stream>>>(probe_set<T>(a), (const T*)st[0], (const T*)st[1],
+                                                           (const T*)st[2], a->d_stash, a->d_acc, 0);
+    CK(cudaGetLastError());
+  }
+  if ((rc = run_procedure<T>(h, 1, 1.0, 1.0, -1.0, 1.0, st, st))) return rc;
+  if (objective && a->nprobe) {
+    fdtd::probe_energy_kernel<T><<<1, 256, 0, h->stream>>>(probe_set<T>(a), (const T*)st[0], (const T*)st[1],
+                                                           (const T*)st[2], a->d_stash, a->d_acc, 1);
+    CK(cudaGetLastError());
+  }
+  if (h->src_comp >= 0 && (rc = add_point(h, st[h->src_comp], post_b))) return rc;
+  if (tb && (rc = copy_arrays(h, tb, st, 0, 3))) return rc;
+  return FDTD_OK;
+}
+
+// The three adjoint pair launches of procedure `slot` on lam (in place).
+template <typename T>
+int adj_procedure(fdtd_adj_t* a, int slot, void* const* eb, void* const* ea, double post) {
+  fdtd_t* h = a->h;
+  const ProcCoef& P = h->proc[slot];
+  for (int q = 0; q < 3; ++q) {
+    const PairGeom& g = h->geom[P.op][q];
+    if (g.empty()) continue;
+    fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, a->lam, a->lam);
+    const T ks = p.ks, kd = p.kd;
+    p.ks = -kd;  // transposed couplings
+    p.kd = -ks;
+    fdtd::AdjExtra<T> x;
+    x.e_before = (const T*)eb[g.ec];
+    x.e_after = (const T*)ea[g.ec];
+    x.grad = a->grad[g.ec];
+    x.inv_h = 1.0 / P.h;
+    x.src_at = (g.ec == h->src_comp) ? a->src_at : -1;
+    x.src_post = post;
+    h->launches++;
+    if (g.rows) {
+      switch (pick_rows_L(g.N)) {
+        case 1: launch_adj_rows_L<T, 1>(h, g, p, x); break;
+        case 2: launch_adj_rows_L<T, 2>(h, g, p, x); break;
+        case 4: launch_adj_rows_L<T, 4>(h, g, p, x); break;
+        case 8: launch_adj_rows_L<T, 8>(h, g, p, x); break;
+        case 12: launch_adj_rows_L<T, 12>(h, g, p, x); break;
+        case 16: launch_adj_rows_L<T, 16>(h, g, p, x); break;
+        case 24: launch_adj_rows_L<T, 24>(h, g, p, x); break;
+        case 32: launch_adj_rows_L<T, 32>(h, g, p, x); break;
+        default: return FDTD_ERR_UNSUPPORTED;
+      }
+    } else {
+      const AdjCfg& c = a->cfg[g.axis == AX_Y ? 0 : 1];
+      if (!c.ok) return FDTD_ERR_UNSUPPORTED;
+      if (c.lanes == 32 && c.L == 8) launch_adj_strided_L<T, 32, 8>(h, g, p, x);
+      else if (c.lanes == 32 && c.L == 16) launch_adj_strided_L<T, 32, 16>(h, g, p, x);
+      else if (c.lanes == 16 && c.L == 8) launch_adj_strided_L<T, 16, 8>(h, g, p, x);
+      else if (c.lanes == 16 && c.L == 16) launch_adj_strided_L<T, 16, 16>(h, g, p, x);
+      else if (c.lanes == 16 && c.L == 32) launch_adj_strided_L<T, 16, 32>(h, g, p, x);
+      else if (c.lanes == 8 && c.L == 32) launch_adj_strided_L<T, 8, 32>(h, g, p, x);
+      else return FDTD_ERR_UNSUPPORTED;
+    }
+    CK(cudaGetLastError());
+  }
+  return FDTD_OK;
+}
+
+template <typename T>
+int adj_point_term(fdtd_adj_t* a, double post) {
+  fdtd_t* h = a->h;
+  if (h->src_comp < 0 || post == 0.0) return FDTD_OK;
+  // post = (h/2) f with f proportional to 1/eps at the source sample
+  fdtd::grad_point_kernel<T><<<1, 32, 0, h->stream>>>(a->grad[h->src_comp], (const T*)a->lam[h->src_comp],
+                                                      a->src_at, -post / a->eps_src);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+template <typename T>
+int adj_inject(fdtd_adj_t* a, void* const* eb, void* const* ea, double post, double jbar) {
+  fdtd_t* h = a->h;
+  if (!a->nprobe) return FDTD_OK;
+  const unsigned blocks = (unsigned)std::min(1024, (a->nprobe + 255) / 256);
+  fdtd::probe_inject_kernel<T><<<blocks, 256, 0, h->stream>>>(
+      probe_set<T>(a), (T*)a->lam[0], (T*)a->lam[1], (T*)a->lam[2], (const T*)eb[0], (const T*)eb[1],
+      (const T*)eb[2], (const T*)ea[0], (const T*)ea[1], (const T*)ea[2], post, jbar);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+template <typename T>
+int adj_forward_t(fdtd_adj_t* a) {
+  fdtd_t* h = a->h;
+  int rc;
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(a->u0h[c], h->f[3 + c], (size_t)h->count * h->esize, cudaMemcpyDeviceToDevice, h->stream));
+  if ((rc = scheme_init(h))) return rc;
+  CK(cudaMemsetAsync(a->d_acc, 0, sizeof(double), h->stream));
+  for (long long n = 0; n < a->nsteps; ++n) {
+    if (n % a->every == 0) {
+      void* dst[6];
+      for (int c = 0; c < 6; ++c) dst[c] = arr_at(a->ckpt, (n / a->every) * 6 + c, h);
+      if ((rc = copy_arrays(h, dst, h->f, 0, 6))) return rc;
+    }
+    if ((rc = adj_forward_step<T>(a, h->f, n, true, nullptr, nullptr))) return rc;
+    h->steps++;
+  }
+  h->output_valid = false;
+  CK(cudaMemcpyAsync(&a->objective, a->d_acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+template <typename T>
+int adj_backward_t(fdtd_adj_t* a, double jbar) {
+  fdtd_t* h = a->h;
+  int rc;
+  const size_t bytes = (size_t)h->count * h->esize;
+  for (int c = 0; c < 6; ++c) CK(cudaMemsetAsync(a->lam[c], 0, bytes, h->stream));
+  for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(a->grad[c], 0, sizeof(double) * h->count, h->stream));
+  auto slot = [&](int s, void** out) {
+    for (int c = 0; c < 3; ++c) out[c] = arr_at(a->tape, (long long)s * 3 + c, h);
+  };
+  for (int seg = a->nseg - 1; seg >= 0; --seg) {
+    const long long n0 = (long long)seg * a->every;
+    const long long n1 = std::min(n0 + a->every, a->nsteps);
+    void* src[6];
+    for (int c = 0; c < 6; ++c) src[c] = arr_at(a->ckpt, (long long)seg * 6 + c, h);
+    if ((rc = copy_arrays(h, a->work, src, 0, 6))) return rc;
+    void* t0[3];
+    slot(0, t0);
+    if ((rc = copy_arrays(h, t0, a->work, 0, 3))) return rc;
+    for (long long n = n0; n < n1; ++n) {
+      const int m = (int)(n - n0);
+      void *ta[3], *tb[3];
+      slot(2 * m + 1, ta);
+      slot(2 * m + 2, tb);
+      if ((rc = adj_forward_step<T>(a, a->work, n, false, ta, tb))) return rc;
+    }
+    for (long long n = n1 - 1; n >= n0; --n) {
+      const int m = (int)(n - n0);
+      void *e0[3], *e1[3], *e2[3];
+      slot(2 * m, e0);
+      slot(2 * m + 1, e1);
+      slot(2 * m + 2, e2);
+      const double post_a = 0.5 * h->dt * source_value(h, n);
+      const double post_b = 0.5 * h->dt * source_value(h, n + 1);
+      // B procedure of step n, with the objective's w_B term
+      if ((rc = adj_point_term<T>(a, post_b))) return rc;
+      if ((rc = adj_inject<T>(a, e1, e2, post_b, jbar))) return rc;
+      if ((rc = adj_procedure<T>(a, 1, e1, e2, post_b))) return rc;
+      if ((rc = adj_inject<T>(a, e1, e2, post_b, jbar))) return rc;
+      // A procedure of step n
+      if ((rc = adj_point_term<T>(a, post_a))) return rc;
+      if ((rc = adj_procedure<T>(a, 0, e0, e1, post_a))) return rc;
+    }
+  }
+  // input initialization v0 = u0 + (dt/2) B u0 + (dt/2) f
+  if ((rc = adj_point_term<T>(a, 0.5 * h->dt * source_value(h, 0)))) return rc;
+  const ProcCoef& P = h->proc[1];
+  for (int q = 0; q < 3; ++q) {
+    const PairGeom& g = h->geom[P.op][q];
+    if (g.empty() || g.N < 2) continue;
+    void* in[6] = {nullptr, nullptr, nullptr, a->u0h[0], a->u0h[1], a->u0h[2]};
+    in[g.ec] = a->lam[g.ec];
+    fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, in, in);
+    const double sgn = -1.0;  // B pairs
+    const double coef = -0.5 * h->dt * sgn / (spacing(h, g.axis) * kEps0 * kEps0);
+    const long long total = g.n_lines() * (g.N - 1);
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 32));
+    fdtd::init_grad_kernel<T><<<blocks, 256, 0, h->stream>>>(p, g.rows ? 1 : 0, (const T*)a->lam[g.ec],
+                                                             h->eps_node[g.ec], a->grad[g.ec], coef);
+    CK(cudaGetLastError());
+  }
+  const long long cells = (long long)h->nx * h->ny * h->nz;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((cells + 255) / 256, 152LL * 32));
+  fdtd::cell_grad_kernel<<<blocks, 256, 0, h->stream>>>(a->grad[0], a->grad[1], a->grad[2], h->nx, h->ny, h->nz,
+                                                        h->pitch, h->plane, kEps0, a->d_cell);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+void adj_free(fdtd_adj_t* a) {
+  void* ptrs[] = {a->d_probe_at, a->d_probe_comp, a->d_stash, a->d_acc, a->d_cell, a->ckpt, a->tape};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int c = 0; c < 6; ++c) {
+    if (a->work[c]) cudaFree(a->work[c]);
+    if (a->lam[c]) cudaFree(a->lam[c]);
+  }
+  for (int c = 0; c < 3; ++c) {
+    if (a->grad[c]) cudaFree(a->grad[c]);
+    if (a->u0h[c]) cudaFree(a->u0h[c]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t checkpoint_every,
+                    fdtd_adj_t** out) {
+  if (!h || !block || !out || nsteps < 1 || checkpoint_every < 1) return FDTD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->scheme != FDTD_FADI || !h->per_node) return FDTD_ERR_UNSUPPORTED;
+  if (!h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
+  if (h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
+  const int i0 = block[0], i1 = block[1], j0 = block[2], j1 = block[3], k0 = block[4], k1 = block[5];
+  if (i0 < 0 || j0 < 0 || k0 < 0 || i1 < i0 || j1 < j0 || k1 < k0 || i1 > h->nx + 1 || j1 > h->ny + 1 ||
+      k1 > h->nz + 1)
+    return FDTD_ERR_INVALID_ARG;
+  fdtd_adj_t* a = new (std::nothrow) fdtd_adj_s();
+  if (!a) return FDTD_ERR_OOM;
+  a->h = h;
+  a->nsteps = nsteps;
+  a->every = checkpoint_every;
+  a->nseg = (int)((nsteps + checkpoint_every - 1) / checkpoint_every);
+  // probe samples: interior E samples whose index (i, j, k) lies in the block
+  std::vector<long long> at;
+  std::vector<int> comp;
+  for (int c = 0; c < 3; ++c) {
+    int sx, sy, sz;
+    comp_extent(c, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+    for (int k = k0; k < std::min(k1, sz); ++k)
+      for (int j = j0; j < std::min(j1, sy); ++j)
+        for (int i = i0; i < std::min(i1, sx); ++i) {
+          const bool wall_x = (c != EX) && (i == 0 || i == h->nx);
+          const bool wall_y = (c != EY) && (j == 0 || j == h->ny);
+          const bool wall_z = (c != EZ) && (k == 0 || k == h->nz);
+          if (wall_x || wall_y || wall_z) continue;
+          at.push_back(elem_index(h, i, j, k));
+          comp.push_back(c);
+        }
+  }
+  a->nprobe = (int)at.size();
+  if (h->src_comp >= 0) {
+    a->src_at = elem_index(h, h->src_i, h->src_j, h->src_k);
+    double er = 1.0;
+    if (cudaMemcpy(&er, h->eps_node[h->src_comp] + a->src_at, sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      delete a;
+      return FDTD_ERR_CUDA;
+    }
+    a->eps_src = kEps0 * er;
+  }
+  const size_t arr = (size_t)h->count * h->esize;
+  bool ok = true;
+  auto alloc = [&](void** p, size_t n) {
+    if (!ok) return;
+    if (cudaMalloc(p, n) != cudaSuccess) ok = false;
+    else a->bytes += (long long)n;
+  };
+  alloc((void**)&a->d_probe_at, sizeof(long long) * std::max<size_t>(1, at.size()));
+  alloc((void**)&a->d_probe_comp, sizeof(int) * std::max<size_t>(1, comp.size()));
+  alloc((void**)&a->d_stash, sizeof(double) * std::max<size_t>(1, at.size()));
+  alloc((void**)&a->d_acc, sizeof(double));
+  alloc((void**)&a->d_cell, sizeof(double) * (size_t)h->nx * h->ny * h->nz);
+  alloc(&a->ckpt, arr * 6 * (size_t)a->nseg);
+  alloc(&a->tape, arr * 3 * (size_t)(2 * checkpoint_every + 1));
+  for (int c = 0; c < 6; ++c) {
+    alloc(&a->work[c], arr);
+    alloc(&a->lam[c], arr);
+  }
+  for (int c = 0; c < 3; ++c) {
+    alloc((void**)&a->grad[c], sizeof(double) * h->count);
+    alloc(&a->u0h[c], arr);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    adj_free(a);
+    delete a;
+    return FDTD_ERR_OOM;
+  }
+  if (!at.empty() &&
+      (cudaMemcpy(a->d_probe_at, at.data(), sizeof(long long) * at.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(a->d_probe_comp, comp.data(), sizeof(int) * comp.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    adj_free(a);
+    delete a;
+    return FDTD_ERR_CUDA;
+  }
+  for (int ax = 0; ax < 2; ++ax) {
+    const int N = ax == 0 ? h->ny : h->nz;
+    a->cfg[ax] = h->prec == FDTD_F64 ? adj_strided_cfg<double>(N) : adj_strided_cfg<float>(N);
+    if (!a->cfg[ax].ok && N >= 2) {
+      adj_free(a);
+      delete a;
+      return FDTD_ERR_UNSUPPORTED;
+    }
+  }
+  *out = a;
+  return FDTD_OK;
+}
+
+int fdtd_adj_forward(fdtd_adj_t* a, double* objective) {
+  if (!a || !objective) return FDTD_ERR_INVALID_ARG;
+  fdtd_t* h = a->h;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (a->forward_done || !h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
+  int rc = h->prec == FDTD_F64 ? adj_forward_t<double>(a) : adj_forward_t<float>(a);
+  if (rc) return rc;
+  a->forward_done = true;
+  *objective = a->objective;
+  return FDTD_OK;
+}
+
+int fdtd_adj_backward(fdtd_adj_t* a, double jbar, double* grad_eps_r, int on_device) {
+  if (!a || !grad_eps_r || !std::isfinite(jbar)) return FDTD_ERR_INVALID_ARG;
+  fdtd_t* h = a->h;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (!a->forward_done) return FDTD_ERR_STATE;
+  int rc = h->prec == FDTD_F64 ? adj_backward_t<double>(a, jbar) : adj_backward_t<float>(a, jbar);
+  if (rc) return rc;
+  const size_t n = sizeof(double) * (size_t)h->nx * h->ny * h->nz;
+  CK(cudaMemcpyAsync(grad_eps_r, a->d_cell, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+int fdtd_adj_memory(const fdtd_adj_t* a, int64_t* bytes) {
+  if (!a || !bytes) return FDTD_ERR_INVALID_ARG;
+  *bytes = a->bytes;
+  return FDTD_OK;
+}
+
+int fdtd_adj_destroy(fdtd_adj_t* a) {
+  if (!a) return FDTD_OK;
+  cudaStreamSynchronize(a->h->stream);
+  adj_free(a);
+  delete a;
   return FDTD_OK;
 }
 

@@ -1,4 +1,4 @@
-"""Batched stepping of many independent cavities (workload 4 recipe at
+"""Batched stepping of many independent cavities (the 64-cavity recipe at
 reduced sizes): every grid against the FP64 oracle and against the same
 grid stepped on its own (the batch runs the same arithmetic: bit-identical)."""
 import numpy as np

@@ -44,7 +44,7 @@ def run_cavity(n, steps, prec, cfl=4.0, seed=2, scheme="fadi"):
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_cavity_128_fadi_1000_steps(prec):
-    """Workload 2: 128^3 PEC cavity, 1 mm, CFL 4, 8 seeded modes, 1000 FADI steps."""
+    """128^3 PEC cavity, 1 mm, CFL 4, 8 seeded modes, 1000 FADI steps."""
     out, ref, e0, e1 = run_cavity(128, 1000, prec)
     err = energy_norm_rel(out, ref)
     drift = abs(e1[1] / e0[1] - 1.0)
@@ -75,7 +75,7 @@ def test_cavity_128_flod_fss_f32(scheme):
 
 
 def run_blocks(n, steps, prec, scheme, seed=3):
-    """Workload 3: eps_r blocks in [1, 10], 0.5 mm cells, CFL 8, z dipole at the centre."""
+    """256^3-type dipole run: eps_r blocks in [1, 10], 0.5 mm cells, CFL 8, z dipole at the centre."""
     from paper_2011_14043_gb300 import Simulation
     d = 0.5e-3
     g = G.Grid(n, n, n, d, d, d)
@@ -93,7 +93,7 @@ def run_blocks(n, steps, prec, scheme, seed=3):
 
 @pytest.mark.parametrize("scheme", ["flod", "fss"])
 def test_blocks_256_f32_vs_f64(scheme):
-    """FP32 precision statement at the full workload-3 size: FP32 fields vs the
+    """FP32 precision statement at the full 256^3 eps-block dipole size: FP32 fields vs the
     FP64 path (itself pinned to the oracle to 1e-12 on the same recipe at
     reduced size in test_gpu_parity.py)."""
     f64 = run_blocks(256, 1000, "f64", scheme)
@@ -122,7 +122,7 @@ def run_batch(wls, prec, steps):
 
 
 def test_batch_64_cavities_500_steps():
-    """Workload 4 at full size: 64 seeded cavities of uneven sizes, CFL numbers
+    """The 64-cavity batch at full size: 64 seeded cavities of uneven sizes, CFL numbers
     and eps_r blocks, 500 FADI steps as one batch.  Every FP32 instance within
     1e-4 of the FP64 batch; the FP64 batch against the FP64 oracle (structured
     stepper) on the smallest instance over all 500 steps, to 1e-12."""

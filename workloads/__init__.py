@@ -56,7 +56,7 @@ def zero_fields(nx: int, ny: int, nz: int, dtype=np.float64) -> dict:
 
 
 # ---------------------------------------------------------------------------
-# Workload 1: 2-D (nz = 1) Gaussian Ez pulse
+# 2-D (nz = 1) Gaussian Ez pulse
 # ---------------------------------------------------------------------------
 
 def gaussian_ez_2d(nx: int, ny: int, sigma_cells: float, seed: int) -> dict:
@@ -268,3 +268,25 @@ def workload_batch(seed: int = 4, count: int = 64, steps: int = 500):
                             fields=mode_sum_fields(modes, nx, ny, nz), eps_r=eps,
                             extra={"modes": modes}))
     return out
+
+
+def workload_adjoint(seed: int = 5, n: int = 192, steps: int = 500, cfl: float = 4.0, region=(64, 128),
+                     checkpoint_every: int = 25) -> Workload:
+    """Differentiable FADI run: eps_r uniform in [1, 6] per cell inside the
+    central design cube [region)^3, 1 elsewhere; 1 mm cells; z-directed dipole
+    (10 GHz, 50% bandwidth modulated Gaussian) at the Ez sample (48, 96, 96);
+    objective = probe energy over the E samples of cells
+    [140, 144) x [94, 98) x [94, 98) over all steps.  Sample positions scale
+    with n / 192 for smaller test grids."""
+    rng = np.random.default_rng(seed)
+    d = 1e-3
+    eps = np.ones((n, n, n))
+    lo, hi = (region[0] * n) // 192, (region[1] * n) // 192
+    eps[lo:hi, lo:hi, lo:hi] = rng.uniform(1.0, 6.0, (hi - lo,) * 3)
+    s = lambda v: (v * n) // 192
+    block = (s(140), s(140) + max(1, s(4)), s(94), s(94) + max(1, s(4)), s(94), s(94) + max(1, s(4)))
+    return Workload(f"adjoint_{n}", n, n, n, d, d, d, cfl, steps, "fadi",
+                    fields=zero_fields(n, n, n), eps_r=eps,
+                    source={"comp": "ez", "i": s(48), "j": s(96), "k": s(96), "f0": 10e9, "frac_bw": 0.5},
+                    extra={"probe_block": block, "checkpoint_every": checkpoint_every,
+                           "region": (lo, hi)})
