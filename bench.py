@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", type=int, nargs=2, default=(0, 0), help="kernel-shape overrides (fdtd_desc.tune)")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-cavity batch measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args()
@@ -199,6 +200,58 @@ def run_e2e(args, prec, fields):
     return {"s": t1 - t0, "h2d": nbytes, "d2h": nbytes}
 
 
+def replica_throughput(local_ms: float, units_per_rank: float, ws: int, device: str):
+    """Replicas (one independent grid per rank, no exchange in the data path):
+    the job takes as long as its slowest rank, so the time is the MAX over
+    ranks and the value all ranks' units over that time."""
+    ms = local_ms
+    if ws > 1:
+        import torch
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * units_per_rank / (ms / 1e3)
+
+
+def adjoint_section(args):
+    """Gradient of the probe energy with respect to eps_r on the 192^3
+    differentiable run (eps_r in [1, 6] in the central 64^3, dipole, 4^3 probe
+    block, 500 steps, checkpoints every 25), FP32: forward (with checkpoints)
+    and adjoint (recomputation + transposed procedures) timed separately."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_14043_gb300.adjoint import ProbeEnergyProblem
+    wl = W.workload_adjoint()
+    n = wl.nx
+    c0 = 299792458.0
+    dt = wl.cfl / (c0 * math.sqrt(3.0 / wl.dx ** 2))
+    cur = W.dipole_current((np.arange(wl.steps + 1) + 0.5) * dt)
+    s = wl.source
+    prob = ProbeEnergyProblem(n, n, n, wl.dx, steps=wl.steps, probe_block=wl.extra["probe_block"], dt=dt,
+                              precision="f32", checkpoint_every=wl.extra["checkpoint_every"],
+                              source=(s["comp"], s["i"], s["j"], s["k"], cur))
+    from paper_2011_14043_gb300.adjoint import AdjointRun
+    run = AdjointRun(prob, wl.eps_r)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = run.forward()
+    t1 = time.perf_counter()
+    out = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    run.backward(1.0, out=out)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    mem = run.memory_bytes()
+    run.close()
+    cs = n ** 3 * wl.steps
+    return {"workload": f"FADI {n}^3, eps_r U[1,6] in the central 64^3, z dipole, 4^3 probe block, "
+                        f"{wl.steps} steps, checkpoints every {wl.extra['checkpoint_every']}",
+            "dtype": "f32", "objective": J, "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "forward_cell_steps_per_s": cs / (t1 - t0), "gradient_cell_steps_per_s": cs / (t2 - t0),
+            "backward_over_forward": (t2 - t1) / (t1 - t0), "device_bytes": mem,
+            "timing": "host wall clock around the synchronous C-ABI calls"}
+
+
 def batch_rel_err(a: dict, b: dict) -> float:
     """Relative L2 in the vacuum energy norm (E weighted by eps0, H by mu0)."""
     import numpy as np
@@ -344,12 +397,7 @@ def main():
     time.sleep(0.4)
     r32 = run_gpu(args, "f32", fields)
     clocks = sampler.stop()
-    ms = r32["ms"]
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * cells * args.steps / (ms / 1e3)
+    ms, value = replica_throughput(r32["ms"], cells * args.steps, ws, "cuda")
 
     # dominant kernel roofline from live CUDA events in the timed region
     st = r32["stats"]
@@ -396,6 +444,8 @@ def main():
                        "d2h_bytes_per_step": e["d2h"] / args.steps}
     if not args.no_batch:
         line["batch"] = batch_section(args)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_section(args)
     if rank == 0 and not args.no_cpu_baseline:
         v, s = cpu_baseline(n, steps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -193,3 +193,24 @@ def test_tma_path_bit_identical_to_direct_path(prec, dims):
     b, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 3, tune=(16, 1))
     for c in G.COMPS:
         assert np.array_equal(a[c], b[c]), c
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fadi_probes_at_and_beside_the_source(prec):
+    """FADI probe series (the output field w_B/2 of every step) at the source
+    sample itself and next to it, against the oracle's output field."""
+    nx, ny, nz = 20, 18, 16
+    d = 1e-3
+    g = G.Grid(nx, ny, nz, d, d, d)
+    dt = 5.0 * g.dt_cfl()
+    eps = W.eps_blocks(9, nx, ny, nz, 1.0, 4.0)
+    steps = 40
+    cur = W.dipole_current((np.arange(steps + 1) + 0.5) * dt * 15)
+    src = ("ez", 10, 9, 8, cur)
+    P = oracle_problem(nx, ny, nz, d, d, d, dt, eps=eps, source=src)
+    probes = [("ez", 10, 9, 8), ("ez", 11, 9, 8), ("ex", 10, 9, 8)]
+    _, _, ref = S.run_fadi(P, W.zero_fields(nx, ny, nz), steps, probes=probes)
+    _, series, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "fadi", prec, W.zero_fields(nx, ny, nz), steps,
+                              eps=eps, source=src, probes=probes)
+    for a, b in zip(series, ref):
+        assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b)), (np.max(np.abs(a - b)), np.max(np.abs(b)))
