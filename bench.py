@@ -288,11 +288,12 @@ def run_batch(wls, prec, steps, warmup, want_fields):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     per_step = b.launches_per_step()
+    cfg = b.config()
     fields = [s.get_fields() for s in sims] if want_fields else None
     b.close()
     for s in sims:
         s.close()
-    return {"ms": ms, "launches_per_step": per_step, "fields": fields}
+    return {"ms": ms, "launches_per_step": per_step, "fields": fields, "config": cfg}
 
 
 def batch_section(args):
@@ -309,6 +310,7 @@ def batch_section(args):
            "workload": f"{len(wls)} seeded PEC cavities, 1 mm cells, sizes 32..160 x 32..96 x 32..128, "
                        f"CFL U[2,10], eps_r blocks U[1,4], 8 seeded modes, FADI",
            "gpu_launches": r32["launches_per_step"] * args.batch_steps,
+           "launch_shape": r32["config"],
            "hbm_frac_step": 96.0 * cells * args.batch_steps / (r32["ms"] / 1e3) / 1e9
            / measured_peaks()[0]["hbm_gbs"]}
     if not args.no_fp64:

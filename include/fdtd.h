@@ -199,9 +199,10 @@ int fdtd_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
 
 /* Batches of many independent cavities.  A batch steps a set of
  * handles together: each procedure of the scheme runs as one launch per
- * (line direction, segment length) group covering every grid of the batch,
- * and one step of the whole batch is captured once as a CUDA graph and
- * replayed.  Every grid runs exactly the arithmetic of its own handle's
+ * launch-shape group (line direction, lanes, segment length and count)
+ * covering every grid of the batch; the groups of one procedure run
+ * concurrently on parallel graph branches, and one step of the whole batch
+ * is captured once as a CUDA graph and replayed.  Every grid runs exactly the arithmetic of its own handle's
  * fdtd_step.  Handles must share scheme, precision and stream, be distinct,
  * and have no source or probe (FDTD_ERR_UNSUPPORTED); they stay owned by
  * the caller, stay usable for set/get/energy, and must outlive the batch.
@@ -212,6 +213,20 @@ int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps);
 int fdtd_batch_destroy(fdtd_batch_t* b);
 /* Kernel launches per batch step (for accounting); valid after a step. */
 int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
+/* Launch shape of the batch: cfg = {y lanes, y L, z lanes, z L, x warps per
+ * block} (lanes: lines per tile of the y/z kernels; L: nodes per thread,
+ * which sets the carry-chain depth ceil(N/L); grids with uniform media keep
+ * the L of their coefficient tables).  By default the first fdtd_batch_step
+ * tunes it: each candidate shape is timed on the batch's own data (out of
+ * place, into the handles' scratch arrays, so the state is untouched) and
+ * the fastest kept; results are cached per device, precision, scheme and
+ * grid list for the process, and appended to the file named by the
+ * environment variable FDTD_TUNE_CACHE when set.  tune_ms (may be NULL)
+ * receives the tuned time of each direction's launches for one step.
+ * fdtd_batch_set_config fixes the shape (FDTD_ERR_INVALID_ARG for a shape
+ * that is not built); cfg = NULL returns to tuning. */
+int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[5], double tune_ms[3]);
+int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg);
 
 /* Reverse mode: gradient of a probe-energy objective of FADI with respect to
  * the per-cell permittivity.

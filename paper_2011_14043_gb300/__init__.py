@@ -253,6 +253,23 @@ class Batch:
     def step(self, n: int = 1):
         check(lib().fdtd_batch_step(self._h, int(n)), "fdtd_batch_step")
 
+    def config(self) -> dict:
+        """Launch shape in use (tuned on the first step unless fixed) and the
+        tuned per-direction times of one step's launches (ms)."""
+        cfg = (ctypes.c_int32 * 5)()
+        ms = (ctypes.c_double * 3)()
+        check(lib().fdtd_batch_get_config(self._h, cfg, ms), "fdtd_batch_get_config")
+        return {"y": (cfg[0], cfg[1]), "z": (cfg[2], cfg[3]), "x_warps_per_block": cfg[4],
+                "tuned_ms": {"y": ms[0], "z": ms[1], "x": ms[2]}}
+
+    def set_config(self, y=None, z=None, x_warps_per_block=8):
+        """Fix the launch shape: y, z = (lanes, L); None for both returns to tuning."""
+        if y is None and z is None:
+            check(lib().fdtd_batch_set_config(self._h, None), "fdtd_batch_set_config")
+            return
+        cfg = (ctypes.c_int32 * 5)(y[0], y[1], z[0], z[1], x_warps_per_block)
+        check(lib().fdtd_batch_set_config(self._h, cfg), "fdtd_batch_set_config")
+
     def launches_per_step(self) -> int:
         v = ctypes.c_int64()
         check(lib().fdtd_batch_launches(self._h, ctypes.byref(v)), "fdtd_batch_launches")

@@ -19,6 +19,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -1441,11 +1444,23 @@ int fdtd_reset_stats(fdtd_t* h) {
 // ===========================================================================
 namespace {
 
-constexpr int kBatchLanes = 16;
+// Shape of the batched launches, per line direction:
+//   y, z lines: lanes (lines per tile) and L (nodes per thread; the carry
+//               chains then span P = ceil(N / L) segments);
+//   x lines:    warps (lines) per block.
+// Grids with per-node media take any L; grids with uniform media keep the L
+// their coefficient tables were built for.
+struct BatchCfg {
+  int lanes[2] = {16, 16};
+  int L[2] = {16, 16};
+  int wpb = 8;
+};
+
+constexpr int kBatchBranches = 4;  // concurrent graph branches per procedure
 
 struct BatchGroup {
   int kind = 0;             // 0 lines along y, 1 along z, 2 along x
-  int L = 16, P = 1;        // segment length; segments per block (strided)
+  int L = 16, P = 1, lanes = 16, wpb = 8;
   int ngrids = 0;
   long long nitems = 0;     // tiles (strided) or lines (x)
   void* d_params = nullptr; // PairParams<T>[ngrids]
@@ -1459,24 +1474,32 @@ struct fdtd_batch_s {
   int prec = 0, scheme = 0;
   cudaStream_t stream = nullptr;       // the handles' stream
   cudaStream_t run = nullptr;          // capture/replay stream (never the legacy default)
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t branch[kBatchBranches] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+  cudaEvent_t ev_join[kBatchBranches] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<BatchGroup> groups[2];           // per procedure slot
   std::vector<const void*> bound;              // state pointers the tables were built for
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  long long launches = 0;
+  BatchCfg cfg;
+  bool tuned = false;       // cfg chosen (by the tuner, the cache or the caller)
+  bool autotune = true;
+  double tune_ms[3] = {0, 0, 0};  // per direction: time of the chosen shape (both procedures)
 };
 
 namespace {
 
+void free_group_list(std::vector<BatchGroup>& gs) {
+  for (auto& g : gs) {
+    if (g.d_params) cudaFree(g.d_params);
+    if (g.d_index) cudaFree(g.d_index);
+  }
+  gs.clear();
+}
+
 void free_groups(fdtd_batch_t* b) {
-  for (auto& gs : b->groups)
-    for (auto& g : gs) {
-      if (g.d_params) cudaFree(g.d_params);
-      if (g.d_index) cudaFree(g.d_index);
-    }
-  b->groups[0].clear();
-  b->groups[1].clear();
+  free_group_list(b->groups[0]);
+  free_group_list(b->groups[1]);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
@@ -1493,11 +1516,50 @@ void free_groups(fdtd_batch_t* b) {
   } while (0)
 
 template <typename T>
-int build_groups_t(fdtd_batch_t* b) {
-  free_groups(b);
+const void* batch_strided_fn(int lanes, int L) {
+  if (lanes == 32 && L == 8) return (const void*)fdtd::proc_strided_batch_kernel<T, 32, 8>;
+  if (lanes == 32 && L == 16) return (const void*)fdtd::proc_strided_batch_kernel<T, 32, 16>;
+  if (lanes == 16 && L == 8) return (const void*)fdtd::proc_strided_batch_kernel<T, 16, 8>;
+  if (lanes == 16 && L == 16) return (const void*)fdtd::proc_strided_batch_kernel<T, 16, 16>;
+  if (lanes == 16 && L == 32) return (const void*)fdtd::proc_strided_batch_kernel<T, 16, 32>;
+  if (lanes == 8 && L == 16) return (const void*)fdtd::proc_strided_batch_kernel<T, 8, 16>;
+  if (lanes == 8 && L == 32) return (const void*)fdtd::proc_strided_batch_kernel<T, 8, 32>;
+  return nullptr;
+}
+
+template <typename T>
+bool batch_shape_ok(int N, int lanes, int L) {
+  const void* fn = batch_strided_fn<T>(lanes, L);
+  if (!fn) return false;
+  const int P = segments(N, L, lanes);
+  if (P > 32) return false;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return false;
+  return P * lanes <= a.maxThreadsPerBlock;
+}
+
+// L of one grid's y/z lines under cfg: the configured L when it fits, else
+// the next longer one; uniform media keep the L of their tables.
+template <typename T>
+int batch_grid_L(const fdtd_t* h, int kind, int N, int lanes, int Lcfg) {
+  if (!h->per_node) return batch_shape_ok<T>(N, lanes, h->strided_cfg[kind].L) ? h->strided_cfg[kind].L : -1;
+  for (int L : {8, 16, 32})
+    if (L >= Lcfg && batch_shape_ok<T>(N, lanes, L)) return L;
+  return -1;
+}
+
+// Group every pair of every grid by launch shape.  `only_kind` >= 0 keeps
+// one direction (tuning); `scratch_out` writes to the handles' scratch arrays
+// instead of in place (tuning runs leave the state untouched).
+template <typename T>
+int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup> (&out)[2], int only_kind,
+                   bool scratch_out) {
   for (int slot = 0; slot < 2; ++slot) {
-    // key: (kind, L) -> grids in the group
-    std::vector<std::pair<std::pair<int, int>, std::vector<std::pair<int, int>>>> keys;  // (kind,L) -> (grid, q)
+    struct Key {
+      int kind, L, lanes, P;
+      std::vector<std::pair<int, int>> members;  // (grid, pair)
+    };
+    std::vector<Key> keys;
     for (int gi = 0; gi < (int)b->h.size(); ++gi) {
       fdtd_t* h = b->h[gi];
       const ProcCoef& P = h->proc[slot];
@@ -1505,115 +1567,290 @@ int build_groups_t(fdtd_batch_t* b) {
         const PairGeom& g = h->geom[P.op][q];
         if (g.empty()) continue;
         const int kind = g.rows ? 2 : (g.axis == AX_Y ? 0 : 1);
-        const int L = g.rows ? pick_rows_L(g.N) : h->strided_cfg[kind].L;
+        if (only_kind >= 0 && kind != only_kind) continue;
+        int L, lanes = 0, Pseg = 0;
+        if (g.rows) {
+          L = pick_rows_L(g.N);
+        } else {
+          lanes = cfg.lanes[kind];
+          L = batch_grid_L<T>(h, kind, g.N, lanes, cfg.L[kind]);
+          if (L < 0) return FDTD_ERR_UNSUPPORTED;
+          Pseg = segments(g.N, L, lanes);
+        }
         bool found = false;
         for (auto& k : keys)
-          if (k.first.first == kind && k.first.second == L) {
-            k.second.push_back({gi, q});
+          if (k.kind == kind && k.L == L && k.lanes == lanes && k.P == Pseg) {
+            k.members.push_back({gi, q});
             found = true;
+            break;
           }
-        if (!found) keys.push_back({{kind, L}, {{gi, q}}});
+        if (!found) keys.push_back({kind, L, lanes, Pseg, {{gi, q}}});
       }
     }
     for (auto& k : keys) {
       BatchGroup bg;
-      bg.kind = k.first.first;
-      bg.L = k.first.second;
-      bg.ngrids = (int)k.second.size();
+      bg.kind = k.kind;
+      bg.L = k.L;
+      bg.lanes = k.lanes;
+      bg.P = k.P;
+      bg.wpb = cfg.wpb;
+      bg.ngrids = (int)k.members.size();
       std::vector<fdtd::PairParams<T>> params;
       std::vector<fdtd::BatchTile> tiles;
       std::vector<long long> starts(1, 0);
-      int Pmax = 1;
       for (int m = 0; m < bg.ngrids; ++m) {
-        fdtd_t* h = b->h[k.second[m].first];
-        const int q = k.second[m].second;
+        fdtd_t* h = b->h[k.members[m].first];
+        const int q = k.members[m].second;
         const ProcCoef& P = h->proc[slot];
         const PairGeom& g = h->geom[P.op][q];
-        params.push_back(make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, h->f));
+        if (scratch_out) {
+          int rc = ensure_scratch(h);
+          if (rc) return rc;
+        }
+        params.push_back(make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, scratch_out ? h->scratch : h->f));
         if (bg.kind == 2) {
           starts.push_back(starts.back() + g.n_lines());
         } else {
-          Pmax = std::max(Pmax, segments(g.N, bg.L, kBatchLanes));
-          const int tx = (g.lane_hi + kBatchLanes - 1) / kBatchLanes;
+          const int tx = (g.lane_hi + bg.lanes - 1) / bg.lanes;
           for (int o = 0; o < g.n_o; ++o)
-            for (int bx = 0; bx < tx; ++bx) tiles.push_back({m, bx * kBatchLanes, g.o_lo + o, 0});
+            for (int bx = 0; bx < tx; ++bx) tiles.push_back({m, bx * bg.lanes, g.o_lo + o, 0});
         }
       }
-      bg.P = Pmax;
-      if (Pmax > 32) return FDTD_ERR_UNSUPPORTED;
       BCK(cudaMalloc(&bg.d_params, sizeof(fdtd::PairParams<T>) * params.size()));
+      out[slot].push_back(bg);  // freed with the list from here on
       BCK(cudaMemcpy(bg.d_params, params.data(), sizeof(fdtd::PairParams<T>) * params.size(),
                      cudaMemcpyHostToDevice));
       if (bg.kind == 2) {
         bg.nitems = starts.back();
         BCK(cudaMalloc(&bg.d_index, sizeof(long long) * starts.size()));
+        out[slot].back() = bg;
         BCK(cudaMemcpy(bg.d_index, starts.data(), sizeof(long long) * starts.size(), cudaMemcpyHostToDevice));
       } else {
         bg.nitems = (long long)tiles.size();
         BCK(cudaMalloc(&bg.d_index, sizeof(fdtd::BatchTile) * tiles.size()));
+        out[slot].back() = bg;
         BCK(cudaMemcpy(bg.d_index, tiles.data(), sizeof(fdtd::BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
       }
-      b->groups[slot].push_back(bg);
     }
   }
   return FDTD_OK;
 }
 
-template <typename T, int L>
-void launch_batch_strided_L(fdtd_batch_t* b, const BatchGroup& g) {
-  const int threads = g.P * kBatchLanes;
-  const size_t smem = 6 * (size_t)(g.P | 1) * kBatchLanes * sizeof(T);
-  fdtd::proc_strided_batch_kernel<T, kBatchLanes, L><<<(unsigned)g.nitems, threads, smem, b->run>>>(
+template <typename T, int LANES, int L>
+void launch_batch_strided_LL(const BatchGroup& g, cudaStream_t s) {
+  const int threads = g.P * LANES;
+  const size_t smem = 6 * (size_t)(g.P | 1) * LANES * sizeof(T);
+  fdtd::proc_strided_batch_kernel<T, LANES, L><<<(unsigned)g.nitems, threads, smem, s>>>(
       (const fdtd::PairParams<T>*)g.d_params, (const fdtd::BatchTile*)g.d_index);
 }
 
 template <typename T, int L>
-void launch_batch_rows_L(fdtd_batch_t* b, const BatchGroup& g) {
-  const int wpb = 8;
-  fdtd::proc_rows_batch_kernel<T, L><<<(unsigned)((g.nitems + wpb - 1) / wpb), wpb * 32, 0, b->run>>>(
+void launch_batch_rows_L(const BatchGroup& g, cudaStream_t s) {
+  const int wpb = g.wpb;
+  fdtd::proc_rows_batch_kernel<T, L><<<(unsigned)((g.nitems + wpb - 1) / wpb), wpb * 32, 0, s>>>(
       (const fdtd::PairParams<T>*)g.d_params, (const long long*)g.d_index, g.ngrids);
 }
 
 template <typename T>
-int launch_batch_group(fdtd_batch_t* b, const BatchGroup& g) {
-  b->launches++;
+int launch_batch_group(const BatchGroup& g, cudaStream_t s) {
   if (g.kind == 2) {
     switch (g.L) {
-      case 1: launch_batch_rows_L<T, 1>(b, g); break;
-      case 2: launch_batch_rows_L<T, 2>(b, g); break;
-      case 4: launch_batch_rows_L<T, 4>(b, g); break;
-      case 8: launch_batch_rows_L<T, 8>(b, g); break;
-      case 12: launch_batch_rows_L<T, 12>(b, g); break;
-      case 16: launch_batch_rows_L<T, 16>(b, g); break;
-      case 24: launch_batch_rows_L<T, 24>(b, g); break;
-      case 32: launch_batch_rows_L<T, 32>(b, g); break;
+      case 1: launch_batch_rows_L<T, 1>(g, s); break;
+      case 2: launch_batch_rows_L<T, 2>(g, s); break;
+      case 4: launch_batch_rows_L<T, 4>(g, s); break;
+      case 8: launch_batch_rows_L<T, 8>(g, s); break;
+      case 12: launch_batch_rows_L<T, 12>(g, s); break;
+      case 16: launch_batch_rows_L<T, 16>(g, s); break;
+      case 24: launch_batch_rows_L<T, 24>(g, s); break;
+      case 32: launch_batch_rows_L<T, 32>(g, s); break;
       default: return FDTD_ERR_UNSUPPORTED;
     }
   } else {
-    switch (g.L) {
-      case 8: launch_batch_strided_L<T, 8>(b, g); break;
-      case 16: launch_batch_strided_L<T, 16>(b, g); break;
-      case 32: launch_batch_strided_L<T, 32>(b, g); break;
-      default: return FDTD_ERR_UNSUPPORTED;
-    }
+    const int lanes = g.lanes, L = g.L;
+    if (lanes == 32 && L == 8) launch_batch_strided_LL<T, 32, 8>(g, s);
+    else if (lanes == 32 && L == 16) launch_batch_strided_LL<T, 32, 16>(g, s);
+    else if (lanes == 16 && L == 8) launch_batch_strided_LL<T, 16, 8>(g, s);
+    else if (lanes == 16 && L == 16) launch_batch_strided_LL<T, 16, 16>(g, s);
+    else if (lanes == 16 && L == 32) launch_batch_strided_LL<T, 16, 32>(g, s);
+    else if (lanes == 8 && L == 16) launch_batch_strided_LL<T, 8, 16>(g, s);
+    else if (lanes == 8 && L == 32) launch_batch_strided_LL<T, 8, 32>(g, s);
+    else return FDTD_ERR_UNSUPPORTED;
   }
   BCK(cudaGetLastError());
   return FDTD_OK;
 }
 
-// One time step of every grid: the scheme's procedure sequence, each
-// procedure one launch per group.
+// One time step of every grid: the scheme's procedure sequence.  The groups
+// of one procedure write disjoint arrays, so they fork onto parallel
+// branches; the next procedure starts when all of them have joined.
 template <typename T>
 int batch_one_step(fdtd_batch_t* b) {
   static const int seq_fss[3] = {0, 1, 0};
   static const int seq_two[2] = {0, 1};
   const int* seq = b->scheme == FDTD_FSS ? seq_fss : seq_two;
   const int n = b->scheme == FDTD_FSS ? 3 : 2;
-  for (int k = 0; k < n; ++k)
-    for (const auto& g : b->groups[seq[k]]) {
-      int rc = launch_batch_group<T>(b, g);
+  for (int k = 0; k < n; ++k) {
+    const auto& gs = b->groups[seq[k]];
+    const int nb = std::min<int>(kBatchBranches, (int)gs.size());
+    BCK(cudaEventRecord(b->ev_fork, b->run));
+    for (int i = 0; i < nb; ++i) BCK(cudaStreamWaitEvent(b->branch[i], b->ev_fork, 0));
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+      int rc = launch_batch_group<T>(gs[gi], b->branch[gi % nb]);
       if (rc) return rc;
     }
+    for (int i = 0; i < nb; ++i) {
+      BCK(cudaEventRecord(b->ev_join[i], b->branch[i]));
+      BCK(cudaStreamWaitEvent(b->run, b->ev_join[i], 0));
+    }
+  }
+  return FDTD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuner: per direction, time the candidate launch shapes on the batch's own
+// data (both procedures, out of place into scratch) and keep the fastest.
+// Results are cached per (device, precision, scheme, grid list) for the
+// process, and in the file named by FDTD_TUNE_CACHE when that is set.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, BatchCfg> g_tune_cache;
+
+std::string batch_key(const fdtd_batch_t* b) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "?";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  std::string s = name + "|p" + std::to_string(b->prec) + "|s" + std::to_string(b->scheme);
+  for (const fdtd_t* h : b->h)
+    s += "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz) +
+         (h->per_node ? "n" : "u");
+  // long keys are folded to a hash (FNV-1a) after the device and precision
+  if (s.size() > 200) {
+    uint64_t x = 1469598103934665603ull;
+    for (char c : s) x = (x ^ (unsigned char)c) * 1099511628211ull;
+    char buf[32];
+    snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)x);
+    s = name + "|p" + std::to_string(b->prec) + "|n" + std::to_string(b->h.size()) + "|" + buf;
+  }
+  return s;
+}
+
+void tune_cache_load() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = getenv("FDTD_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[512];
+  BatchCfg c;
+  while (fscanf(f, "%511s %d %d %d %d %d", key, &c.lanes[0], &c.L[0], &c.lanes[1], &c.L[1], &c.wpb) == 6)
+    g_tune_cache[key] = c;
+  fclose(f);
+}
+
+void tune_cache_store(const std::string& key, const BatchCfg& c) {
+  g_tune_cache[key] = c;
+  const char* path = getenv("FDTD_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.lanes[0], c.L[0], c.lanes[1], c.L[1], c.wpb);
+  fclose(f);
+}
+
+// Time of one direction's launches for both procedures under cfg (ms, best
+// of `reps`), or a negative value when the shape does not apply.
+template <typename T>
+double time_direction(fdtd_batch_t* b, const BatchCfg& cfg, int kind, int reps) {
+  std::vector<BatchGroup> gs[2];
+  if (build_groups_t<T>(b, cfg, gs, kind, true) != FDTD_OK) {
+    free_group_list(gs[0]);
+    free_group_list(gs[1]);
+    cudaGetLastError();
+    return -1.0;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  bool ok = true;
+  for (int r = 0; r < reps + 1 && ok; ++r) {  // the first pass warms up
+    cudaEventRecord(e0, b->run);
+    for (int slot = 0; slot < 2 && ok; ++slot)
+      for (const auto& g : gs[slot])
+        if (launch_batch_group<T>(g, b->run) != FDTD_OK) ok = false;
+    cudaEventRecord(e1, b->run);
+    if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_group_list(gs[0]);
+  free_group_list(gs[1]);
+  return ok ? best : -1.0;
+}
+
+template <typename T>
+int batch_tune_t(fdtd_batch_t* b) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_cache_load();
+  const std::string key = batch_key(b);
+  auto it = g_tune_cache.find(key);
+  if (it != g_tune_cache.end()) {
+    b->cfg = it->second;
+    b->tuned = true;
+    return FDTD_OK;
+  }
+  // the tuning runs read the state and write scratch: order after the
+  // handles' earlier work
+  BCK(cudaEventRecord(b->ev_in, b->stream));
+  BCK(cudaStreamWaitEvent(b->run, b->ev_in, 0));
+  static const int c32[][2] = {{16, 8}, {16, 16}, {16, 32}, {32, 8}, {32, 16}};
+  static const int c64[][2] = {{16, 8}, {16, 16}, {16, 32}, {8, 16}, {8, 32}};
+  const int(*cand)[2] = sizeof(T) == 8 ? c64 : c32;
+  BatchCfg cfg = b->cfg;
+  for (int kind = 0; kind < 2; ++kind) {
+    double best = -1;
+    BatchCfg pick = cfg;
+    for (int q = 0; q < 5; ++q) {
+      BatchCfg t = cfg;
+      t.lanes[kind] = cand[q][0];
+      t.L[kind] = cand[q][1];
+      const double ms = time_direction<T>(b, t, kind, 3);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        pick = t;
+      }
+    }
+    if (best < 0) return FDTD_ERR_UNSUPPORTED;
+    cfg = pick;
+    b->tune_ms[kind] = best;
+  }
+  {
+    double best = -1;
+    int pick = cfg.wpb;
+    for (int wpb : {4, 8, 16}) {
+      BatchCfg t = cfg;
+      t.wpb = wpb;
+      const double ms = time_direction<T>(b, t, 2, 3);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        pick = wpb;
+      }
+    }
+    cfg.wpb = pick;
+    b->tune_ms[2] = best < 0 ? 0 : best;
+  }
+  BCK(cudaGetLastError());
+  b->cfg = cfg;
+  b->tuned = true;
+  tune_cache_store(key, cfg);
   return FDTD_OK;
 }
 
@@ -1622,12 +1859,25 @@ int batch_prepare(fdtd_batch_t* b) {
     int rc = scheme_init(h);
     if (rc) return rc;
   }
+  if (!b->tuned) {
+    if (b->autotune) {
+      int rc = b->prec == FDTD_F64 ? batch_tune_t<double>(b) : batch_tune_t<float>(b);
+      if (rc) return rc;
+    }
+    b->tuned = true;
+    b->bound.clear();
+  }
   std::vector<const void*> ptrs;
   for (fdtd_t* h : b->h)
     for (int c = 0; c < 6; ++c) ptrs.push_back(h->f[c]);
   if (ptrs == b->bound && !b->groups[0].empty()) return FDTD_OK;
-  int rc = b->prec == FDTD_F64 ? build_groups_t<double>(b) : build_groups_t<float>(b);
-  if (rc) return rc;
+  free_groups(b);
+  int rc = b->prec == FDTD_F64 ? build_groups_t<double>(b, b->cfg, b->groups, -1, false)
+                               : build_groups_t<float>(b, b->cfg, b->groups, -1, false);
+  if (rc) {
+    free_groups(b);
+    return rc;
+  }
   b->bound = ptrs;
   return FDTD_OK;
 }
@@ -1655,11 +1905,19 @@ int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batc
   b->prec = handles[0]->prec;
   b->scheme = handles[0]->scheme;
   b->stream = (cudaStream_t)stream;
-  if (cudaStreamCreateWithFlags(&b->run, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&b->run, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < kBatchBranches && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     fdtd_batch_destroy(b);
     return FDTD_ERR_CUDA;
+  }
+  if (b->prec == FDTD_F64) {
+    b->cfg.lanes[0] = b->cfg.lanes[1] = 16;
   }
   *out = b;
   return FDTD_OK;
@@ -1672,6 +1930,11 @@ int fdtd_batch_destroy(fdtd_batch_t* b) {
   free_groups(b);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int i = 0; i < kBatchBranches; ++i) {
+    if (b->branch[i]) cudaStreamDestroy(b->branch[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
   if (b->run) cudaStreamDestroy(b->run);
   delete b;
   return FDTD_OK;
@@ -1720,6 +1983,45 @@ int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step) {
   long long c = 0;
   for (int k = 0; k < n; ++k) c += (long long)b->groups[seq[k]].size();
   *per_step = c;
+  return FDTD_OK;
+}
+
+int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[5], double tune_ms[3]) {
+  if (!b || !cfg) return FDTD_ERR_INVALID_ARG;
+  cfg[0] = b->cfg.lanes[0];
+  cfg[1] = b->cfg.L[0];
+  cfg[2] = b->cfg.lanes[1];
+  cfg[3] = b->cfg.L[1];
+  cfg[4] = b->cfg.wpb;
+  if (tune_ms)
+    for (int k = 0; k < 3; ++k) tune_ms[k] = b->tune_ms[k];
+  return FDTD_OK;
+}
+
+int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg) {
+  if (!b) return FDTD_ERR_INVALID_ARG;
+  if (!cfg) {  // back to automatic: tune again before the next step
+    b->autotune = true;
+    b->tuned = false;
+    free_groups(b);
+    b->bound.clear();
+    return FDTD_OK;
+  }
+  for (int k = 0; k < 2; ++k) {
+    const int lanes = cfg[2 * k], L = cfg[2 * k + 1];
+    const void* fn = b->prec == FDTD_F64 ? batch_strided_fn<double>(lanes, L) : batch_strided_fn<float>(lanes, L);
+    if (!fn) return FDTD_ERR_INVALID_ARG;
+  }
+  if (cfg[4] != 4 && cfg[4] != 8 && cfg[4] != 16) return FDTD_ERR_INVALID_ARG;
+  b->cfg.lanes[0] = cfg[0];
+  b->cfg.L[0] = cfg[1];
+  b->cfg.lanes[1] = cfg[2];
+  b->cfg.L[1] = cfg[3];
+  b->cfg.wpb = cfg[4];
+  b->autotune = false;
+  b->tuned = true;
+  free_groups(b);
+  b->bound.clear();
   return FDTD_OK;
 }
 

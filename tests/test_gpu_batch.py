@@ -1,6 +1,8 @@
 """Batched stepping of many independent cavities (the 64-cavity recipe at
-reduced sizes): every grid against the FP64 oracle and against the same
-grid stepped on its own (the batch runs the same arithmetic: bit-identical)."""
+reduced sizes): every grid against the FP64 oracle, and, with the batch's
+segment length pinned to the handles' own, against the same grid stepped on
+its own (the same arithmetic: bit-identical).  Tuned and fixed launch
+shapes against the oracle; the tuner's cache file."""
 import numpy as np
 import pytest
 
@@ -46,6 +48,7 @@ def test_batch_matches_oracle_and_single(scheme, prec):
     steps = 9
     sims = [make_sim(sp, scheme, prec) for sp in specs]
     batch = Batch(sims)
+    batch.set_config(y=(16, 16), z=(16, 16))   # the handles' own segment length
     batch.step(4)
     batch.step(steps - 4)            # a second call replays the same graph
     assert batch.launches_per_step() >= 2
@@ -74,3 +77,58 @@ def test_batch_rejects_mixed_and_sourced():
         Batch([a, c])
     with pytest.raises(FdtdError):
         Batch([a, a])
+
+
+def run_against_oracle(specs, scheme, prec, steps, configure):
+    from paper_2011_14043_gb300 import Batch
+    sims = [make_sim(sp, scheme, prec) for sp in specs]
+    batch = Batch(sims)
+    configure(batch)
+    batch.step(steps)
+    cfg = batch.config()
+    for sp, sim in zip(specs, sims):
+        nx, ny, nz, cfl, eps, u0 = sp
+        g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+        ref, _, _ = S.run_fundamental(S.Problem(g, sim.dt, eps_r_cell=eps), scheme, u0, steps)
+        assert energy_norm_rel(sim.get_fields(), ref) <= TOL[prec], cfg
+    batch.close()
+    return cfg
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_tuned_batch_matches_oracle(prec):
+    specs = small_batch(77, 6)
+    cfg = run_against_oracle(specs, "fadi", prec, 7, lambda b: None)
+    assert cfg["y"][1] in (8, 16, 32) and cfg["z"][1] in (8, 16, 32)
+    assert cfg["x_warps_per_block"] in (4, 8, 16)
+
+
+@pytest.mark.parametrize("prec,shape", [("f32", (32, 8)), ("f32", (16, 32)), ("f32", (32, 16)),
+                                        ("f64", (8, 32)), ("f64", (16, 8)), ("f64", (8, 16))])
+def test_fixed_batch_shapes_match_oracle(prec, shape):
+    specs = small_batch(91, 5)
+    cfg = run_against_oracle(specs, "flod", prec, 6, lambda b: b.set_config(y=shape, z=shape, x_warps_per_block=4))
+    assert cfg["y"] == shape and cfg["z"] == shape
+
+
+def test_tuner_cache_file(tmp_path, monkeypatch):
+    from paper_2011_14043_gb300 import Batch, FdtdError
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("FDTD_TUNE_CACHE", str(path))
+    specs = small_batch(123, 3)
+    sims = [make_sim(sp, "fadi", "f32") for sp in specs]
+    b1 = Batch(sims)
+    b1.step(1)
+    cfg1 = b1.config()
+    b1.close()
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split()[1:] == [str(v) for v in (*cfg1["y"], *cfg1["z"],
+                                                                       cfg1["x_warps_per_block"])]
+    sims2 = [make_sim(sp, "fadi", "f32") for sp in specs]
+    b2 = Batch(sims2)
+    b2.step(1)
+    assert b2.config()["y"] == cfg1["y"] and b2.config()["z"] == cfg1["z"]
+    assert len(path.read_text().splitlines()) == 1     # served from the cache
+    with pytest.raises(FdtdError):
+        b2.set_config(y=(24, 16), z=(16, 16))
+    b2.close()
