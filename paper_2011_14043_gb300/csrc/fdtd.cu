@@ -100,6 +100,7 @@ struct fdtd_s {
   int tmap_bn[6][2] = {{0}};
   ProcCoef proc[3];  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing)
   bool per_node = false;
+  bool shape_tuned = false;   // per-node y/z launch shapes chosen by timing
   double eps_r = 1.0, mu_r = 1.0;          // uniform media
   double* eps_node[3] = {nullptr, nullptr, nullptr};  // per-node eps_r at E samples (device)
   std::vector<double> eps_host[3];  // the same on the host, only while coefficients are built
@@ -132,6 +133,8 @@ struct fdtd_s {
 };
 
 namespace {
+
+int single_tune(fdtd_t* h);
 
 int cuda_fail(fdtd_t* h, cudaError_t e) {
   if (e == cudaSuccess) return FDTD_OK;
@@ -1255,6 +1258,7 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   // tune[1] bit 1 keeps per-node coefficients even for a uniform eps
   h->per_node = !e_uniform || (h->desc.tune[1] & 2) != 0;
   h->eps_r = h->per_node ? 1.0 : e0;
+  h->shape_tuned = false;
   int rc = FDTD_OK;
   if (h->per_node) {
     for (int c = 0; c < 3; ++c) {
@@ -1368,6 +1372,10 @@ int fdtd_step(fdtd_t* h, int64_t nsteps) {
   if (nsteps == 0) return FDTD_OK;
   int rc = scheme_init(h);
   if (rc) return rc;
+  if (h->per_node && !h->shape_tuned && h->desc.tune[0] == 0) {
+    if ((rc = single_tune(h))) return rc;
+  }
+  h->shape_tuned = true;
   if ((rc = ensure_probe_capacity(h, h->steps + nsteps))) return rc;
   for (int64_t q = 0; q < nsteps; ++q)
     if ((rc = one_step(h))) return rc;
@@ -1715,13 +1723,10 @@ int batch_one_step(fdtd_batch_t* b) {
 std::mutex g_tune_mu;
 std::map<std::string, BatchCfg> g_tune_cache;
 
+std::string device_name();
+
 std::string batch_key(const fdtd_batch_t* b) {
-  int dev = 0;
-  cudaDeviceProp prop;
-  std::string name = "?";
-  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
-  for (char& c : name)
-    if (c == ' ' || c == '\t') c = '_';
+  const std::string name = device_name();
   std::string s = name + "|p" + std::to_string(b->prec) + "|s" + std::to_string(b->scheme);
   for (const fdtd_t* h : b->h)
     s += "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz) +
@@ -1881,6 +1886,110 @@ int batch_prepare(fdtd_batch_t* b) {
   b->bound = ptrs;
   return FDTD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Single handles with per-node media: their y/z kernels take any (lanes, L)
+// (the per-node solve has no L-dependent tables).  At the first step each
+// candidate is timed on the handle's own data (both procedures, out of
+// place into scratch) and the fastest kept; cached per (device, precision,
+// scheme, grid) for the process.
+// ---------------------------------------------------------------------------
+std::map<std::string, std::pair<StridedCfg, StridedCfg>> g_single_cache;
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "?";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  return name;
+}
+
+template <typename T>
+bool strided_ok(int N, bool pn, int lanes, int L) {
+  const void* fn = strided_fn_rt<T>(pn, lanes, L);
+  if (!fn) return false;
+  const int P = segments(N, L, lanes);
+  if (P > 32) return false;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return false;
+  return P * lanes <= a.maxThreadsPerBlock;
+}
+
+template <typename T>
+double time_axis(fdtd_t* h, int ax, const StridedCfg& c, int reps) {
+  if (ensure_scratch(h) != FDTD_OK) return -1.0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.0;
+  }
+  double best = 1e30;
+  bool ok = true;
+  for (int r = 0; r < reps + 1 && ok; ++r) {  // the first pass warms up
+    cudaEventRecord(e0, h->stream);
+    for (int slot = 0; slot < 2; ++slot) {
+      const ProcCoef& P = h->proc[slot];
+      for (int q = 0; q < 3; ++q) {
+        const PairGeom& g = h->geom[P.op][q];
+        if (g.empty() || g.rows || (g.axis == AX_Y ? 0 : 1) != ax) continue;
+        fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, h->scratch);
+        launch_strided<T>(h, g, p, true, c.lanes, c.L);
+      }
+    }
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) ok = false;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ok ? best : -1.0;
+}
+
+template <typename T>
+int single_tune_t(fdtd_t* h) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const std::string key = device_name() + "|p" + std::to_string(h->prec) + "|s" + std::to_string(h->scheme) +
+                          "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz);
+  auto it = g_single_cache.find(key);
+  if (it != g_single_cache.end()) {
+    h->strided_cfg[0] = it->second.first;
+    h->strided_cfg[1] = it->second.second;
+    return FDTD_OK;
+  }
+  static const int c32[][2] = {{32, 8}, {32, 16}, {16, 8}, {16, 16}, {16, 32}};
+  static const int c64[][2] = {{16, 8}, {16, 16}, {8, 16}, {8, 32}, {16, 32}};
+  const int(*cand)[2] = sizeof(T) == 8 ? c64 : c32;
+  for (int ax = 0; ax < 2; ++ax) {
+    const int N = ax == 0 ? h->ny : h->nz;
+    if (N < 2) continue;
+    double best = -1;
+    StridedCfg pick = h->strided_cfg[ax];
+    for (int q = 0; q < 5; ++q) {
+      if (!strided_ok<T>(N, true, cand[q][0], cand[q][1])) continue;
+      StridedCfg c;
+      c.ok = true;
+      c.lanes = cand[q][0];
+      c.L = cand[q][1];
+      const double ms = time_axis<T>(h, ax, c, 3);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        pick = c;
+      }
+    }
+    h->strided_cfg[ax] = pick;
+  }
+  h->output_valid = false;  // scratch was written
+  CK(cudaGetLastError());
+  g_single_cache[key] = {h->strided_cfg[0], h->strided_cfg[1]};
+  return FDTD_OK;
+}
+
+int single_tune(fdtd_t* h) { return h->prec == FDTD_F64 ? single_tune_t<double>(h) : single_tune_t<float>(h); }
 
 }  // namespace
 
@@ -2168,12 +2277,13 @@ int adj_forward_step(fdtd_adj_t* a, void* const* st, long long n, bool objective
 
 // The three adjoint pair launches of procedure `slot` on lam (in place).
 template <typename T>
-int adj_procedure(fdtd_adj_t* a, int slot, void* const* eb, void* const* ea, double post) {
+int adj_procedure(fdtd_adj_t* a, int slot, void* const* eb, void* const* ea, double post, int only_axis = -1) {
   fdtd_t* h = a->h;
   const ProcCoef& P = h->proc[slot];
   for (int q = 0; q < 3; ++q) {
     const PairGeom& g = h->geom[P.op][q];
     if (g.empty()) continue;
+    if (only_axis >= 0 && (g.rows || (g.axis == AX_Y ? 0 : 1) != only_axis)) continue;
     fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, a->lam, a->lam);
     const T ks = p.ks, kd = p.kd;
     p.ks = -kd;  // transposed couplings
@@ -2237,6 +2347,70 @@ int adj_inject(fdtd_adj_t* a, void* const* eb, void* const* ea, double post, dou
   return FDTD_OK;
 }
 
+// Launch shape of the adjoint y/z kernels: every feasible candidate timed
+// on the context's own (zeroed) adjoint arrays, both procedures.
+std::map<std::string, std::pair<AdjCfg, AdjCfg>> g_adj_cache;
+
+template <typename T>
+int adj_tune_t(fdtd_adj_t* a) {
+  fdtd_t* h = a->h;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const std::string key = device_name() + "|p" + std::to_string(h->prec) + "|" + std::to_string(h->nx) + "x" +
+                          std::to_string(h->ny) + "x" + std::to_string(h->nz);
+  auto it = g_adj_cache.find(key);
+  if (it != g_adj_cache.end()) {
+    a->cfg[0] = it->second.first;
+    a->cfg[1] = it->second.second;
+    return FDTD_OK;
+  }
+  const size_t bytes = (size_t)h->count * h->esize;
+  for (int c = 0; c < 6; ++c) CK(cudaMemsetAsync(a->lam[c], 0, bytes, h->stream));
+  for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(a->grad[c], 0, sizeof(double) * h->count, h->stream));
+  static const int c32[][2] = {{32, 8}, {32, 16}, {16, 8}, {16, 16}, {16, 32}};
+  static const int c64[][2] = {{16, 8}, {16, 16}, {16, 32}, {8, 32}, {16, 16}};
+  const int(*cand)[2] = sizeof(T) == 8 ? c64 : c32;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int ax = 0; ax < 2; ++ax) {
+    const int N = ax == 0 ? h->ny : h->nz;
+    if (N < 2) continue;
+    double best = -1;
+    AdjCfg pick = a->cfg[ax];
+    for (int q = 0; q < 5; ++q) {
+      const int lanes = cand[q][0], L = cand[q][1];
+      const int P = segments(N, L, lanes);
+      cudaFuncAttributes fa;
+      if (P > 32 || cudaFuncGetAttributes(&fa, adj_strided_fn<T>(lanes, L)) != cudaSuccess ||
+          P * lanes > fa.maxThreadsPerBlock)
+        continue;
+      a->cfg[ax] = {true, lanes, L};
+      double ms_best = 1e30;
+      bool ok = true;
+      for (int r = 0; r < 4 && ok; ++r) {
+        cudaEventRecord(e0, h->stream);
+        for (int slot = 0; slot < 2 && ok; ++slot)
+          if (adj_procedure<T>(a, slot, h->f, h->f, 0.0, ax) != FDTD_OK) ok = false;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) ms_best = std::min(ms_best, (double)ms);
+      }
+      if (ok && (best < 0 || ms_best < best)) {
+        best = ms_best;
+        pick = a->cfg[ax];
+      }
+    }
+    a->cfg[ax] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  g_adj_cache[key] = {a->cfg[0], a->cfg[1]};
+  return FDTD_OK;
+}
+
 template <typename T>
 int adj_forward_t(fdtd_adj_t* a) {
   fdtd_t* h = a->h;
@@ -2244,6 +2418,10 @@ int adj_forward_t(fdtd_adj_t* a) {
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpyAsync(a->u0h[c], h->f[3 + c], (size_t)h->count * h->esize, cudaMemcpyDeviceToDevice, h->stream));
   if ((rc = scheme_init(h))) return rc;
+  // launch shapes: forward (as fdtd_step would choose them) and adjoint
+  if (!h->shape_tuned && h->desc.tune[0] == 0 && (rc = single_tune(h))) return rc;
+  h->shape_tuned = true;
+  if ((rc = adj_tune_t<T>(a))) return rc;
   CK(cudaMemsetAsync(a->d_acc, 0, sizeof(double), h->stream));
   for (long long n = 0; n < a->nsteps; ++n) {
     if (n % a->every == 0) {

@@ -214,3 +214,19 @@ def test_fadi_probes_at_and_beside_the_source(prec):
                               eps=eps, source=src, probes=probes)
     for a, b in zip(series, ref):
         assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b)), (np.max(np.abs(a - b)), np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_tuned_per_node_shapes_match_oracle(prec):
+    """Per-node handles time their y/z launch shapes at the first step; the
+    tuned run (any shape) and every fixed segment length give the oracle's answer."""
+    nx, ny, nz = 30, 70, 45
+    d = 1e-3
+    g = G.Grid(nx, ny, nz, d, d, d)
+    dt = 6.0 * g.dt_cfl()
+    eps = W.eps_blocks(17, nx, ny, nz, 1.0, 6.0)
+    u0 = random_fields(nx, ny, nz, seed=17)
+    ref, _, _ = S.run_fundamental(S.Problem(g, dt, eps_r_cell=eps), "fss", u0, 5)
+    for tune in ((0, 0), (8, 0), (16, 0), (32, 0)):
+        out, _, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "fss", prec, u0, 5, eps=eps, tune=tune)
+        check(out, ref, prec)
