@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tune", type=int, nargs=2, default=(0, 0), help="kernel-shape overrides (fdtd_desc.tune)")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-cavity batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
+    ap.add_argument("--suite", action="store_true",
+                    help="print throughput of every workload recipe (one JSON line each) instead of the bench line")
     ap.add_argument("--adjoint-n", type=int, default=192, help="cells per axis of the gradient run")
     ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--adjoint-every", type=int, default=25, help="checkpoint spacing of the gradient run")
@@ -384,8 +386,81 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def suite(args):
+    """Throughput of every workload recipe at its full size (one JSON line
+    each; not the bench line): GPU FP32 and FP64 cell-steps/s with CUDA events
+    after warm-up, and the FP64 oracle on one host core over a short sample."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_14043_gb300 import Simulation
+    import oracle.grid as G
+    import oracle.schemes as S
+
+    def gpu(nx, ny, nz, d, scheme, prec, cfl, fields, eps=None, src=None, steps=50, warm=5):
+        sim = Simulation(nx, ny, nz, d, scheme=scheme, precision=prec, cfl=cfl)
+        if eps is not None:
+            sim.set_material(eps)
+        if src is not None:
+            sim.set_source(*src)
+        sim.set_fields(fields)
+        sim.step(warm)
+        sim.synchronize()
+        stream = torch.cuda.ExternalStream(sim._stream.value) if sim._stream.value else torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sim.close()
+        return nx * ny * nz * steps / (ms / 1e3)
+
+    def cpu(nx, ny, nz, d, scheme, cfl, fields, eps=None, steps=2):
+        g = G.Grid(nx, ny, nz, d, d, d)
+        P = S.Problem(g, cfl * g.dt_cfl(), eps_r_cell=eps)
+        u = S.fadi_init(P, fields) if scheme == "fadi" else {c: fields[c].copy() for c in G.COMPS}
+        step = {"fadi": S.fadi_step, "flod": S.flod_step, "fss": S.fss_step}[scheme]
+        t0 = time.perf_counter()
+        for k in range(steps):
+            u = step(P, u, k)
+        return nx * ny * nz * steps / (time.perf_counter() - t0)
+
+    out = []
+    w = W.workload_2d_gaussian()
+    out.append({"workload": "2-D TM FADI 64x64, CFL 5", "f64": gpu(64, 64, 1, 1e-3, "fadi", "f64", 5.0, w.fields,
+                                                                  steps=200),
+                "f32": gpu(64, 64, 1, 1e-3, "fadi", "f32", 5.0, w.fields, steps=200),
+                "oracle_1core": cpu(64, 64, 1, 1e-3, "fadi", 5.0, w.fields, steps=20)})
+    w = W.workload_cavity_modes()
+    out.append({"workload": "FADI 128^3 cavity, CFL 4, 8 modes",
+                "f32": gpu(128, 128, 128, 1e-3, "fadi", "f32", 4.0, w.fields, steps=200),
+                "f64": gpu(128, 128, 128, 1e-3, "fadi", "f64", 4.0, w.fields, steps=50),
+                "oracle_1core": cpu(128, 128, 128, 1e-3, "fadi", 4.0, w.fields, steps=2)})
+    n = 256
+    d = 0.5e-3
+    eps = W.eps_blocks(3, n, n, n, 1.0, 10.0)
+    dt = 8.0 / (299792458.0 * math.sqrt(3.0 / d ** 2))
+    cur = W.dipole_current((np.arange(200) + 0.5) * dt)
+    z = W.zero_fields(n, n, n)
+    for scheme in ("flod", "fss"):
+        out.append({"workload": f"{scheme.upper()} 256^3, eps_r blocks U[1,10], CFL 8, z dipole",
+                    "f32": gpu(n, n, n, d, scheme, "f32", 8.0, z, eps, ("ez", 128, 128, 128, cur), steps=100),
+                    "f64": gpu(n, n, n, d, scheme, "f64", 8.0, z, eps, ("ez", 128, 128, 128, cur), steps=20),
+                    "oracle_1core": cpu(n, n, n, d, scheme, 8.0, z, eps, steps=1)})
+    for o in out:
+        o["unit"] = "cell-steps/s"
+        print(json.dumps(o), flush=True)
+
+
 def main():
     args = parse()
+    if args.suite:
+        from paper_2011_14043_gb300 import build
+        build()
+        suite(args)
+        return
     ws, rank, local = dist_env()
     if args.impl == "reference":
         reference_arm(args)

@@ -254,25 +254,27 @@ __global__ void cell_grad_kernel(const double* gx, const double* gy, const doubl
     const int j = (int)((c / nx) % ny);
     const int k = (int)(c / ((long long)nx * ny));
     double acc = 0.0;
-    // in-domain cells along an axis next to node n (cells n-1 and n)
-    auto cnt = [](int n, int N) { return (n > 0 ? 1 : 0) + (n < N ? 1 : 0); };
+    // 1 / (in-domain cells along an axis next to node n): cells n-1 and n,
+    // so the share of one sample is the product of two factors 1 or 1/2
+    // (exact; no division)
+    auto half = [](int n, int N) { return (n > 0 && n < N) ? 0.5 : 1.0; };
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj) {
         // Ex (i+1/2, j+dj, k+dk): cells (i, j+dj-1..j+dj, k+dk-1..k+dk)
         const long long at = (long long)(k + dk) * plane + (long long)(j + dj) * pitch + i;
-        acc += gx[at] / (double)(cnt(j + dj, ny) * cnt(k + dk, nz));
+        acc += gx[at] * (half(j + dj, ny) * half(k + dk, nz));
       }
     for (int dk = 0; dk < 2; ++dk)
       for (int di = 0; di < 2; ++di) {
         // Ey (i+di, j+1/2, k+dk)
         const long long at = (long long)(k + dk) * plane + (long long)j * pitch + i + di;
-        acc += gy[at] / (double)(cnt(i + di, nx) * cnt(k + dk, nz));
+        acc += gy[at] * (half(i + di, nx) * half(k + dk, nz));
       }
     for (int dj = 0; dj < 2; ++dj)
       for (int di = 0; di < 2; ++di) {
         // Ez (i+di, j+dj, k+1/2)
         const long long at = (long long)k * plane + (long long)(j + dj) * pitch + i + di;
-        acc += gz[at] / (double)(cnt(i + di, nx) * cnt(j + dj, ny));
+        acc += gz[at] * (half(i + di, nx) * half(j + dj, ny));
       }
     out[c] = eps0 * acc;
   }

@@ -15,6 +15,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1721,13 +1722,15 @@ int batch_one_step(fdtd_batch_t* b) {
 // process, and in the file named by FDTD_TUNE_CACHE when that is set.
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
-std::map<std::string, BatchCfg> g_tune_cache;
+// every tuner's results: key -> five shape numbers (see the key makers)
+using TuneVal = std::array<int, 5>;
+std::map<std::string, TuneVal> g_tune_cache;
 
 std::string device_name();
 
 std::string batch_key(const fdtd_batch_t* b) {
   const std::string name = device_name();
-  std::string s = name + "|p" + std::to_string(b->prec) + "|s" + std::to_string(b->scheme);
+  std::string s = "batch|" + name + "|p" + std::to_string(b->prec) + "|s" + std::to_string(b->scheme);
   for (const fdtd_t* h : b->h)
     s += "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz) +
          (h->per_node ? "n" : "u");
@@ -1737,11 +1740,13 @@ std::string batch_key(const fdtd_batch_t* b) {
     for (char c : s) x = (x ^ (unsigned char)c) * 1099511628211ull;
     char buf[32];
     snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)x);
-    s = name + "|p" + std::to_string(b->prec) + "|n" + std::to_string(b->h.size()) + "|" + buf;
+    s = "batch|" + name + "|p" + std::to_string(b->prec) + "|n" + std::to_string(b->h.size()) + "|" + buf;
   }
   return s;
 }
 
+// The file named by FDTD_TUNE_CACHE (when set) is read once per process and
+// every new result is appended: "key v0 v1 v2 v3 v4" per line.
 void tune_cache_load() {
   static bool loaded = false;
   if (loaded) return;
@@ -1751,19 +1756,26 @@ void tune_cache_load() {
   FILE* f = fopen(path, "r");
   if (!f) return;
   char key[512];
-  BatchCfg c;
-  while (fscanf(f, "%511s %d %d %d %d %d", key, &c.lanes[0], &c.L[0], &c.lanes[1], &c.L[1], &c.wpb) == 6)
-    g_tune_cache[key] = c;
+  TuneVal v;
+  while (fscanf(f, "%511s %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4]) == 6) g_tune_cache[key] = v;
   fclose(f);
 }
 
-void tune_cache_store(const std::string& key, const BatchCfg& c) {
-  g_tune_cache[key] = c;
+bool tune_cache_get(const std::string& key, TuneVal* v) {
+  tune_cache_load();
+  auto it = g_tune_cache.find(key);
+  if (it == g_tune_cache.end()) return false;
+  *v = it->second;
+  return true;
+}
+
+void tune_cache_put(const std::string& key, const TuneVal& v) {
+  g_tune_cache[key] = v;
   const char* path = getenv("FDTD_TUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.lanes[0], c.L[0], c.lanes[1], c.L[1], c.wpb);
+  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4]);
   fclose(f);
 }
 
@@ -1804,11 +1816,14 @@ double time_direction(fdtd_batch_t* b, const BatchCfg& cfg, int kind, int reps) 
 template <typename T>
 int batch_tune_t(fdtd_batch_t* b) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  tune_cache_load();
   const std::string key = batch_key(b);
-  auto it = g_tune_cache.find(key);
-  if (it != g_tune_cache.end()) {
-    b->cfg = it->second;
+  TuneVal v;
+  if (tune_cache_get(key, &v)) {
+    b->cfg.lanes[0] = v[0];
+    b->cfg.L[0] = v[1];
+    b->cfg.lanes[1] = v[2];
+    b->cfg.L[1] = v[3];
+    b->cfg.wpb = v[4];
     b->tuned = true;
     return FDTD_OK;
   }
@@ -1855,7 +1870,7 @@ int batch_tune_t(fdtd_batch_t* b) {
   BCK(cudaGetLastError());
   b->cfg = cfg;
   b->tuned = true;
-  tune_cache_store(key, cfg);
+  tune_cache_put(key, {cfg.lanes[0], cfg.L[0], cfg.lanes[1], cfg.L[1], cfg.wpb});
   return FDTD_OK;
 }
 
@@ -1894,8 +1909,6 @@ int batch_prepare(fdtd_batch_t* b) {
 // place into scratch) and the fastest kept; cached per (device, precision,
 // scheme, grid) for the process.
 // ---------------------------------------------------------------------------
-std::map<std::string, std::pair<StridedCfg, StridedCfg>> g_single_cache;
-
 std::string device_name() {
   int dev = 0;
   cudaDeviceProp prop;
@@ -1953,12 +1966,14 @@ double time_axis(fdtd_t* h, int ax, const StridedCfg& c, int reps) {
 template <typename T>
 int single_tune_t(fdtd_t* h) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  const std::string key = device_name() + "|p" + std::to_string(h->prec) + "|s" + std::to_string(h->scheme) +
-                          "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz);
-  auto it = g_single_cache.find(key);
-  if (it != g_single_cache.end()) {
-    h->strided_cfg[0] = it->second.first;
-    h->strided_cfg[1] = it->second.second;
+  const std::string key = "grid|" + device_name() + "|p" + std::to_string(h->prec) + "|s" +
+                          std::to_string(h->scheme) + "|" + std::to_string(h->nx) + "x" + std::to_string(h->ny) +
+                          "x" + std::to_string(h->nz);
+  TuneVal v;
+  if (tune_cache_get(key, &v) && strided_ok<T>(std::max(h->ny, 2), true, v[0], v[1]) &&
+      strided_ok<T>(std::max(h->nz, 2), true, v[2], v[3])) {
+    h->strided_cfg[0] = {true, v[0], v[1]};
+    h->strided_cfg[1] = {true, v[2], v[3]};
     return FDTD_OK;
   }
   static const int c32[][2] = {{32, 8}, {32, 16}, {16, 8}, {16, 16}, {16, 32}};
@@ -1985,7 +2000,8 @@ int single_tune_t(fdtd_t* h) {
   }
   h->output_valid = false;  // scratch was written
   CK(cudaGetLastError());
-  g_single_cache[key] = {h->strided_cfg[0], h->strided_cfg[1]};
+  tune_cache_put(key, {h->strided_cfg[0].lanes, h->strided_cfg[0].L, h->strided_cfg[1].lanes,
+                       h->strided_cfg[1].L, 0});
   return FDTD_OK;
 }
 
@@ -2349,18 +2365,16 @@ int adj_inject(fdtd_adj_t* a, void* const* eb, void* const* ea, double post, dou
 
 // Launch shape of the adjoint y/z kernels: every feasible candidate timed
 // on the context's own (zeroed) adjoint arrays, both procedures.
-std::map<std::string, std::pair<AdjCfg, AdjCfg>> g_adj_cache;
-
 template <typename T>
 int adj_tune_t(fdtd_adj_t* a) {
   fdtd_t* h = a->h;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  const std::string key = device_name() + "|p" + std::to_string(h->prec) + "|" + std::to_string(h->nx) + "x" +
-                          std::to_string(h->ny) + "x" + std::to_string(h->nz);
-  auto it = g_adj_cache.find(key);
-  if (it != g_adj_cache.end()) {
-    a->cfg[0] = it->second.first;
-    a->cfg[1] = it->second.second;
+  const std::string key = "adjoint|" + device_name() + "|p" + std::to_string(h->prec) + "|" +
+                          std::to_string(h->nx) + "x" + std::to_string(h->ny) + "x" + std::to_string(h->nz);
+  TuneVal v;
+  if (tune_cache_get(key, &v) && adj_strided_fn<T>(v[0], v[1]) && adj_strided_fn<T>(v[2], v[3])) {
+    a->cfg[0] = {true, v[0], v[1]};
+    a->cfg[1] = {true, v[2], v[3]};
     return FDTD_OK;
   }
   const size_t bytes = (size_t)h->count * h->esize;
@@ -2407,7 +2421,7 @@ int adj_tune_t(fdtd_adj_t* a) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
-  g_adj_cache[key] = {a->cfg[0], a->cfg[1]};
+  tune_cache_put(key, {a->cfg[0].lanes, a->cfg[0].L, a->cfg[1].lanes, a->cfg[1].L, 0});
   return FDTD_OK;
 }
 
