@@ -286,3 +286,42 @@ def run_fundamental(P: Problem, scheme: str, u0: dict, steps: int, probes=()):
             series[p][n] = out[c][k, j, i]
     field_out = flod2_output(P, u) if scheme == "flod2" else u
     return field_out, u, series
+
+
+# ---------------------------------------------------------------------------
+# D'Yakonov (Beam-Warming) and Douglas-Gunn splittings (Sec. II, "Fundamental
+# Implications and Significance"): extra equivalence pins of the procedure
+# ---------------------------------------------------------------------------
+
+def orig_dy_step(P: Problem, u: dict) -> dict:
+    """Eq. 25: (I - dt/2 A) u* = (I + dt/2 A)(I + dt/2 B) u^n, (I - dt/2 B) u^{n+1} = u*."""
+    tau = P.dt / 2
+    w = add(u, apply_op(P.grid, P.mat, "B", u), tau)
+    rhs = add(w, apply_op(P.grid, P.mat, "A", w), tau)
+    ustar = solve_implicit(P.grid, P.mat, "A", tau, rhs)
+    return solve_implicit(P.grid, P.mat, "B", tau, ustar)
+
+
+def fast_dy_init(P: Problem, u0: dict) -> dict:
+    """Eq. 27: v^{-1/2} = (1/2 I - dt/4 B) u^0."""
+    return add(scale(u0, 0.5), apply_op(P.grid, P.mat, "B", u0), -P.dt / 4)
+
+
+def fast_dy_step(P: Problem, u: dict, vm: dict):
+    """Eq. 26 from (u^n, v^{n-1/2}): v^n = u^n - v^{n-1/2}; (1/2 I - dt/4 A) u^{n+1/2} = v^n;
+    v^{n+1/2} = u^{n+1/2} - v^n; (1/2 I - dt/4 B) u^{n+1} = v^{n+1/2}.  The two solve +
+    subtract pairs are the updating procedure.  Returns (u^{n+1}, v^{n+1/2})."""
+    v = add(u, vm, -1.0)
+    vh, _, _ = procedure(P, v, "A", P.dt)          # state <- u^{n+1/2} - v^n = v^{n+1/2}
+    v1, _, _ = procedure(P, vh, "B", P.dt)         # state <- u^{n+1} - v^{n+1/2}
+    return add(v1, vh), vh
+
+
+def orig_dg_step(P: Problem, u: dict):
+    """Eq. 29 (delta formulation): (I - dt/2 A) du* = dt (A + B) u^n,
+    (I - dt/2 B) du = du*, u^{n+1} = u^n + du.  Returns (u^{n+1}, du*, du)."""
+    tau = P.dt / 2
+    rhs = scale(add(apply_op(P.grid, P.mat, "A", u), apply_op(P.grid, P.mat, "B", u)), P.dt)
+    dus = solve_implicit(P.grid, P.mat, "A", tau, rhs)
+    du = solve_implicit(P.grid, P.mat, "B", tau, dus)
+    return add(u, du), dus, du
