@@ -130,7 +130,10 @@ int fdtd_set_state(fdtd_t* h, int comp, const void* data, int on_device);
 int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* current, int64_t count);
 
 /* Record one physical field sample after every step.  *id receives the
- * probe index (0, 1, ...).  At most 16 probes. */
+ * probe index (0, 1, ...).  At most 16 probes.  FADI samples its output
+ * field w/2 (Eq. 9) from the two solves of the step; FLOD2 applies the
+ * output processing (Eq. 23) to the whole state every step while it has
+ * probes (one extra procedure per step). */
 int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id);
 
 /* Advance nsteps time steps (asynchronous on the handle's stream). */

@@ -99,6 +99,7 @@ struct fdtd_s {
   CUtensorMap tmap[6][2];
   const void* tmap_ptr[6][2] = {{nullptr}};
   int tmap_bn[6][2] = {{0}};
+  int tmap_lanes[6][2] = {{0}};
   ProcCoef proc[3];  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing)
   bool per_node = false;
   bool shape_tuned = false;   // per-node y/z launch shapes chosen by timing
@@ -604,7 +605,6 @@ template <typename T>
 constexpr int tma_L() { return 16; }
 int tma_L_rt(const fdtd_t*) { return 16; }
 
-int tma_lanes(const fdtd_t* h) { return h->prec == FDTD_F64 ? 8 : 16; }
 
 bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
   // the coefficient tables' carry products are built for the strided L
@@ -614,9 +614,8 @@ bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
 
 // Tensor map of component c for tiles of LANES lines x BN nodes along y
 // (kind 0) or z (kind 1).  Re-encoded when the array moved.
-int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
-  if (h->tmap_ptr[c][kind] != h->f[c] || h->tmap_bn[c][kind] != BN) {
-    const int lanes = tma_lanes(h);
+int get_tmap(fdtd_t* h, int c, int kind, int BN, int lanes, const CUtensorMap** out) {
+  if (h->tmap_ptr[c][kind] != h->f[c] || h->tmap_bn[c][kind] != BN || h->tmap_lanes[c][kind] != lanes) {
     cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->ny + 1), (cuuint64_t)(h->nz + 1)};
     cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->esize, (cuuint64_t)h->plane * h->esize};
     cuuint32_t box[3] = {(cuuint32_t)lanes, kind == 0 ? (cuuint32_t)BN : 1u, kind == 0 ? 1u : (cuuint32_t)BN};
@@ -633,33 +632,35 @@ int get_tmap(fdtd_t* h, int c, int kind, int BN, const CUtensorMap** out) {
     }
     h->tmap_ptr[c][kind] = h->f[c];
     h->tmap_bn[c][kind] = BN;
+    h->tmap_lanes[c][kind] = lanes;
   }
   *out = &h->tmap[c][kind];
   return FDTD_OK;
 }
 
 template <typename T>
-size_t tma_smem_bytes(int lanes, int BN, int P) {
-  return 4 * (size_t)BN * lanes * sizeof(T) + 6 * (size_t)(P | 1) * lanes * sizeof(T) + 2 * sizeof(uint64_t);
+size_t tma_smem_bytes(int lanes, int BN, int P, int nst) {
+  return 2 * (size_t)nst * BN * lanes * sizeof(T) + 6 * (size_t)(P | 1) * lanes * sizeof(T) +
+         (size_t)nst * sizeof(uint64_t);
 }
 
-template <typename T, int LANES, int MINB>
+template <typename T, int LANES, int MINB, int NST>
 int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   constexpr int L = tma_L<T>();
   const int BN = ((g.N + 7) / 8) * 8;
   const int P = segments(g.N, L, LANES);
   const int kind = g.axis == AX_Y ? 0 : 1;
   const CUtensorMap *tE, *tH;
-  int rc = get_tmap(h, g.ec, kind, BN, &tE);
+  int rc = get_tmap(h, g.ec, kind, BN, LANES, &tE);
   if (rc) return rc;
-  if ((rc = get_tmap(h, g.hc, kind, BN, &tH))) return rc;
+  if ((rc = get_tmap(h, g.hc, kind, BN, LANES, &tH))) return rc;
   fdtd::TmaTiles q;
   q.BN = BN;
   q.zbox = kind;
   q.tiles_x = (g.lane_hi + LANES - 1) / LANES;
   q.n_tiles = q.tiles_x * g.n_o;
-  const size_t smem = tma_smem_bytes<T>(LANES, BN, P);
-  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, L, MINB>;
+  const size_t smem = tma_smem_bytes<T>(LANES, BN, P, NST);
+  auto kern = fdtd::proc_strided_tma_kernel<T, LANES, L, MINB, NST>;
   static bool attr_set = false;  // one flag per instantiation
   if (!attr_set) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -721,8 +722,11 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   } else if (tma_eligible(h, g) && p.e_in == p.e_out && p.e_in == (const T*)h->f[g.ec] &&
              p.h_in == (const T*)h->f[g.hc]) {
     int rc;
-    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 8, 2>(h, g, p);
-    else rc = launch_strided_tma<T, 16, 2>(h, g, p);
+    // 16-line tiles, two blocks per SM, two-stage ring (measured at 256^3:
+    // a three-stage ring 9 % slower, three blocks per SM 12 % slower, 32-line
+    // tiles with one block per SM equal)
+    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 8, 2, 2>(h, g, p);
+    else rc = launch_strided_tma<T, 16, 2, 2>(h, g, p);
     if (rc) return rc;
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];
@@ -870,13 +874,13 @@ int scheme_init(fdtd_t* h) {
 }
 
 template <typename T>
-int record_probes(fdtd_t* h, int mode, double post) {
+int record_probes(fdtd_t* h, int mode, double post, void* const* arrays) {
   if (h->nprobes == 0) return FDTD_OK;
   fdtd::ProbeParams<T> pp;
   pp.n = h->nprobes;
   const long long src_at = h->src_comp >= 0 ? elem_index(h, h->src_i, h->src_j, h->src_k) : -1;
   for (int q = 0; q < h->nprobes; ++q) {
-    pp.arr[q] = (const T*)h->f[h->probe_comp[q]];
+    pp.arr[q] = (const T*)arrays[h->probe_comp[q]];
     pp.at[q] = h->probe_at[q];
     pp.sub[q] = (h->probe_comp[q] == h->src_comp && h->probe_at[q] == src_at) ? post : 0.0;
   }
@@ -888,8 +892,10 @@ int record_probes(fdtd_t* h, int mode, double post) {
 
 // mode 1 (FADI, after B): post = the source just added after the B
 // subtraction, which the output w_B/2 does not contain
-int probes(fdtd_t* h, int mode, double post = 0.0) {
-  return h->prec == FDTD_F64 ? record_probes<double>(h, mode, post) : record_probes<float>(h, mode, post);
+int probes(fdtd_t* h, int mode, double post = 0.0, void* const* arrays = nullptr) {
+  if (!arrays) arrays = h->f;
+  return h->prec == FDTD_F64 ? record_probes<double>(h, mode, post, arrays)
+                             : record_probes<float>(h, mode, post, arrays);
 }
 
 int ensure_probe_capacity(fdtd_t* h, long long need) {
@@ -917,6 +923,8 @@ int ensure_probe_capacity(fdtd_t* h, long long need) {
 //   FLOD  P_A(dt), P_B(dt) with +(dt/4) f in each implicit RHS (Eq. 15);
 //   FSS   P_A(dt/2), P_B(dt), P_A(dt/2) with +(h/4) f (Eq. 17);
 //   FLOD2 FLOD main iterations (Eq. 21).
+int physical_to_scratch(fdtd_t* h);
+
 int one_step(fdtd_t* h) {
   const long long n = h->steps;
   const double dt = h->dt;
@@ -939,8 +947,11 @@ int one_step(fdtd_t* h) {
         if (h->scheme == FDTD_FLOD) {
           if ((rc = probes(h, 2))) return rc;
         } else {
-          // probes of the FLOD2 physical field: output processing (Eq. 23) into scratch
-          return FDTD_ERR_UNSUPPORTED;
+          // probes of the FLOD2 physical field: output processing (Eq. 23)
+          // of the new state into scratch, sampled there
+          h->output_valid = false;
+          if ((rc = physical_to_scratch(h))) return rc;
+          if ((rc = probes(h, 2, 0.0, h->scratch))) return rc;
         }
       }
       break;
@@ -1354,7 +1365,6 @@ int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id) {
   if (!h || !id || check_comp(comp)) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
   if (h->nprobes >= fdtd::kMaxProbes) return FDTD_ERR_INVALID_ARG;
-  if (h->scheme == FDTD_FLOD2) return FDTD_ERR_UNSUPPORTED;
   int sx, sy, sz;
   comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
   if (i < 0 || j < 0 || k < 0 || i >= sx || j >= sy || k >= sz) return FDTD_ERR_INVALID_ARG;

@@ -497,28 +497,30 @@ struct TmaTiles {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
-// Dynamic shared memory: [2 stages][E, H][BN][LANES] + [6][LANES][P|1] + 2 mbarriers.
+// Dynamic shared memory: [NST stages][E, H][BN][LANES] + [6][LANES][P|1] + NST mbarriers.
 // At most 256 nodes per line, so at most ceil(256 / L) segments of LANES threads;
 // MINB blocks share an SM so that one block's barriers overlap another's work.
-template <typename T, int LANES, int L, int MINB>
+// Tile k of a block uses stage k % NST; its copy is issued NST tiles ahead.
+template <typename T, int LANES, int L, int MINB, int NST>
 __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     proc_strided_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
                             const PairParams<T> p, const TmaTiles q) {
+  static_assert(NST >= 2 && NST <= 4, "ring depth");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x % LANES;
   const int s = threadIdx.x / LANES;
   const int P = blockDim.x / LANES;
   const int stage_elems = q.BN * LANES;
   T* buf = reinterpret_cast<T*>(smem_raw);
-  T* sh = buf + 4 * stage_elems;
+  T* sh = buf + 2 * NST * stage_elems;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 6 * chain_stride(P) * LANES);
   const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
   const int j0 = s * L;
   const int N = p.N;
 
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int st = 0; st < NST; ++st) mbar_init(&bars[st], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -538,24 +540,26 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     }
   };
   if (threadIdx.x == 0) {
-    if ((int)blockIdx.x < q.n_tiles) issue(blockIdx.x, 0);
-    if ((int)(blockIdx.x + gridDim.x) < q.n_tiles) issue(blockIdx.x + gridDim.x, 1);
+#pragma unroll
+    for (int st = 0; st < NST; ++st)
+      if ((int)blockIdx.x + st * (int)gridDim.x < q.n_tiles) issue(blockIdx.x + st * gridDim.x, st);
   }
 
-  uint32_t parity0 = 0, parity1 = 0;
+  uint32_t parity = 0;  // bit st: phase parity expected next on stage st
   int k = 0;
   for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
-    const int stage = k & 1;
-    const uint32_t par = stage ? parity1 : parity0;
-    if (!mbar_wait_bounded(&bars[stage], par, kWaitLimitNs)) {
-      // Give up: flag it, let the other stage's copy (if any) land, return.
+    const int stage = k % NST;
+    if (!mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs)) {
+      // Give up: flag it, let the other stages' copies (if any) land, return.
       if (threadIdx.x == 0) atomicExch(p.err, 1);
-      const int other = tile + (int)gridDim.x;
-      if (other < q.n_tiles) mbar_wait_bounded(&bars[stage ^ 1], stage ? parity0 : parity1, kWaitLimitNs);
+      for (int d = 1; d < NST; ++d) {
+        const int other = tile + d * (int)gridDim.x;
+        const int st = (k + d) % NST;
+        if (other < q.n_tiles) mbar_wait_bounded(&bars[st], (parity >> st) & 1u, kWaitLimitNs);
+      }
       return;
     }
-    if (stage) parity1 ^= 1u;
-    else parity0 ^= 1u;
+    parity ^= 1u << stage;
 
     const int x0 = (tile % q.tiles_x) * LANES;
     const int o = p.o_lo + tile / q.tiles_x;
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     const T hm1 = (j0 > 0 && j0 - 1 < N) ? sH[(j0 - 1) * LANES + lane] : T(0);
     __syncthreads();  // this stage's buffer is free again
     if (threadIdx.x == 0) {
-      const int next = tile + 2 * (int)gridDim.x;
+      const int next = tile + NST * (int)gridDim.x;
       if (next < q.n_tiles) {
         fence_proxy_async_smem();
         issue(next, stage);

@@ -230,3 +230,21 @@ def test_tuned_per_node_shapes_match_oracle(prec):
     for tune in ((0, 0), (8, 0), (16, 0), (32, 0)):
         out, _, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "fss", prec, u0, 5, eps=eps, tune=tune)
         check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_flod2_probes_vs_oracle(prec):
+    """FLOD2 probe series: the output processing (Eq. 23) of every step's state."""
+    nx, ny, nz = 22, 19, 17
+    d = 1e-3
+    g = G.Grid(nx, ny, nz, d, d, d)
+    dt = 6.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=31)
+    steps = 15
+    probes = [("ex", 5, 6, 7), ("hz", 10, 3, 9), ("ez", 1, 1, 1)]
+    P = S.Problem(g, dt)
+    ref_u, _, ref = S.run_fundamental(P, "flod2", u0, steps, probes=probes)
+    out, series, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "flod2", prec, u0, steps, probes=probes)
+    check(out, ref_u, prec)
+    for a, b in zip(series, ref):
+        assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b))
