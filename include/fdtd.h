@@ -250,7 +250,7 @@ int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg);
  *   fdtd_set_material, non-uniform or tune[1] bit 1), fields and source set,
  *   no probes, and not yet stepped (FDTD_ERR_UNSUPPORTED / FDTD_ERR_STATE
  *   otherwise).  Device memory: about (6 nsteps/checkpoint_every +
- *   6 checkpoint_every + 21) state arrays (fdtd_adj_memory gives the bytes);
+ *   6 checkpoint_every + 18) state arrays (fdtd_adj_memory gives the bytes);
  *   FDTD_ERR_OOM when it does not fit.  The context borrows h, which must
  *   outlive it.
  * fdtd_adj_forward: runs the nsteps steps on h (h advances; its fields are

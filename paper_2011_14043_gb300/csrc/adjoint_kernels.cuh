@@ -12,11 +12,12 @@
 // (T^{-T} = diag(q) S^{-1} because S is symmetric), so the same pivots of S
 // serve both directions.  The eps dependence of b = h/(2 eps) enters through
 // the RHS term and T; both collapse to one local product,
-//     dJ/d eps_j += (1/h) y_j (E_j - E'_j + post_j),
-// with E and E' the forward E state before and after the procedure and post
-// the source added after the subtraction.  Derivation: b_j (s D_h H + 1/2 Lam w)_j
-// = 1/2 w_j - E_j from the forward row, d b_j/d eps_j = -b_j/eps_j,
-// q_j/eps_j = 2/h, and w = E' - post + E.
+//     dJ/d eps_j += (1/h) y_j D_j,   D_j = 2 E_j - w_j,
+// with E the forward E state before the procedure and w its solve; D is
+// what the forward kernels record (d_out = E_in - E_out, the subtraction
+// of Eqs. 40/47 being E_out = w - E).  Derivation: b_j (s D_h H + 1/2 Lam w)_j
+// = 1/2 w_j - E_j from the forward row, d b_j/d eps_j = -b_j/eps_j and
+// q_j/eps_j = 2/h.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,25 +29,18 @@ namespace fdtd {
 
 template <typename T>
 struct AdjExtra {
-  const T* e_before;  // forward E state of this pair's component before the procedure
-  const T* e_after;   // ... and after it (source included)
+  const T* d;         // forward record D = 2 E - w of this pair's component
   double* grad;       // dJ/d eps per E sample (field layout), accumulated
   double inv_h;       // 1 / procedure length
-  long long src_at;   // source sample of this component (-1: none)
-  double src_post;    // value added there after the subtraction
 };
 
-// Store of one adjoint segment: H update, E output, eps gradient.
+// Store of one adjoint node: H update, E output, eps gradient.
 template <typename T, int L>
 __device__ __forceinline__ void adj_store_node(const PairParams<T>& p, const AdjExtra<T>& x, long long at, int j,
                                                T E, T H, T q, T y, T ynext) {
   p.e_out[at] = fma(q, y, -E);
   p.h_out[at] = fma(p.kd, ynext - y, H);
-  if (j >= 1) {
-    double diff = (double)x.e_before[at] - (double)x.e_after[at];
-    if (at == x.src_at) diff += x.src_post;
-    x.grad[at] += x.inv_h * (double)y * diff;
-  }
+  if (j >= 1) x.grad[at] += x.inv_h * (double)y * (double)x.d[at];
 }
 
 // Lines along y or z: the per-node strided solve with unit row scaling.
@@ -140,12 +134,31 @@ __global__ void adj_rows_kernel(const PairParams<T> p, const AdjExtra<T> x) {
   const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
   const T win = warp_chain_backward<T>(y[0], pb);
   phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
+  if (j0 + L <= N) {
+    // whole segment: record, gradient and outputs as 16-byte vectors
+    T dd[L];
+    double g[L];
+    load_seg<T, L>(x.d + base + j0, dd);
+    load_seg<double, L>(x.grad + base + j0, g);
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const int j = j0 + t;
-    if (j < N) {
+    for (int t = 0; t < L; ++t) {
       const T ynext = (t + 1 < L) ? y[t + 1] : win;
-      adj_store_node<T, L>(p, x, base + j, j, E[t], H[t], q[t], y[t], ynext);
+      const T e_out = fma(q[t], y[t], -E[t]);
+      H[t] = fma(p.kd, ynext - y[t], H[t]);
+      E[t] = e_out;
+      if (j0 + t >= 1) g[t] += x.inv_h * (double)y[t] * (double)dd[t];
+    }
+    store_seg<T, L>(p.e_out + base + j0, E);
+    store_seg<T, L>(p.h_out + base + j0, H);
+    store_seg<double, L>(x.grad + base + j0, g);
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int j = j0 + t;
+      if (j < N) {
+        const T ynext = (t + 1 < L) ? y[t + 1] : win;
+        adj_store_node<T, L>(p, x, base + j, j, E[t], H[t], q[t], y[t], ynext);
+      }
     }
   }
 }
@@ -156,27 +169,29 @@ struct ProbeSet {
   const long long* at;   // sample offsets (field layout)
   const int* comp;       // E component of each sample (0..2)
   int n;
-  long long src_at;      // source sample (-1: none) and its component
-  int src_comp;
 };
 
-// Forward: mode 0 stashes the E state before the B procedure; mode 1 adds
-// sum (w_B/2)^2 with w_B = E_after_B (before its source) + stash to *acc.
+// mode 0 stashes the E state before the B procedure; mode 1 adds
+// sum (w_B/2)^2 with w_B = E_after_B (before its source) + stash to *acc
+// (forward pass); mode 2 writes w_B to wrec[k] (recomputation, for the
+// reverse pass).
 template <typename T>
 __global__ void probe_energy_kernel(ProbeSet<T> ps, const T* e0, const T* e1, const T* e2, double* stash,
-                                    double* acc, int mode) {
+                                    double* acc, int mode, double* wrec) {
   const T* e[3] = {e0, e1, e2};
   double sum = 0.0;
   for (int k = threadIdx.x; k < ps.n; k += blockDim.x) {
     const double v = (double)e[ps.comp[k]][ps.at[k]];
     if (mode == 0) {
       stash[k] = v;
-    } else {
+    } else if (mode == 1) {
       const double w = v + stash[k];
       sum += 0.25 * w * w;
+    } else {
+      wrec[k] = v + stash[k];
     }
   }
-  if (mode == 0) return;
+  if (mode != 1) return;
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
@@ -188,20 +203,15 @@ __global__ void probe_energy_kernel(ProbeSet<T> ps, const T* e0, const T* e1, co
   }
 }
 
-// Backward: lam_E += jbar * w_B/2 at the probe samples, with
-// w_B = E_after - post + E_before from the recomputed forward states.
+// Backward: lam_E += jbar * w_B/2 at the probe samples (w_B recorded by
+// the recomputation).
 template <typename T>
-__global__ void probe_inject_kernel(ProbeSet<T> ps, T* l0, T* l1, T* l2, const T* b0, const T* b1, const T* b2,
-                                    const T* a0, const T* a1, const T* a2, double post, double jbar) {
+__global__ void probe_inject_kernel(ProbeSet<T> ps, T* l0, T* l1, T* l2, const double* wrec, double jbar) {
   T* lam[3] = {l0, l1, l2};
-  const T* eb[3] = {b0, b1, b2};
-  const T* ea[3] = {a0, a1, a2};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ps.n; k += gridDim.x * blockDim.x) {
     const int c = ps.comp[k];
     const long long at = ps.at[k];
-    double w = (double)ea[c][at] + (double)eb[c][at];
-    if (c == ps.src_comp && at == ps.src_at) w -= post;
-    lam[c][at] = (T)((double)lam[c][at] + jbar * 0.5 * w);
+    lam[c][at] = (T)((double)lam[c][at] + jbar * 0.5 * wrec[k]);
   }
 }
 

@@ -490,6 +490,7 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.ks = (T)(sgn * c.ks);
   p.offh = (T)c.offh;
   p.offl = (T)c.offl;
+  p.d_out = nullptr;
   (void)h;
   return p;
 }
@@ -2236,7 +2237,8 @@ struct fdtd_adj_s {
   double* d_acc = nullptr;
   double* d_cell = nullptr;
   void* ckpt = nullptr;     // nseg x 6 state arrays
-  void* tape = nullptr;     // (2 every + 1) x 3 E arrays of one segment
+  void* tape = nullptr;     // 2 every x 3 records D (per procedure, per E component) of one segment
+  double* d_wrec = nullptr; // every x nprobe: w_B at the probe samples, per step of the segment
   void* work[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* lam[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* grad[3] = {nullptr, nullptr, nullptr};
@@ -2261,8 +2263,6 @@ fdtd::ProbeSet<T> probe_set(const fdtd_adj_t* a) {
   ps.at = a->d_probe_at;
   ps.comp = a->d_probe_comp;
   ps.n = a->nprobe;
-  ps.src_at = a->src_at;
-  ps.src_comp = a->h->src_comp;
   return ps;
 }
 
@@ -2272,38 +2272,50 @@ int copy_arrays(fdtd_t* h, void* const* dst, void* const* src, int first, int n)
   return FDTD_OK;
 }
 
-// One FADI step of the forward model on `st` (in place), optionally with the
-// objective's probe accumulation; E states after A and after B copied to
-// tape slots ta, tb when given.
+// One FADI step of the forward model on `st` (in place).  objective: add
+// the step's probe energy to *d_acc.  rec_a, rec_b (recomputation): the
+// per-node kernels also write each procedure's record D = E_in - E_out
+// there, and w_B at the probe samples goes to wrec.
 template <typename T>
-int adj_forward_step(fdtd_adj_t* a, void* const* st, long long n, bool objective, void* const* ta,
-                     void* const* tb) {
+int adj_forward_step(fdtd_adj_t* a, void* const* st, long long n, bool objective, void* const* rec_a,
+                     void* const* rec_b, double* wrec) {
   fdtd_t* h = a->h;
   const double post_a = 0.5 * h->dt * source_value(h, n);
   const double post_b = 0.5 * h->dt * source_value(h, n + 1);
-  int rc = run_procedure<T>(h, 0, 1.0, 1.0, -1.0, 1.0, st, st);
+  auto proc = [&](int slot, void* const* rec) -> int {
+    const ProcCoef& P = h->proc[slot];
+    for (int q = 0; q < 3; ++q) {
+      const PairGeom& g = h->geom[P.op][q];
+      fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, st, st);
+      if (rec) p.d_out = (T*)rec[g.ec];
+      int rc = launch_pair<T>(h, g, p);
+      if (rc) return rc;
+    }
+    return FDTD_OK;
+  };
+  int rc = proc(0, rec_a);
   if (rc) return rc;
   if (h->src_comp >= 0 && (rc = add_point(h, st[h->src_comp], post_a))) return rc;
-  if (ta && (rc = copy_arrays(h, ta, st, 0, 3))) return rc;
-  if (objective && a->nprobe) {
+  const bool probes = a->nprobe && (objective || wrec);
+  if (probes) {
     fdtd::probe_energy_kernel<T><<<1, 256, 0, h->stream>>>(probe_set<T>(a), (const T*)st[0], (const T*)st[1],
-                                                           (const T*)st[2], a->d_stash, a->d_acc, 0);
+                                                           (const T*)st[2], a->d_stash, a->d_acc, 0, nullptr);
     CK(cudaGetLastError());
   }
-  if ((rc = run_procedure<T>(h, 1, 1.0, 1.0, -1.0, 1.0, st, st))) return rc;
-  if (objective && a->nprobe) {
+  if ((rc = proc(1, rec_b))) return rc;
+  if (probes) {
     fdtd::probe_energy_kernel<T><<<1, 256, 0, h->stream>>>(probe_set<T>(a), (const T*)st[0], (const T*)st[1],
-                                                           (const T*)st[2], a->d_stash, a->d_acc, 1);
+                                                           (const T*)st[2], a->d_stash, a->d_acc,
+                                                           objective ? 1 : 2, wrec);
     CK(cudaGetLastError());
   }
   if (h->src_comp >= 0 && (rc = add_point(h, st[h->src_comp], post_b))) return rc;
-  if (tb && (rc = copy_arrays(h, tb, st, 0, 3))) return rc;
   return FDTD_OK;
 }
 
 // The three adjoint pair launches of procedure `slot` on lam (in place).
 template <typename T>
-int adj_procedure(fdtd_adj_t* a, int slot, void* const* eb, void* const* ea, double post, int only_axis = -1) {
+int adj_procedure(fdtd_adj_t* a, int slot, void* const* rec, int only_axis = -1) {
   fdtd_t* h = a->h;
   const ProcCoef& P = h->proc[slot];
   for (int q = 0; q < 3; ++q) {
@@ -2315,12 +2327,9 @@ int adj_procedure(fdtd_adj_t* a, int slot, void* const* eb, void* const* ea, dou
     p.ks = -kd;  // transposed couplings
     p.kd = -ks;
     fdtd::AdjExtra<T> x;
-    x.e_before = (const T*)eb[g.ec];
-    x.e_after = (const T*)ea[g.ec];
+    x.d = (const T*)rec[g.ec];
     x.grad = a->grad[g.ec];
     x.inv_h = 1.0 / P.h;
-    x.src_at = (g.ec == h->src_comp) ? a->src_at : -1;
-    x.src_post = post;
     h->launches++;
     if (g.rows) {
       switch (pick_rows_L(g.N)) {
@@ -2362,13 +2371,12 @@ int adj_point_term(fdtd_adj_t* a, double post) {
 }
 
 template <typename T>
-int adj_inject(fdtd_adj_t* a, void* const* eb, void* const* ea, double post, double jbar) {
+int adj_inject(fdtd_adj_t* a, const double* wrec, double jbar) {
   fdtd_t* h = a->h;
   if (!a->nprobe) return FDTD_OK;
   const unsigned blocks = (unsigned)std::min(1024, (a->nprobe + 255) / 256);
-  fdtd::probe_inject_kernel<T><<<blocks, 256, 0, h->stream>>>(
-      probe_set<T>(a), (T*)a->lam[0], (T*)a->lam[1], (T*)a->lam[2], (const T*)eb[0], (const T*)eb[1],
-      (const T*)eb[2], (const T*)ea[0], (const T*)ea[1], (const T*)ea[2], post, jbar);
+  fdtd::probe_inject_kernel<T><<<blocks, 256, 0, h->stream>>>(probe_set<T>(a), (T*)a->lam[0], (T*)a->lam[1],
+                                                              (T*)a->lam[2], wrec, jbar);
   CK(cudaGetLastError());
   return FDTD_OK;
 }
@@ -2414,7 +2422,7 @@ int adj_tune_t(fdtd_adj_t* a) {
       for (int r = 0; r < 4 && ok; ++r) {
         cudaEventRecord(e0, h->stream);
         for (int slot = 0; slot < 2 && ok; ++slot)
-          if (adj_procedure<T>(a, slot, h->f, h->f, 0.0, ax) != FDTD_OK) ok = false;
+          if (adj_procedure<T>(a, slot, h->f, ax) != FDTD_OK) ok = false;
         cudaEventRecord(e1, h->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
         float ms = 0;
@@ -2453,7 +2461,7 @@ int adj_forward_t(fdtd_adj_t* a) {
       for (int c = 0; c < 6; ++c) dst[c] = arr_at(a->ckpt, (n / a->every) * 6 + c, h);
       if ((rc = copy_arrays(h, dst, h->f, 0, 6))) return rc;
     }
-    if ((rc = adj_forward_step<T>(a, h->f, n, true, nullptr, nullptr))) return rc;
+    if ((rc = adj_forward_step<T>(a, h->f, n, true, nullptr, nullptr, nullptr))) return rc;
     h->steps++;
   }
   h->output_valid = false;
@@ -2478,32 +2486,31 @@ int adj_backward_t(fdtd_adj_t* a, double jbar) {
     void* src[6];
     for (int c = 0; c < 6; ++c) src[c] = arr_at(a->ckpt, (long long)seg * 6 + c, h);
     if ((rc = copy_arrays(h, a->work, src, 0, 6))) return rc;
-    void* t0[3];
-    slot(0, t0);
-    if ((rc = copy_arrays(h, t0, a->work, 0, 3))) return rc;
     for (long long n = n0; n < n1; ++n) {
       const int m = (int)(n - n0);
-      void *ta[3], *tb[3];
-      slot(2 * m + 1, ta);
-      slot(2 * m + 2, tb);
-      if ((rc = adj_forward_step<T>(a, a->work, n, false, ta, tb))) return rc;
+      void *ra[3], *rb[3];
+      slot(2 * m, ra);
+      slot(2 * m + 1, rb);
+      if ((rc = adj_forward_step<T>(a, a->work, n, false, ra, rb, a->d_wrec + (size_t)m * a->nprobe))) return rc;
     }
     for (long long n = n1 - 1; n >= n0; --n) {
       const int m = (int)(n - n0);
-      void *e0[3], *e1[3], *e2[3];
-      slot(2 * m, e0);
-      slot(2 * m + 1, e1);
-      slot(2 * m + 2, e2);
+      void *ra[3], *rb[3];
+      slot(2 * m, ra);
+      slot(2 * m + 1, rb);
+      const double* wrec = a->d_wrec + (size_t)m * a->nprobe;
       const double post_a = 0.5 * h->dt * source_value(h, n);
       const double post_b = 0.5 * h->dt * source_value(h, n + 1);
-      // B procedure of step n, with the objective's w_B term
+      // B procedure of step n: the objective's w_B term enters w-bar; with
+      // it added to the E adjoint before the transposed solve, the output
+      // E-bar = q y - E-bar' needs it added back once more
       if ((rc = adj_point_term<T>(a, post_b))) return rc;
-      if ((rc = adj_inject<T>(a, e1, e2, post_b, jbar))) return rc;
-      if ((rc = adj_procedure<T>(a, 1, e1, e2, post_b))) return rc;
-      if ((rc = adj_inject<T>(a, e1, e2, post_b, jbar))) return rc;
+      if ((rc = adj_inject<T>(a, wrec, jbar))) return rc;
+      if ((rc = adj_procedure<T>(a, 1, rb))) return rc;
+      if ((rc = adj_inject<T>(a, wrec, jbar))) return rc;
       // A procedure of step n
       if ((rc = adj_point_term<T>(a, post_a))) return rc;
-      if ((rc = adj_procedure<T>(a, 0, e0, e1, post_a))) return rc;
+      if ((rc = adj_procedure<T>(a, 0, ra))) return rc;
     }
   }
   // input initialization v0 = u0 + (dt/2) B u0 + (dt/2) f
@@ -2532,7 +2539,7 @@ int adj_backward_t(fdtd_adj_t* a, double jbar) {
 }
 
 void adj_free(fdtd_adj_t* a) {
-  void* ptrs[] = {a->d_probe_at, a->d_probe_comp, a->d_stash, a->d_acc, a->d_cell, a->ckpt, a->tape};
+  void* ptrs[] = {a->d_probe_at, a->d_probe_comp, a->d_stash, a->d_acc, a->d_cell, a->ckpt, a->tape, a->d_wrec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int c = 0; c < 6; ++c) {
@@ -2608,7 +2615,8 @@ int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t c
   alloc((void**)&a->d_acc, sizeof(double));
   alloc((void**)&a->d_cell, sizeof(double) * (size_t)h->nx * h->ny * h->nz);
   alloc(&a->ckpt, arr * 6 * (size_t)a->nseg);
-  alloc(&a->tape, arr * 3 * (size_t)(2 * checkpoint_every + 1));
+  alloc(&a->tape, arr * 3 * (size_t)(2 * checkpoint_every));
+  alloc((void**)&a->d_wrec, sizeof(double) * std::max<size_t>(1, at.size()) * (size_t)checkpoint_every);
   for (int c = 0; c < 6; ++c) {
     alloc(&a->work[c], arr);
     alloc(&a->lam[c], arr);

@@ -78,6 +78,8 @@ struct PairParams {
   T ks;                  // per-node: RHS coupling of the scaled rows, s sign(h) / d_eta
   T offh, offl;          // per-node: off-diagonal -|ks| |kd| / 2 as hi + lo
   int* err;              // set to 1 when a bounded device wait gives up
+  T* d_out;              // per-node kernels: when set, also E_in - E_out per E node
+                         // (the reverse pass's record of the procedure)
 };
 
 // ---------------------------------------------------------------------------
@@ -430,6 +432,13 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
   T win;
   strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
+  if constexpr (PER_NODE) {
+    if (active && p.d_out) {
+#pragma unroll
+      for (int t = 0; t < L; ++t)
+        if (j0 + t < N) p.d_out[base + (long long)(j0 + t) * ls] = E[t] - fma(p.alpha, y[t], p.beta * E[t]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -715,11 +724,23 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     const T win = warp_chain_backward<T>(y[0], pb);
     phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
     // H update and subtraction below use y (= w) and win
+    T D[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
       H[t] = fma(p.kd, wnext - y[t], H[t]);
-      E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+      const T e_new = fma(p.alpha, y[t], p.beta * E[t]);
+      D[t] = E[t] - e_new;
+      E[t] = e_new;
+    }
+    if (p.d_out) {
+      if (j0 + L <= N) {
+        store_seg<T, L>(p.d_out + base + j0, D);
+      } else {
+#pragma unroll
+        for (int t = 0; t < L; ++t)
+          if (j0 + t < N) p.d_out[base + j0 + t] = D[t];
+      }
     }
   } else {
     // homogeneous media: lanes in the converged interior use the limit
