@@ -398,7 +398,7 @@ def suite(args):
     import oracle.schemes as S
 
     def gpu(nx, ny, nz, d, scheme, prec, cfl, fields, eps=None, src=None, steps=50, warm=5):
-        sim = Simulation(nx, ny, nz, d, scheme=scheme, precision=prec, cfl=cfl)
+        sim = Simulation(nx, ny, nz, d, scheme=scheme, precision=prec, cfl=cfl, tune=tuple(args.tune))
         if eps is not None:
             sim.set_material(eps)
         if src is not None:
@@ -438,6 +438,11 @@ def suite(args):
                 "f32": gpu(128, 128, 128, 1e-3, "fadi", "f32", 4.0, w.fields, steps=200),
                 "f64": gpu(128, 128, 128, 1e-3, "fadi", "f64", 4.0, w.fields, steps=50),
                 "oracle_1core": cpu(128, 128, 128, 1e-3, "fadi", 4.0, w.fields, steps=2)})
+    f256 = workload_fields(256)
+    out.append({"workload": "FADI 256^3 cavity, CFL 4, 8 modes (no per-launch timing)",
+                "f32": gpu(256, 256, 256, 1e-3, "fadi", "f32", 4.0, f256, steps=200),
+                "f64": gpu(256, 256, 256, 1e-3, "fadi", "f64", 4.0, f256, steps=20)})
+    del f256
     n = 256
     d = 0.5e-3
     eps = W.eps_blocks(3, n, n, n, 1.0, 10.0)

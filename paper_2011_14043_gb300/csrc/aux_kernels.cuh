@@ -52,6 +52,25 @@ __global__ void add_point_kernel(T* y, long long at, double a) {
   if (threadIdx.x == 0 && blockIdx.x == 0) y[at] = (T)((double)y[at] + a);
 }
 
+// y[at] += coef * table[*step + offset] (0 outside the table): a point
+// source whose value is read on the device, so that steps replayed from one
+// captured graph see each step's value.  The product is rounded before the
+// add (no fused multiply-add), as when the host forms coef * f.
+template <typename T>
+__global__ void add_point_table_kernel(T* y, long long at, const double* table, long long len,
+                                       const long long* step, int offset, double coef) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const long long n = *step + offset;
+    const double v = (n >= 0 && n < len) ? table[n] : 0.0;
+    y[at] = (T)__dadd_rn((double)y[at], __dmul_rn(coef, v));
+  }
+}
+
+// mode 0: *step = value;  mode 1: *step += 1.
+__global__ void step_counter_kernel(long long* step, long long value, int mode) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step = mode == 0 ? value : *step + 1;
+}
+
 constexpr int kMaxProbes = 16;
 
 template <typename T>

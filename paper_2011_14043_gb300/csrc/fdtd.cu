@@ -128,6 +128,16 @@ struct fdtd_s {
   long long launches = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;     // reusable events
+  // one-step CUDA graph (steps without probes or per-launch timing): the
+  // three pairs of each procedure on parallel branches
+  cudaStream_t g_run = nullptr, g_br[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t g_in = nullptr, g_out = nullptr, g_fork = nullptr, g_join[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t g_exec = nullptr;
+  std::vector<const void*> g_bound;     // state pointers the graph was captured with
+  long long g_kernels = 0;              // kernels per replay
+  double* d_srcval = nullptr;           // f_E(n) = src_scale * I(n), n < src_current.size()
+  long long srcval_len = 0;
+  long long* d_step = nullptr;          // step index read by graph-replayed source kernels
   std::vector<std::pair<int, std::pair<int, int>>> ev_rec;  // (class, (start ev, stop ev))
   long long timed_launches[3] = {0, 0, 0};
   double timed_ms[3] = {0, 0, 0};
@@ -645,6 +655,18 @@ size_t tma_smem_bytes(int lanes, int BN, int P, int nst) {
          (size_t)nst * sizeof(uint64_t);
 }
 
+// The TMA kernels take up to 227 KB of dynamic shared memory (set once per
+// instantiation, outside any stream capture).
+template <typename T, int LANES, int MINB, int NST>
+cudaError_t ensure_tma_attr() {
+  static bool attr_set = false;
+  if (attr_set) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fdtd::proc_strided_tma_kernel<T, LANES, tma_L<T>(), MINB, NST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) attr_set = true;
+  return e;
+}
+
 template <typename T, int LANES, int MINB, int NST>
 int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   constexpr int L = tma_L<T>();
@@ -662,11 +684,7 @@ int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& 
   q.n_tiles = q.tiles_x * g.n_o;
   const size_t smem = tma_smem_bytes<T>(LANES, BN, P, NST);
   auto kern = fdtd::proc_strided_tma_kernel<T, LANES, L, MINB, NST>;
-  static bool attr_set = false;  // one flag per instantiation
-  if (!attr_set) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set = true;
-  }
+  CK((ensure_tma_attr<T, LANES, MINB, NST>()));
   const int grid = std::min(q.n_tiles, MINB * h->num_sms);
   kern<<<grid, P * LANES, smem, h->stream>>>(*tE, *tH, p, q);
   return FDTD_OK;
@@ -926,6 +944,133 @@ int ensure_probe_capacity(fdtd_t* h, long long need) {
 //   FLOD2 FLOD main iterations (Eq. 21).
 int physical_to_scratch(fdtd_t* h);
 
+void graph_release(fdtd_t* h) {
+  if (h->g_exec) cudaGraphExecDestroy(h->g_exec);
+  h->g_exec = nullptr;
+  h->g_bound.clear();
+}
+
+bool graph_usable(const fdtd_t* h) {
+  return !h->timing && h->nprobes == 0 && (h->desc.tune[1] & 8) == 0 &&
+         (h->src_comp < 0 || h->d_srcval != nullptr);
+}
+
+// nsteps steps as replays of a captured one-step graph: each procedure forks
+// its three pair launches (disjoint arrays) onto parallel branches and joins
+// them before the next procedure; a point source is added by kernels that
+// read each step's value from a device table indexed by a device step
+// counter.  Same kernels, same arguments, same results as one_step.
+int step_graph(fdtd_t* h, int64_t nsteps) {
+  if (!h->g_run) {
+    CK(cudaStreamCreateWithFlags(&h->g_run, cudaStreamNonBlocking));
+    for (int b = 0; b < 3; ++b) {
+      CK(cudaStreamCreateWithFlags(&h->g_br[b], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&h->g_join[b], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&h->g_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->g_out, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->g_fork, cudaEventDisableTiming));
+  }
+  const bool src = h->src_comp >= 0;
+  std::vector<const void*> ptrs(h->f, h->f + 6);
+  if (!h->g_exec || ptrs != h->g_bound) {
+    graph_release(h);
+    if (h->prec == FDTD_F64) CK((ensure_tma_attr<double, 8, 2, 2>()));
+    else CK((ensure_tma_attr<float, 16, 2, 2>()));
+    static const int seq_fss[3] = {0, 1, 0};
+    static const int seq_two[2] = {0, 1};
+    const int* seq = h->scheme == FDTD_FSS ? seq_fss : seq_two;
+    const int nproc = h->scheme == FDTD_FSS ? 3 : 2;
+    // the source terms of one_step: coefficient of f added before and after
+    // each procedure (0 = none), and the step offset of the value after it
+    const double dt = h->dt;
+    double pre[3] = {0, 0, 0}, post[3] = {0, 0, 0};
+    int post_off[3] = {0, 0, 0};
+    if (h->scheme == FDTD_FADI) {
+      post[0] = 0.5 * dt;
+      post[1] = 0.5 * dt;
+      post_off[1] = 1;
+    } else if (h->scheme == FDTD_FSS) {
+      pre[0] = post[0] = 0.125 * dt;
+      pre[1] = post[1] = 0.25 * dt;
+      pre[2] = post[2] = 0.125 * dt;
+    } else {
+      pre[0] = post[0] = 0.25 * dt;
+      pre[1] = post[1] = 0.25 * dt;
+    }
+    if (src && !h->d_step) CK(cudaMalloc(&h->d_step, sizeof(long long)));
+    const long long src_at = src ? elem_index(h, h->src_i, h->src_j, h->src_k) : 0;
+    auto add_src = [&](double coef, int off) -> cudaError_t {
+      if (!src || coef == 0.0) return cudaSuccess;
+      if (h->prec == FDTD_F64)
+        fdtd::add_point_table_kernel<double><<<1, 32, 0, h->g_run>>>((double*)h->f[h->src_comp], src_at,
+                                                                     h->d_srcval, h->srcval_len, h->d_step, off, coef);
+      else
+        fdtd::add_point_table_kernel<float><<<1, 32, 0, h->g_run>>>((float*)h->f[h->src_comp], src_at, h->d_srcval,
+                                                                    h->srcval_len, h->d_step, off, coef);
+      h->launches++;
+      return cudaGetLastError();
+    };
+    cudaStream_t home = h->stream;
+    const long long before = h->launches;
+    CK(cudaStreamBeginCapture(h->g_run, cudaStreamCaptureModeThreadLocal));
+    int rc = FDTD_OK;
+    for (int k = 0; k < nproc && rc == FDTD_OK; ++k) {
+      if (add_src(pre[k], 0) != cudaSuccess) rc = FDTD_ERR_CUDA;
+      if (rc == FDTD_OK && cudaEventRecord(h->g_fork, h->g_run) != cudaSuccess) rc = FDTD_ERR_CUDA;
+      const ProcCoef& P = h->proc[seq[k]];
+      for (int q = 0; q < 3 && rc == FDTD_OK; ++q) {
+        if (cudaStreamWaitEvent(h->g_br[q], h->g_fork, 0) != cudaSuccess) { rc = FDTD_ERR_CUDA; break; }
+        h->stream = h->g_br[q];
+        const PairGeom& g = h->geom[P.op][q];
+        if (h->prec == FDTD_F64) {
+          fdtd::PairParams<double> p = make_params<double>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, h->f);
+          rc = launch_pair<double>(h, g, p);
+        } else {
+          fdtd::PairParams<float> p = make_params<float>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, h->f, h->f);
+          rc = launch_pair<float>(h, g, p);
+        }
+        h->stream = home;
+        if (rc == FDTD_OK && (cudaEventRecord(h->g_join[q], h->g_br[q]) != cudaSuccess ||
+                              cudaStreamWaitEvent(h->g_run, h->g_join[q], 0) != cudaSuccess))
+          rc = FDTD_ERR_CUDA;
+      }
+      if (rc == FDTD_OK && add_src(post[k], post_off[k]) != cudaSuccess) rc = FDTD_ERR_CUDA;
+    }
+    if (rc == FDTD_OK && src) {
+      fdtd::step_counter_kernel<<<1, 32, 0, h->g_run>>>(h->d_step, 0, 1);
+      h->launches++;
+      if (cudaGetLastError() != cudaSuccess) rc = FDTD_ERR_CUDA;
+    }
+    h->stream = home;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->g_run, &graph);
+    h->g_kernels = h->launches - before;
+    h->launches = before;
+    if (rc != FDTD_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != FDTD_OK ? rc : cuda_fail(h, e);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&h->g_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    h->g_bound = ptrs;
+  }
+  CK(cudaEventRecord(h->g_in, h->stream));
+  CK(cudaStreamWaitEvent(h->g_run, h->g_in, 0));
+  if (src) {
+    fdtd::step_counter_kernel<<<1, 32, 0, h->g_run>>>(h->d_step, h->steps, 0);
+    CK(cudaGetLastError());
+  }
+  for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(h->g_exec, h->g_run));
+  CK(cudaEventRecord(h->g_out, h->g_run));
+  CK(cudaStreamWaitEvent(h->stream, h->g_out, 0));
+  h->launches += nsteps * h->g_kernels;
+  h->steps += nsteps;
+  return FDTD_OK;
+}
+
 int one_step(fdtd_t* h) {
   const long long n = h->steps;
   const double dt = h->dt;
@@ -1018,6 +1163,19 @@ int refresh_src_scale(fdtd_t* h) {
                   cudaMemcpyDeviceToHost));
   const double area = h->src_comp == EX ? h->dy * h->dz : (h->src_comp == EY ? h->dx * h->dz : h->dx * h->dy);
   h->src_scale = -1.0 / (area * kEps0 * er);
+  // device copy of the per-step values for graph-replayed steps
+  graph_release(h);
+  const long long len = (long long)h->src_current.size();
+  if (len != h->srcval_len) {
+    if (h->d_srcval) cudaFree(h->d_srcval);
+    h->d_srcval = nullptr;
+    h->srcval_len = 0;
+    CK(cudaMalloc(&h->d_srcval, sizeof(double) * (size_t)std::max(len, 1LL)));
+    h->srcval_len = len;
+  }
+  std::vector<double> v((size_t)len);
+  for (long long n = 0; n < len; ++n) v[(size_t)n] = source_value(h, n);
+  if (len) CK(cudaMemcpy(h->d_srcval, v.data(), sizeof(double) * (size_t)len, cudaMemcpyHostToDevice));
   return FDTD_OK;
 }
 
@@ -1224,6 +1382,18 @@ int fdtd_destroy(fdtd_t* h) {
   if (h->d_partial) cudaFree(h->d_partial);
   if (h->d_err) cudaFree(h->d_err);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->g_run) cudaStreamSynchronize(h->g_run);
+  graph_release(h);
+  for (int b = 0; b < 3; ++b) {
+    if (h->g_br[b]) cudaStreamDestroy(h->g_br[b]);
+    if (h->g_join[b]) cudaEventDestroy(h->g_join[b]);
+  }
+  if (h->g_run) cudaStreamDestroy(h->g_run);
+  if (h->g_in) cudaEventDestroy(h->g_in);
+  if (h->g_out) cudaEventDestroy(h->g_out);
+  if (h->g_fork) cudaEventDestroy(h->g_fork);
+  if (h->d_srcval) cudaFree(h->d_srcval);
+  if (h->d_step) cudaFree(h->d_step);
   delete h;
   return FDTD_OK;
 }
@@ -1272,6 +1442,7 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   h->per_node = !e_uniform || (h->desc.tune[1] & 2) != 0;
   h->eps_r = h->per_node ? 1.0 : e0;
   h->shape_tuned = false;
+  graph_release(h);
   int rc = FDTD_OK;
   if (h->per_node) {
     for (int c = 0; c < 3; ++c) {
@@ -1342,6 +1513,7 @@ int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* curr
     h->src_comp = -1;
     h->src_current.clear();
     h->output_valid = false;
+    graph_release(h);
     return FDTD_OK;
   }
   if (comp < 0 || comp > 2) return FDTD_ERR_INVALID_ARG;
@@ -1389,8 +1561,12 @@ int fdtd_step(fdtd_t* h, int64_t nsteps) {
   }
   h->shape_tuned = true;
   if ((rc = ensure_probe_capacity(h, h->steps + nsteps))) return rc;
-  for (int64_t q = 0; q < nsteps; ++q)
-    if ((rc = one_step(h))) return rc;
+  if (graph_usable(h)) {
+    if ((rc = step_graph(h, nsteps))) return rc;
+  } else {
+    for (int64_t q = 0; q < nsteps; ++q)
+      if ((rc = one_step(h))) return rc;
+  }
   h->output_valid = false;
   return FDTD_OK;
 }

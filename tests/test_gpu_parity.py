@@ -248,3 +248,33 @@ def test_flod2_probes_vs_oracle(prec):
     check(out, ref_u, prec)
     for a, b in zip(series, ref):
         assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme,media", [("fadi", "uniform"), ("fss", "blocks"), ("flod", "blocks"),
+                                          ("fadi", "blocks+source"), ("fss", "blocks+source"),
+                                          ("flod2", "uniform+source")])
+def test_graph_steps_bit_identical_to_stream_steps(scheme, media, prec):
+    """Steps without probes replay a captured one-step graph whose pairs run
+    on parallel branches (a source is read from a device table indexed by a
+    device step counter); tune[1] bit 3 forces the stream path.  Same kernels
+    and arguments: identical fields; and the oracle's answer."""
+    nx, ny, nz = 40, 33, 29
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 5.0 * g.dt_cfl()
+    steps = 9
+    u0 = random_fields(nx, ny, nz, seed=77)
+    eps = W.eps_blocks(77, nx, ny, nz, 1.0, 4.0) if media.startswith("blocks") else None
+    src = None
+    if media.endswith("source"):
+        cur = W.dipole_current((np.arange(steps + 1) + 0.5) * dt * 30) * 1e-4
+        src = ("ez", 20, 16, 14, cur)
+    a, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, scheme, prec, u0, steps, eps=eps, source=src,
+                         tune=(16, 0))
+    b, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, scheme, prec, u0, steps, eps=eps, source=src,
+                         tune=(16, 8))
+    for c in G.COMPS:
+        assert np.array_equal(a[c], b[c]), c
+    P = oracle_problem(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, eps=eps, source=src)
+    ref, _, _ = S.run_fundamental(P, scheme, u0, steps)
+    check(a, ref, prec)
