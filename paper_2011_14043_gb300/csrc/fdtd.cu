@@ -542,7 +542,6 @@ const void* strided_fn_rt(bool pn, int lanes, int L) {
   if (lanes == 32 && L == 8) return strided_fn<T, 32, 8>(pn);
   if (lanes == 32 && L == 16) return strided_fn<T, 32, 16>(pn);
   if (lanes == 32 && L == 32) return strided_fn<T, 32, 32>(pn);
-  if (lanes == 16 && L == 17) return strided_fn<T, 16, 17>(pn);
   if (lanes == 16 && L == 8) return strided_fn<T, 16, 8>(pn);
   if (lanes == 16 && L == 16) return strided_fn<T, 16, 16>(pn);
   if (lanes == 16 && L == 32) return strided_fn<T, 16, 32>(pn);
@@ -556,7 +555,6 @@ void launch_strided(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T
   if (lanes == 32 && L == 8) launch_strided_L<T, 32, 8>(h, g, p, pn);
   else if (lanes == 32 && L == 16) launch_strided_L<T, 32, 16>(h, g, p, pn);
   else if (lanes == 32 && L == 32) launch_strided_L<T, 32, 32>(h, g, p, pn);
-  else if (lanes == 16 && L == 17) launch_strided_L<T, 16, 17>(h, g, p, pn);
   else if (lanes == 16 && L == 8) launch_strided_L<T, 16, 8>(h, g, p, pn);
   else if (lanes == 16 && L == 16) launch_strided_L<T, 16, 16>(h, g, p, pn);
   else if (lanes == 16 && L == 32) launch_strided_L<T, 16, 32>(h, g, p, pn);
@@ -944,7 +942,11 @@ int ensure_probe_capacity(fdtd_t* h, long long need) {
 //   FLOD2 FLOD main iterations (Eq. 21).
 int physical_to_scratch(fdtd_t* h);
 
+// Drop the captured step.  Replays still in flight on the (non-blocking)
+// replay stream finish first: callers go on to rewrite or free buffers the
+// graph reads (source table, coefficients).
 void graph_release(fdtd_t* h) {
+  if (h->g_run) cudaStreamSynchronize(h->g_run);
   if (h->g_exec) cudaGraphExecDestroy(h->g_exec);
   h->g_exec = nullptr;
   h->g_bound.clear();
