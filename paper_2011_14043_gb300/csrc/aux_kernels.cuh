@@ -71,6 +71,34 @@ __global__ void step_counter_kernel(long long* step, long long value, int mode) 
   if (threadIdx.x == 0 && blockIdx.x == 0) *step = mode == 0 ? value : *step + 1;
 }
 
+// Compact [sz][sy][sx] <-> padded (plane, pitch) layout of one component,
+// for host copies staged through a contiguous device buffer.
+template <typename T>
+__global__ void unpack_kernel(const T* __restrict__ src, T* __restrict__ dst, int sx, int sy, int sz,
+                              long long pitch, long long plane) {
+  const long long n = (long long)sx * sy * sz;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % sx);
+    const long long r = e / sx;
+    const int j = (int)(r % sy);
+    const int k = (int)(r / sy);
+    dst[(long long)k * plane + (long long)j * pitch + i] = src[e];
+  }
+}
+
+template <typename T>
+__global__ void pack_kernel(const T* __restrict__ src, T* __restrict__ dst, int sx, int sy, int sz, long long pitch,
+                            long long plane) {
+  const long long n = (long long)sx * sy * sz;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % sx);
+    const long long r = e / sx;
+    const int j = (int)(r % sy);
+    const int k = (int)(r / sy);
+    dst[e] = src[(long long)k * plane + (long long)j * pitch + i];
+  }
+}
+
 constexpr int kMaxProbes = 16;
 
 template <typename T>

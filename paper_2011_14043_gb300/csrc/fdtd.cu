@@ -90,6 +90,7 @@ struct fdtd_s {
   long long pitch, plane, count;
   void* f[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* scratch[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* stage = nullptr;  // contiguous staging buffer of host copies (one component)
   PairGeom geom[2][3];
   StridedCfg strided_cfg[2];  // y lines, z lines
   int num_sms = 0;
@@ -1181,9 +1182,53 @@ int refresh_src_scale(fdtd_t* h) {
   return FDTD_OK;
 }
 
+// Host copies go through a contiguous device staging buffer (one transfer
+// at full link bandwidth, then a (un)pack kernel) instead of a row-by-row
+// pitched copy; device-to-device copies stay pitched.
+int ensure_stage(fdtd_t* h) {
+  if (h->stage) return FDTD_OK;
+  const size_t n = (size_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
+  CK(cudaMalloc(&h->stage, n * h->esize));
+  return FDTD_OK;
+}
+
+int stage_unpack(fdtd_t* h, int sx, int sy, int sz, void* dst_padded) {
+  const long long n = (long long)sx * sy * sz;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+  if (h->prec == FDTD_F64)
+    fdtd::unpack_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)h->stage, (double*)dst_padded, sx, sy,
+                                                               sz, h->pitch, h->plane);
+  else
+    fdtd::unpack_kernel<float><<<blocks, 256, 0, h->stream>>>((const float*)h->stage, (float*)dst_padded, sx, sy, sz,
+                                                              h->pitch, h->plane);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int stage_pack(fdtd_t* h, int sx, int sy, int sz, const void* src_padded) {
+  const long long n = (long long)sx * sy * sz;
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+  if (h->prec == FDTD_F64)
+    fdtd::pack_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)src_padded, (double*)h->stage, sx, sy, sz,
+                                                             h->pitch, h->plane);
+  else
+    fdtd::pack_kernel<float><<<blocks, 256, 0, h->stream>>>((const float*)src_padded, (float*)h->stage, sx, sy, sz,
+                                                            h->pitch, h->plane);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
 int copy_component(fdtd_t* h, int comp, const void* src_padded, void* dst, int on_device) {
   int sx, sy, sz;
   comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  if (!on_device) {
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    if ((rc = stage_pack(h, sx, sy, sz, src_padded))) return rc;
+    CK(cudaMemcpyAsync(dst, h->stage, (size_t)sx * sy * sz * h->esize, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+  }
   cudaMemcpy3DParms m = {};
   m.srcPtr = make_cudaPitchedPtr((void*)src_padded, (size_t)h->pitch * h->esize, (size_t)h->pitch,
                                  (size_t)(h->ny + 1));
@@ -1198,6 +1243,14 @@ int copy_component(fdtd_t* h, int comp, const void* src_padded, void* dst, int o
 int copy_in_component(fdtd_t* h, int comp, const void* src, void* dst_padded, int on_device) {
   int sx, sy, sz;
   comp_extent(comp, h->nx, h->ny, h->nz, &sx, &sy, &sz);
+  if (!on_device) {
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->stage, src, (size_t)sx * sy * sz * h->esize, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = stage_unpack(h, sx, sy, sz, dst_padded))) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+  }
   cudaMemcpy3DParms m = {};
   m.srcPtr = make_cudaPitchedPtr((void*)src, (size_t)sx * h->esize, (size_t)sx, (size_t)sy);
   m.dstPtr = make_cudaPitchedPtr(dst_padded, (size_t)h->pitch * h->esize, (size_t)h->pitch,
@@ -1396,6 +1449,7 @@ int fdtd_destroy(fdtd_t* h) {
   if (h->g_fork) cudaEventDestroy(h->g_fork);
   if (h->d_srcval) cudaFree(h->d_srcval);
   if (h->d_step) cudaFree(h->d_step);
+  if (h->stage) cudaFree(h->stage);
   delete h;
   return FDTD_OK;
 }
