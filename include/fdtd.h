@@ -19,7 +19,10 @@
  * --------------------------------
  * Errors: every call returns FDTD_OK (0) or a negative FDTD_ERR_* code and
  *   never throws or aborts.  After FDTD_ERR_CUDA the handle is poisoned: every
- *   later call except fdtd_destroy returns FDTD_ERR_STATE.
+ *   later call except fdtd_destroy returns FDTD_ERR_STATE.  A device
+ *   allocation that fails inside a call on a handle returns FDTD_ERR_OOM and
+ *   poisons the handle the same way (the call may have changed part of it);
+ *   fdtd_create cleans up and returns FDTD_ERR_OOM.
  * Arrays: component arrays are C-contiguous [k][j][i] (x fastest) in the
  *   compact Yee shapes (nx, ny, nz = cells):
  *     EX (nz+1, ny+1, nx)   EY (nz+1, ny, nx+1)   EZ (nz, ny+1, nx+1)
@@ -265,6 +268,22 @@ int fdtd_adj_forward(fdtd_adj_t* a, double* objective);
 int fdtd_adj_backward(fdtd_adj_t* a, double jbar, double* grad_eps_r, int on_device);
 int fdtd_adj_memory(const fdtd_adj_t* a, int64_t* bytes);
 int fdtd_adj_destroy(fdtd_adj_t* a);
+
+/* Test hook: the n-th device allocation of the library from now on (0 = the
+ * next one) fails as an out-of-memory would, without calling CUDA; n < 0
+ * disarms it.  For exercising the error and clean-up paths; process-wide. */
+int fdtd_debug_fail_alloc(int64_t n);
+
+/* Self-test of the bounded device waits (failure detection without a GPU
+ * fault).  Every spin-wait in the kernels (the TMA kernels' mbarrier waits)
+ * gives up after a time limit, records that in a device flag and returns, so
+ * that the host reports FDTD_ERR_TIMEOUT and the context stays usable.  This
+ * launches one block whose thread waits, through the same bounded wait, on an
+ * mbarrier expecting one arrival: with arrive = 0 nobody arrives and the call
+ * returns FDTD_ERR_TIMEOUT after about limit_ns; with arrive = 1 the thread
+ * arrives first and the call returns FDTD_OK.  limit_ns in (0, 1e10];
+ * synchronises stream (NULL = legacy default stream). */
+int fdtd_selftest_bounded_wait(int64_t limit_ns, int arrive, void* stream);
 
 /* Static description of an error code. */
 const char* fdtd_strerror(int code);

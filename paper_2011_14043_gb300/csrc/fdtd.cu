@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -149,11 +150,30 @@ namespace {
 
 int single_tune(fdtd_t* h);
 
+// Every device allocation of the library goes through dev_malloc.  A test
+// hook (fdtd_debug_fail_alloc) can make the n-th next one fail as an
+// out-of-memory would, without calling CUDA, to exercise the error paths.
+std::atomic<long long> g_fail_alloc_in{-1};
+
+cudaError_t dev_malloc(void** p, size_t n) {
+  long long k = g_fail_alloc_in.load();
+  while (k >= 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(k, k == 0 ? -1 : k - 1)) {
+      if (k == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, n);
+}
+
 int cuda_fail(fdtd_t* h, cudaError_t e) {
   if (e == cudaSuccess) return FDTD_OK;
   if (h) h->poisoned = true;
   fprintf(stderr, "fdtd: CUDA error: %s\n", cudaGetErrorString(e));
-  return FDTD_ERR_CUDA;
+  return e == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA;
 }
 
 #define CK(call)                                          \
@@ -247,7 +267,7 @@ template <typename T>
 int upload(fdtd_t* h, void** dst, const std::vector<double>& src) {
   std::vector<T> tmp(src.size());
   for (size_t q = 0; q < src.size(); ++q) tmp[q] = (T)src[q];
-  if (!*dst) CK(cudaMalloc(dst, tmp.size() * sizeof(T)));
+  if (!*dst) CK(dev_malloc((void**)dst, tmp.size() * sizeof(T)));
   CK(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return FDTD_OK;
@@ -822,7 +842,7 @@ int procedure_ex(fdtd_t* h, int slot, double sgn, double alpha, double beta, dou
 int ensure_scratch(fdtd_t* h) {
   for (int c = 0; c < 6; ++c) {
     if (!h->scratch[c]) {
-      CK(cudaMalloc(&h->scratch[c], (size_t)h->count * h->esize));
+      CK(dev_malloc((void**)&h->scratch[c], (size_t)h->count * h->esize));
       CK(cudaMemsetAsync(h->scratch[c], 0, (size_t)h->count * h->esize, h->stream));
     }
   }
@@ -921,7 +941,7 @@ int ensure_probe_capacity(fdtd_t* h, long long need) {
   long long cap = std::max<long long>(need, 2 * h->probe_cap);
   cap = std::max<long long>(cap, 1024);
   double* np = nullptr;
-  CK(cudaMalloc(&np, sizeof(double) * fdtd::kMaxProbes * cap));
+  CK(dev_malloc((void**)&np, sizeof(double) * fdtd::kMaxProbes * cap));
   CK(cudaMemsetAsync(np, 0, sizeof(double) * fdtd::kMaxProbes * cap, h->stream));
   if (h->d_probe) {
     CK(cudaMemcpy2DAsync(np, sizeof(double) * cap, h->d_probe, sizeof(double) * h->probe_cap,
@@ -1001,7 +1021,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
       pre[0] = post[0] = 0.25 * dt;
       pre[1] = post[1] = 0.25 * dt;
     }
-    if (src && !h->d_step) CK(cudaMalloc(&h->d_step, sizeof(long long)));
+    if (src && !h->d_step) CK(dev_malloc((void**)&h->d_step, sizeof(long long)));
     const long long src_at = src ? elem_index(h, h->src_i, h->src_j, h->src_k) : 0;
     auto add_src = [&](double coef, int off) -> cudaError_t {
       if (!src || coef == 0.0) return cudaSuccess;
@@ -1173,7 +1193,7 @@ int refresh_src_scale(fdtd_t* h) {
     if (h->d_srcval) cudaFree(h->d_srcval);
     h->d_srcval = nullptr;
     h->srcval_len = 0;
-    CK(cudaMalloc(&h->d_srcval, sizeof(double) * (size_t)std::max(len, 1LL)));
+    CK(dev_malloc((void**)&h->d_srcval, sizeof(double) * (size_t)std::max(len, 1LL)));
     h->srcval_len = len;
   }
   std::vector<double> v((size_t)len);
@@ -1188,7 +1208,7 @@ int refresh_src_scale(fdtd_t* h) {
 int ensure_stage(fdtd_t* h) {
   if (h->stage) return FDTD_OK;
   const size_t n = (size_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
-  CK(cudaMalloc(&h->stage, n * h->esize));
+  CK(dev_malloc((void**)&h->stage, n * h->esize));
   return FDTD_OK;
 }
 
@@ -1297,7 +1317,7 @@ template <typename T>
 int energy_of(fdtd_t* h, void* const* arr, double* out) {
   const int blocks = 152 * 4;
   if (!h->d_partial) {
-    CK(cudaMalloc(&h->d_partial, sizeof(double) * 6 * blocks));
+    CK(dev_malloc((void**)&h->d_partial, sizeof(double) * 6 * blocks));
     h->partial_n = blocks;
   }
   for (int c = 0; c < 6; ++c) {
@@ -1328,6 +1348,29 @@ int energy(fdtd_t* h, void* const* arr, double* out) {
 // ===========================================================================
 
 extern "C" {
+
+int fdtd_debug_fail_alloc(int64_t n) {
+  g_fail_alloc_in.store(n < 0 ? -1 : (long long)n);
+  return FDTD_OK;
+}
+
+int fdtd_selftest_bounded_wait(int64_t limit_ns, int arrive, void* stream) {
+  if (limit_ns <= 0 || limit_ns > 10000000000LL) return FDTD_ERR_INVALID_ARG;
+  int* d_flag = nullptr;
+  if (dev_malloc((void**)&d_flag, sizeof(int)) != cudaSuccess) return FDTD_ERR_OOM;
+  cudaStream_t st = (cudaStream_t)stream;
+  int v = -1;
+  fdtd::bounded_wait_probe_kernel<<<1, 32, 0, st>>>(d_flag, (unsigned long long)limit_ns, arrive ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_flag);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "fdtd: CUDA error: %s\n", cudaGetErrorString(e));
+    return FDTD_ERR_CUDA;
+  }
+  return v == 0 ? FDTD_OK : FDTD_ERR_TIMEOUT;
+}
 
 const char* fdtd_strerror(int code) {
   switch (code) {
@@ -1395,16 +1438,16 @@ int fdtd_create(const fdtd_desc* desc, void* stream, fdtd_t** out) {
     h->strided_cfg[ax] = (a.lanes * a.L == b.lanes * b.L && a.lanes == b.lanes) ? a : b;
   }
   for (int c = 0; c < 6; ++c) {
-    cudaError_t e = cudaMalloc(&h->f[c], (size_t)h->count * h->esize);
+    cudaError_t e = dev_malloc((void**)&h->f[c], (size_t)h->count * h->esize);
     if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
     e = cudaMemsetAsync(h->f[c], 0, (size_t)h->count * h->esize, h->stream);
     if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_CUDA; }
   }
   for (int cls = 0; cls < 3; ++cls)
     h->bytes_per_launch[cls] = 4.0 * (double)d.nx * d.ny * d.nz * (double)h->esize;
-  cudaError_t e = cudaMalloc(&h->d_stash, sizeof(double) * fdtd::kMaxProbes);
+  cudaError_t e = dev_malloc((void**)&h->d_stash, sizeof(double) * fdtd::kMaxProbes);
   if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
-  e = cudaMalloc(&h->d_err, sizeof(int));
+  e = dev_malloc((void**)&h->d_err, sizeof(int));
   if (e != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_OOM; }
   if (cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) { fdtd_destroy(h); return FDTD_ERR_CUDA; }
   {
@@ -1503,7 +1546,7 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   if (h->per_node) {
     for (int c = 0; c < 3; ++c) {
       edge_eps(h, eps, c, h->eps_host[c]);
-      CK(cudaMalloc(&h->eps_node[c], sizeof(double) * h->eps_host[c].size()));
+      CK(dev_malloc((void**)&h->eps_node[c], sizeof(double) * h->eps_host[c].size()));
       CK(cudaMemcpyAsync(h->eps_node[c], h->eps_host[c].data(), sizeof(double) * h->eps_host[c].size(),
                          cudaMemcpyHostToDevice, h->stream));
     }
@@ -1763,7 +1806,7 @@ void free_groups(fdtd_batch_t* b) {
     cudaError_t _e = (call);                                               \
     if (_e != cudaSuccess) {                                               \
       fprintf(stderr, "fdtd batch: CUDA error: %s\n", cudaGetErrorString(_e)); \
-      return FDTD_ERR_CUDA;                                                \
+      return _e == cudaErrorMemoryAllocation ? FDTD_ERR_OOM : FDTD_ERR_CUDA; \
     }                                                                      \
   } while (0)
 
@@ -1868,18 +1911,18 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
             for (int bx = 0; bx < tx; ++bx) tiles.push_back({m, bx * bg.lanes, g.o_lo + o, 0});
         }
       }
-      BCK(cudaMalloc(&bg.d_params, sizeof(fdtd::PairParams<T>) * params.size()));
+      BCK(dev_malloc((void**)&bg.d_params, sizeof(fdtd::PairParams<T>) * params.size()));
       out[slot].push_back(bg);  // freed with the list from here on
       BCK(cudaMemcpy(bg.d_params, params.data(), sizeof(fdtd::PairParams<T>) * params.size(),
                      cudaMemcpyHostToDevice));
       if (bg.kind == 2) {
         bg.nitems = starts.back();
-        BCK(cudaMalloc(&bg.d_index, sizeof(long long) * starts.size()));
+        BCK(dev_malloc((void**)&bg.d_index, sizeof(long long) * starts.size()));
         out[slot].back() = bg;
         BCK(cudaMemcpy(bg.d_index, starts.data(), sizeof(long long) * starts.size(), cudaMemcpyHostToDevice));
       } else {
         bg.nitems = (long long)tiles.size();
-        BCK(cudaMalloc(&bg.d_index, sizeof(fdtd::BatchTile) * tiles.size()));
+        BCK(dev_malloc((void**)&bg.d_index, sizeof(fdtd::BatchTile) * tiles.size()));
         out[slot].back() = bg;
         BCK(cudaMemcpy(bg.d_index, tiles.data(), sizeof(fdtd::BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
       }
@@ -2838,7 +2881,7 @@ int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t c
   bool ok = true;
   auto alloc = [&](void** p, size_t n) {
     if (!ok) return;
-    if (cudaMalloc(p, n) != cudaSuccess) ok = false;
+    if (dev_malloc((void**)p, n) != cudaSuccess) ok = false;
     else a->bytes += (long long)n;
   };
   alloc((void**)&a->d_probe_at, sizeof(long long) * std::max<size_t>(1, at.size()));

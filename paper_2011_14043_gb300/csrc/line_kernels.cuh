@@ -497,6 +497,23 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, ui
       : "memory");
 }
 
+// Self-test of the bounded waits: an mbarrier that expects one arrival;
+// with arrive = 0 nobody arrives, the wait gives up after limit_ns and the
+// kernel reports it through *flag (1), as the TMA kernels do through their
+// error flag; with arrive = 1 thread 0 arrives first and the wait succeeds.
+__global__ void bounded_wait_probe_kernel(int* flag, unsigned long long limit_ns, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) mbar_arrive_expect_tx(&bar, 0);
+    *flag = mbar_wait_bounded(&bar, 0, limit_ns) ? 0 : 1;
+  }
+}
+
 struct TmaTiles {
   int BN;        // nodes per box (>= N, a multiple of 8, <= 256)
   int zbox;      // 0: box {LANES, BN, 1} (lines along y); 1: box {LANES, 1, BN} (along z)

@@ -73,3 +73,8 @@ def test_null_handle_and_pointers(L):
     assert L.fdtd_get_field(None, 0, None, 0) == -1
     assert L.fdtd_strerror(-3).decode().startswith("CUDA error")
     assert L.fdtd_strerror(12345).decode() == "unknown error"
+
+
+@pytest.mark.parametrize("limit", [0, -5, 10_000_000_001])
+def test_bounded_wait_selftest_rejects_bad_limits(L, limit):
+    assert L.fdtd_selftest_bounded_wait(limit, 0, None) == -1
