@@ -71,18 +71,16 @@ def workload_fields(n):
 
 
 def recorded_traffic(kernel_class: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    capture (profiles/dram_traffic.json), or None when the kernels changed
-    since that capture or the capture is of another kernel."""
+    """DRAM bytes per launch of the kernel of one line direction from the
+    committed ncu capture (profiles/dram_traffic.json), or None when the
+    kernels changed since that capture."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
         src = os.path.join(ROOT, "paper_2011_14043_gb300", "csrc", "line_kernels.cuh")
         if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["line_kernels_sha1"]:
             return None
-        if kernel_class not in ("y-lines", "z-lines"):
-            return None
-        return rec["traffic_bytes_per_launch"]
+        return rec["classes"][kernel_class]["traffic_bytes_per_launch"]
     except Exception:
         return None
 

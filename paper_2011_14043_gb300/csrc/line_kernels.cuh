@@ -633,6 +633,166 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
   }
 }
 
+// TMA tensor store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the committed stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// The TMA-fed y/z kernel with its outputs staged in shared memory and written
+// by TMA tensor stores of the same boxes, overlapped with the next tile.
+// Shared memory: [NST stages][E, H][BN][LANES] + [E, H][BN][LANES] output +
+// [6][LANES][P|1] + NST mbarriers.  The output box is written whole: lanes
+// outside [lane_lo, lane_hi) write back the values they loaded, and nodes
+// at or past the line end write zeros (the far-wall E and the unused H row
+// beyond the last face are zero); parts of the box outside the array are
+// clipped by the TMA unit.
+template <typename T, int LANES, int L, int MINB, int NST>
+__global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
+    proc_strided_tma_st_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
+                               const PairParams<T> p, const TmaTiles q) {
+  static_assert(NST >= 2 && NST <= 4, "ring depth");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x % LANES;
+  const int s = threadIdx.x / LANES;
+  const int P = blockDim.x / LANES;
+  const int stage_elems = q.BN * LANES;
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* oE = buf + 2 * NST * stage_elems;
+  T* oH = oE + stage_elems;
+  T* sh = oH + stage_elems;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh + 6 * chain_stride(P) * LANES);
+  const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
+  const int j0 = s * L;
+  const int N = p.N;
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int st = 0; st < NST; ++st) mbar_init(&bars[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto coords = [&](int tile, int& x0, int& o) {
+    x0 = (tile % q.tiles_x) * LANES;
+    o = p.o_lo + tile / q.tiles_x;
+  };
+  auto issue = [&](int tile, int stage) {
+    int x0, o;
+    coords(tile, x0, o);
+    T* dE = buf + (2 * stage + 0) * stage_elems;
+    T* dH = buf + (2 * stage + 1) * stage_elems;
+    mbar_arrive_expect_tx(&bars[stage], stage_bytes);
+    if (q.zbox) {
+      tma_load_3d(dE, &tmE, &bars[stage], x0, o, 0);
+      tma_load_3d(dH, &tmH, &bars[stage], x0, o, 0);
+    } else {
+      tma_load_3d(dE, &tmE, &bars[stage], x0, 0, o);
+      tma_load_3d(dH, &tmH, &bars[stage], x0, 0, o);
+    }
+  };
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int st = 0; st < NST; ++st)
+      if ((int)blockIdx.x + st * (int)gridDim.x < q.n_tiles) issue(blockIdx.x + st * gridDim.x, st);
+  }
+
+  uint32_t parity = 0;  // bit st: phase parity expected next on stage st
+  int k = 0;
+  for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
+    const int stage = k % NST;
+    if (!mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs)) {
+      // Give up: flag it, let the other stages' copies and our own stores land, return.
+      if (threadIdx.x == 0) atomicExch(p.err, 1);
+      for (int d = 1; d < NST; ++d) {
+        const int other = tile + d * (int)gridDim.x;
+        const int st = (k + d) % NST;
+        if (other < q.n_tiles) mbar_wait_bounded(&bars[st], (parity >> st) & 1u, kWaitLimitNs);
+      }
+      if (threadIdx.x == 0) bulk_wait_all();
+      return;
+    }
+    parity ^= 1u << stage;
+
+    int x0, o;
+    coords(tile, x0, o);
+    const int i = x0 + lane;
+    const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
+
+    const T* sE = buf + (2 * stage + 0) * stage_elems;
+    const T* sH = buf + (2 * stage + 1) * stage_elems;
+    T E[L], H[L], y[L], qn[L], ibn[L], ibl[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      qn[t] = T(0);
+      ibn[t] = T(0);
+      ibl[t] = T(0);
+    }
+    if (j0 + L <= N) {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        E[t] = sE[(j0 + t) * LANES + lane];
+        H[t] = sH[(j0 + t) * LANES + lane];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        const int j = j0 + t;
+        const bool in = j < N;
+        E[t] = in ? sE[j * LANES + lane] : T(0);
+        H[t] = in ? sH[j * LANES + lane] : T(0);
+      }
+    }
+    const T hm1 = (j0 > 0 && j0 - 1 < N) ? sH[(j0 - 1) * LANES + lane] : T(0);
+    if (threadIdx.x == 0) bulk_wait_read_all();  // the previous tile's stores have read the output buffer
+    __syncthreads();  // this stage's buffer and the output buffer are free
+    if (threadIdx.x == 0) {
+      const int next = tile + NST * (int)gridDim.x;
+      if (next < q.n_tiles) {
+        fence_proxy_async_smem();
+        issue(next, stage);
+      }
+    }
+    T win;
+    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
+                                      win);
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int j = j0 + t;
+      if (j < q.BN) {
+        T eo = E[t], ho = H[t];
+        if (active && j < N) {
+          const T wnext = (t + 1 < L) ? y[t + 1] : win;
+          eo = fma(p.alpha, y[t], p.beta * E[t]);
+          ho = fma(p.kd, wnext - y[t], H[t]);
+        }
+        oE[j * LANES + lane] = eo;
+        oH[j * LANES + lane] = ho;
+      }
+    }
+    fence_proxy_async_smem();  // the output writes, seen by the TMA unit
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (q.zbox) {
+        tma_store_3d(&tmE, oE, x0, o, 0);
+        tma_store_3d(&tmH, oH, x0, o, 0);
+      } else {
+        tma_store_3d(&tmE, oE, x0, 0, o);
+        tma_store_3d(&tmH, oH, x0, 0, o);
+      }
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+}
+
 // ---------------------------------------------------------------------------
 // Lines along x
 // ---------------------------------------------------------------------------
