@@ -223,18 +223,21 @@ int fdtd_batch_destroy(fdtd_batch_t* b);
 /* Kernel launches per batch step (for accounting); valid after a step. */
 int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
 /* Launch shape of the batch: cfg = {y lanes, y L, z lanes, z L, x warps per
- * block} (lanes: lines per tile of the y/z kernels; L: nodes per thread,
- * which sets the carry-chain depth ceil(N/L); grids with uniform media keep
- * the L of their coefficient tables).  By default the first fdtd_batch_step
- * tunes it: each candidate shape is timed on the batch's own data (out of
- * place, into the handles' scratch arrays, so the state is untouched) and
- * the fastest kept; results are cached per device, precision, scheme and
- * grid list for the process, and appended to the file named by the
- * environment variable FDTD_TUNE_CACHE when set.  tune_ms (may be NULL)
- * receives the tuned time of each direction's launches for one step.
- * fdtd_batch_set_config fixes the shape (FDTD_ERR_INVALID_ARG for a shape
- * that is not built); cfg = NULL returns to tuning. */
-int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[5], double tune_ms[3]);
+ * block, x packing} (lanes: lines per tile of the y/z kernels; L: nodes per
+ * thread, which sets the carry-chain depth ceil(N/L); grids with uniform
+ * media keep the L of their coefficient tables; x packing 1: x lines of up
+ * to 256 nodes in grids with per-node media run on 8, 16 or 32 lanes with 8
+ * nodes per lane, several short lines per warp; 0: one warp per x line).  By
+ * default the first fdtd_batch_step tunes it: each candidate shape is timed
+ * on the batch's own data (out of place, into the handles' scratch arrays,
+ * so the state is untouched) and the fastest kept; results are cached per
+ * device, precision, scheme and grid list for the process, and appended to
+ * the file named by the environment variable FDTD_TUNE_CACHE when set.
+ * tune_ms (may be NULL) receives the tuned time of each direction's
+ * launches for one step.  fdtd_batch_set_config fixes the shape
+ * (FDTD_ERR_INVALID_ARG for a shape that is not built); cfg = NULL returns
+ * to tuning. */
+int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[6], double tune_ms[3]);
 int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg);
 
 /* Reverse mode: gradient of a probe-energy objective of FADI with respect to

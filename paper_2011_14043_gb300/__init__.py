@@ -256,18 +256,19 @@ class Batch:
     def config(self) -> dict:
         """Launch shape in use (tuned on the first step unless fixed) and the
         tuned per-direction times of one step's launches (ms)."""
-        cfg = (ctypes.c_int32 * 5)()
+        cfg = (ctypes.c_int32 * 6)()
         ms = (ctypes.c_double * 3)()
         check(lib().fdtd_batch_get_config(self._h, cfg, ms), "fdtd_batch_get_config")
-        return {"y": (cfg[0], cfg[1]), "z": (cfg[2], cfg[3]), "x_warps_per_block": cfg[4],
+        return {"y": (cfg[0], cfg[1]), "z": (cfg[2], cfg[3]), "x_warps_per_block": cfg[4], "x_pack": cfg[5],
                 "tuned_ms": {"y": ms[0], "z": ms[1], "x": ms[2]}}
 
-    def set_config(self, y=None, z=None, x_warps_per_block=8):
-        """Fix the launch shape: y, z = (lanes, L); None for both returns to tuning."""
+    def set_config(self, y=None, z=None, x_warps_per_block=8, x_pack=1):
+        """Fix the launch shape: y, z = (lanes, L); x_pack 1 lets short x lines of
+        grids with per-node media share warps; None for y and z returns to tuning."""
         if y is None and z is None:
             check(lib().fdtd_batch_set_config(self._h, None), "fdtd_batch_set_config")
             return
-        cfg = (ctypes.c_int32 * 5)(y[0], y[1], z[0], z[1], x_warps_per_block)
+        cfg = (ctypes.c_int32 * 6)(y[0], y[1], z[0], z[1], x_warps_per_block, x_pack)
         check(lib().fdtd_batch_set_config(self._h, cfg), "fdtd_batch_set_config")
 
     def launches_per_step(self) -> int:

@@ -1756,6 +1756,7 @@ struct BatchCfg {
   int lanes[2] = {16, 16};
   int L[2] = {16, 16};
   int wpb = 8;
+  int xpack = 1;  // per-node x lines of up to 128 nodes share warps (8 or 16 lanes per line)
 };
 
 constexpr int kBatchBranches = 4;  // concurrent graph branches per procedure
@@ -1763,6 +1764,8 @@ constexpr int kBatchBranches = 4;  // concurrent graph branches per procedure
 struct BatchGroup {
   int kind = 0;             // 0 lines along y, 1 along z, 2 along x
   int L = 16, P = 1, lanes = 16, wpb = 8;
+  int G = 1;                // y/z tiles per block
+  int lpl = 0;              // x lines of per-node grids: lanes per line (0: one warp per line)
   int ngrids = 0;
   long long nitems = 0;     // tiles (strided) or lines (x)
   void* d_params = nullptr; // PairParams<T>[ngrids]
@@ -1858,7 +1861,7 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
                    bool scratch_out) {
   for (int slot = 0; slot < 2; ++slot) {
     struct Key {
-      int kind, L, lanes, P;
+      int kind, L, lanes, P, pn;
       std::vector<std::pair<int, int>> members;  // (grid, pair)
     };
     std::vector<Key> keys;
@@ -1873,20 +1876,27 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
         int L, lanes = 0, Pseg = 0;
         if (g.rows) {
           L = pick_rows_L(g.N);
+          // per-node media take any L: short lines share a warp (8 or 16
+          // lanes per line) so that every lane streams 8 nodes
+          if (h->per_node && g.N <= 256 && cfg.xpack) {
+            L = 8;
+            lanes = g.N <= 64 ? 8 : (g.N <= 128 ? 16 : 32);
+          }
         } else {
           lanes = cfg.lanes[kind];
           L = batch_grid_L<T>(h, kind, g.N, lanes, cfg.L[kind]);
           if (L < 0) return FDTD_ERR_UNSUPPORTED;
           Pseg = segments(g.N, L, lanes);
         }
+        const int pn = h->per_node ? 1 : 0;  // tiles of one block share the media kind
         bool found = false;
         for (auto& k : keys)
-          if (k.kind == kind && k.L == L && k.lanes == lanes && k.P == Pseg) {
+          if (k.kind == kind && k.L == L && k.lanes == lanes && k.P == Pseg && k.pn == pn) {
             k.members.push_back({gi, q});
             found = true;
             break;
           }
-        if (!found) keys.push_back({kind, L, lanes, Pseg, {{gi, q}}});
+        if (!found) keys.push_back({kind, L, lanes, Pseg, pn, {{gi, q}}});
       }
     }
     for (auto& k : keys) {
@@ -1895,6 +1905,19 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
       bg.L = k.L;
       bg.lanes = k.lanes;
       bg.P = k.P;
+      if (bg.kind == 2) bg.lpl = k.lanes;
+      if (bg.kind != 2) {
+        // about 256 threads per block, within the default shared-memory limit
+        const int tpt = bg.P * bg.lanes;
+        bg.G = std::max(1, std::min(8, 256 / tpt));
+        auto smem = [&](int G) {
+          return fdtd::batch_params_bytes<T>(G) + (size_t)G * 6 * (bg.P | 1) * bg.lanes * sizeof(T);
+        };
+        while (bg.G > 1 && smem(bg.G) > 48 * 1024) --bg.G;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, batch_strided_fn<T>(bg.lanes, bg.L)) == cudaSuccess)
+          while (bg.G > 1 && bg.G * tpt > fa.maxThreadsPerBlock) --bg.G;
+      }
       bg.wpb = cfg.wpb;
       bg.ngrids = (int)k.members.size();
       std::vector<fdtd::PairParams<T>> params;
@@ -1940,10 +1963,11 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
 
 template <typename T, int LANES, int L>
 void launch_batch_strided_LL(const BatchGroup& g, cudaStream_t s) {
-  const int threads = g.P * LANES;
-  const size_t smem = 6 * (size_t)(g.P | 1) * LANES * sizeof(T);
-  fdtd::proc_strided_batch_kernel<T, LANES, L><<<(unsigned)g.nitems, threads, smem, s>>>(
-      (const fdtd::PairParams<T>*)g.d_params, (const fdtd::BatchTile*)g.d_index);
+  const int threads = g.G * g.P * LANES;
+  const size_t smem = fdtd::batch_params_bytes<T>(g.G) + (size_t)g.G * 6 * (g.P | 1) * LANES * sizeof(T);
+  const unsigned blocks = (unsigned)((g.nitems + g.G - 1) / g.G);
+  fdtd::proc_strided_batch_kernel<T, LANES, L><<<blocks, threads, smem, s>>>(
+      (const fdtd::PairParams<T>*)g.d_params, (const fdtd::BatchTile*)g.d_index, (int)g.nitems, g.G);
 }
 
 template <typename T, int L>
@@ -1953,9 +1977,24 @@ void launch_batch_rows_L(const BatchGroup& g, cudaStream_t s) {
       (const fdtd::PairParams<T>*)g.d_params, (const long long*)g.d_index, g.ngrids);
 }
 
+template <typename T, int LPL>
+void launch_batch_rows_pn(const BatchGroup& g, cudaStream_t s) {
+  const int wpb = g.wpb;
+  const long long warps = (g.nitems + (32 / LPL) - 1) / (32 / LPL);
+  fdtd::proc_rows_batch_pn_kernel<T, 8, LPL><<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, s>>>(
+      (const fdtd::PairParams<T>*)g.d_params, (const long long*)g.d_index, g.ngrids);
+}
+
 template <typename T>
 int launch_batch_group(const BatchGroup& g, cudaStream_t s) {
-  if (g.kind == 2) {
+  if (g.kind == 2 && g.lpl > 0) {
+    switch (g.lpl) {
+      case 8: launch_batch_rows_pn<T, 8>(g, s); break;
+      case 16: launch_batch_rows_pn<T, 16>(g, s); break;
+      case 32: launch_batch_rows_pn<T, 32>(g, s); break;
+      default: return FDTD_ERR_UNSUPPORTED;
+    }
+  } else if (g.kind == 2) {
     switch (g.L) {
       case 1: launch_batch_rows_L<T, 1>(g, s); break;
       case 2: launch_batch_rows_L<T, 2>(g, s); break;
@@ -2016,7 +2055,7 @@ int batch_one_step(fdtd_batch_t* b) {
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
 // every tuner's results: key -> five shape numbers (see the key makers)
-using TuneVal = std::array<int, 5>;
+using TuneVal = std::array<int, 6>;
 std::map<std::string, TuneVal> g_tune_cache;
 
 std::string device_name();
@@ -2050,7 +2089,8 @@ void tune_cache_load() {
   if (!f) return;
   char key[512];
   TuneVal v;
-  while (fscanf(f, "%511s %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4]) == 6) g_tune_cache[key] = v;
+  while (fscanf(f, "%511s %d %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 7)
+    g_tune_cache[key] = v;
   fclose(f);
 }
 
@@ -2068,7 +2108,7 @@ void tune_cache_put(const std::string& key, const TuneVal& v) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4]);
+  fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4], v[5]);
   fclose(f);
 }
 
@@ -2117,6 +2157,7 @@ int batch_tune_t(fdtd_batch_t* b) {
     b->cfg.lanes[1] = v[2];
     b->cfg.L[1] = v[3];
     b->cfg.wpb = v[4];
+    b->cfg.xpack = v[5];
     b->tuned = true;
     return FDTD_OK;
   }
@@ -2147,23 +2188,27 @@ int batch_tune_t(fdtd_batch_t* b) {
   }
   {
     double best = -1;
-    int pick = cfg.wpb;
-    for (int wpb : {4, 8, 16}) {
-      BatchCfg t = cfg;
-      t.wpb = wpb;
-      const double ms = time_direction<T>(b, t, 2, 3);
-      if (ms >= 0 && (best < 0 || ms < best)) {
-        best = ms;
-        pick = wpb;
+    int pick = cfg.wpb, pick_pack = cfg.xpack;
+    for (int xpack : {1, 0})
+      for (int wpb : {4, 8, 16}) {
+        BatchCfg t = cfg;
+        t.wpb = wpb;
+        t.xpack = xpack;
+        const double ms = time_direction<T>(b, t, 2, 3);
+        if (ms >= 0 && (best < 0 || ms < best)) {
+          best = ms;
+          pick = wpb;
+          pick_pack = xpack;
+        }
       }
-    }
     cfg.wpb = pick;
+    cfg.xpack = pick_pack;
     b->tune_ms[2] = best < 0 ? 0 : best;
   }
   BCK(cudaGetLastError());
   b->cfg = cfg;
   b->tuned = true;
-  tune_cache_put(key, {cfg.lanes[0], cfg.L[0], cfg.lanes[1], cfg.L[1], cfg.wpb});
+  tune_cache_put(key, {cfg.lanes[0], cfg.L[0], cfg.lanes[1], cfg.L[1], cfg.wpb, cfg.xpack});
   return FDTD_OK;
 }
 
@@ -2294,7 +2339,7 @@ int single_tune_t(fdtd_t* h) {
   h->output_valid = false;  // scratch was written
   CK(cudaGetLastError());
   tune_cache_put(key, {h->strided_cfg[0].lanes, h->strided_cfg[0].L, h->strided_cfg[1].lanes,
-                       h->strided_cfg[1].L, 0});
+                       h->strided_cfg[1].L, 0, 0});
   return FDTD_OK;
 }
 
@@ -2404,13 +2449,14 @@ int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step) {
   return FDTD_OK;
 }
 
-int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[5], double tune_ms[3]) {
+int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[6], double tune_ms[3]) {
   if (!b || !cfg) return FDTD_ERR_INVALID_ARG;
   cfg[0] = b->cfg.lanes[0];
   cfg[1] = b->cfg.L[0];
   cfg[2] = b->cfg.lanes[1];
   cfg[3] = b->cfg.L[1];
   cfg[4] = b->cfg.wpb;
+  cfg[5] = b->cfg.xpack;
   if (tune_ms)
     for (int k = 0; k < 3; ++k) tune_ms[k] = b->tune_ms[k];
   return FDTD_OK;
@@ -2431,11 +2477,13 @@ int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg) {
     if (!fn) return FDTD_ERR_INVALID_ARG;
   }
   if (cfg[4] != 4 && cfg[4] != 8 && cfg[4] != 16) return FDTD_ERR_INVALID_ARG;
+  if (cfg[5] != 0 && cfg[5] != 1) return FDTD_ERR_INVALID_ARG;
   b->cfg.lanes[0] = cfg[0];
   b->cfg.L[0] = cfg[1];
   b->cfg.lanes[1] = cfg[2];
   b->cfg.L[1] = cfg[3];
   b->cfg.wpb = cfg[4];
+  b->cfg.xpack = cfg[5];
   b->autotune = false;
   b->tuned = true;
   free_groups(b);
@@ -2721,7 +2769,7 @@ int adj_tune_t(fdtd_adj_t* a) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
-  tune_cache_put(key, {a->cfg[0].lanes, a->cfg[0].L, a->cfg[1].lanes, a->cfg[1].L, 0});
+  tune_cache_put(key, {a->cfg[0].lanes, a->cfg[0].L, a->cfg[1].lanes, a->cfg[1].L, 0, 0});
   return FDTD_OK;
 }
 

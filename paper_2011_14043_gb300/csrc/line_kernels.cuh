@@ -249,12 +249,16 @@ __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win,
 // first combine (a neighbour's carry) uses p as hi + lo; longer-range
 // products are FP32 (their weight is already below prod(-m)^2 over a
 // segment, far under the rounding of the result).
+// tid, nthr: this thread's index among the nthr threads that own the lines
+// (the whole block unless a block holds several tiles; nthr is a multiple
+// of 32 and equal for every tile of the block, so trip counts match).
 template <typename T, int LANES>
-__device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, int P, int PS, int PW, bool reverse) {
+__device__ __forceinline__ void chain_scan(T* sa, const T* sph, const T* spl, int P, int PS, int PW, bool reverse,
+                                           int tid, int nthr) {
   const unsigned FULL = 0xffffffffu;
   const int items = LANES * PW;
-  for (int first = 0; first < items; first += blockDim.x) {
-    const int it = first + (int)threadIdx.x;
+  for (int first = 0; first < items; first += nthr) {
+    const int it = first + tid;
     const int lane = it / PW;
     const int q = it % PW;
     const bool valid = (it < items) && (q < P);
@@ -282,7 +286,8 @@ __device__ __forceinline__ int chain_stride(int P) { return P | 1; }
 
 // Forward chain: returns y at the last node of segment s-1 (0 for s = 0).
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, HiLo<T> pm) {
+__device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, int lane, T a, HiLo<T> pm, int tid,
+                                                 int nthr) {
   const int PS = chain_stride(P);
   T* sa = sh;
   T* sph = sh + PS * LANES;
@@ -291,14 +296,15 @@ __device__ __forceinline__ T block_chain_forward(T* sh, int P, int PW, int s, in
   sph[lane * PS + s] = pm.hi;
   spl[lane * PS + s] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, false);
+  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, false, tid, nthr);
   __syncthreads();
   return (s > 0) ? sa[lane * PS + s - 1] : T(0);
 }
 
 // Backward chain: returns w at the first node of segment s+1 (0 for the last).
 template <typename T, int LANES>
-__device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, HiLo<T> pm) {
+__device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, int lane, T b, HiLo<T> pm, int tid,
+                                                  int nthr) {
   const int PS = chain_stride(P);
   T* sa = sh + 3 * PS * LANES;
   T* sph = sh + 4 * PS * LANES;
@@ -307,7 +313,7 @@ __device__ __forceinline__ T block_chain_backward(T* sh, int P, int PW, int s, i
   sph[lane * PS + s] = pm.hi;
   spl[lane * PS + s] = pm.lo;
   __syncthreads();
-  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, true);
+  chain_scan<T, LANES>(sa, sph, spl, P, PS, PW, true, tid, nthr);
   __syncthreads();
   return (s + 1 < P) ? sa[lane * PS + s + 1] : T(0);
 }
@@ -324,7 +330,11 @@ template <typename T, int LANES, int L, bool PER_NODE>
 __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
                                               const T (&E)[L], const T (&H)[L], T hm1, const T (&qn)[L],
                                               const T (&ibn)[L], const T (&ibl)[L], HiLo<T> ib_prev, T (&y)[L],
-                                              T& win) {
+                                              T& win, int tid = -1, int nthr = -1) {
+  if (tid < 0) {
+    tid = (int)threadIdx.x;
+    nthr = (int)blockDim.x;
+  }
   const bool conv = (j0 >= p.jc) && (j0 + L <= p.N);
   HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
@@ -334,14 +344,14 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
     else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
   }
   const int PW = pow2_at_least(P);
-  const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf);
+  const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf, tid, nthr);
   if constexpr (PER_NODE) {
     pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
   } else {
     if (conv) pb = phase_backward<T, L, 1>(p, j0, yin, ibn, ibl, ib_prev, y);
     else pb = phase_backward<T, L, 0>(p, j0, yin, ibn, ibl, ib_prev, y);
   }
-  win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb);
+  win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb, tid, nthr);
   if constexpr (PER_NODE) {
     phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
   } else {
@@ -1007,37 +1017,51 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
 // ---------------------------------------------------------------------------
 // Batched lines: many independent grids in one launch
 // ---------------------------------------------------------------------------
-// One launch covers the same pair of every grid of a batch.  y/z lines: one
-// block per tile of LANES lines of one grid, tile table entry =
-// (grid, x0, outer index); the block reads its grid's parameters once into
-// shared memory.  Blocks hold P = blockDim / LANES segments, enough for the
-// longest line of the batch; shorter lines leave their upper segments empty.
+// One launch covers the same pair of every grid of a batch.  y/z lines:
+// tiles of LANES lines of one grid (tile table entry = (grid, x0, outer
+// index)); a block holds G tiles, each on its own P * LANES threads (whole
+// warps) with its own copy of its grid's parameters and its own carry
+// buffers in shared memory, so that short lines still give blocks of a few
+// hundred threads.  All tiles of a launch have the same segment count P and
+// the same media kind (per-node or uniform), so every thread of a block
+// passes the same barriers.  Spare tiles of the last block take part in the
+// barriers with no active lane.
 struct BatchTile {
   int grid, x0, o, pad;
 };
 
+template <typename T>
+__host__ __device__ constexpr size_t batch_params_bytes(int G) {
+  return ((sizeof(PairParams<T>) * (size_t)G + 15) / 16) * 16;
+}
+
 template <typename T, int LANES, int L>
 __global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ params,
-                                          const BatchTile* __restrict__ tiles) {
+                                          const BatchTile* __restrict__ tiles, int ntiles, int G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) PairParams<T> ps;
-  const BatchTile tile = tiles[blockIdx.x];
+  const int tpt = blockDim.x / G;  // threads of one tile
+  const int sub = threadIdx.x / tpt;
+  const int tid = threadIdx.x % tpt;
+  const int P = tpt / LANES;
+  const int tix = blockIdx.x * G + sub;
+  const bool have = tix < ntiles;
+  const BatchTile tile = tiles[have ? tix : blockIdx.x * G];
+  PairParams<T>* ps = reinterpret_cast<PairParams<T>*>(smem_raw);
   {
-    // cooperative word copy of this grid's parameters
+    // cooperative word copy of this tile's grid parameters
     static_assert(sizeof(PairParams<T>) % 4 == 0, "word copy");
     const int* src = reinterpret_cast<const int*>(params + tile.grid);
-    int* dst = reinterpret_cast<int*>(&ps);
-    for (int k = threadIdx.x; k < (int)(sizeof(PairParams<T>) / 4); k += blockDim.x) dst[k] = src[k];
+    int* dst = reinterpret_cast<int*>(ps + sub);
+    for (int k = tid; k < (int)(sizeof(PairParams<T>) / 4); k += tpt) dst[k] = src[k];
   }
   __syncthreads();
-  const PairParams<T>& p = ps;
-  T* sh = reinterpret_cast<T*>(smem_raw);
-  const int lane = threadIdx.x % LANES;
-  const int s = threadIdx.x / LANES;
-  const int P = blockDim.x / LANES;
+  const PairParams<T>& p = ps[sub];
+  T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(G)) + (size_t)sub * 6 * chain_stride(P) * LANES;
+  const int lane = tid % LANES;
+  const int s = tid / LANES;
   const int i = tile.x0 + lane;
   const int o = tile.o;
-  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
+  const bool active = have && (i >= p.lane_lo) && (i < p.lane_hi);
   const long long base = (long long)o * p.os + i;
   const int j0 = s * L;
   const int N = p.N;
@@ -1080,8 +1104,8 @@ __global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ para
     }
   }
   T win;
-  if (pn) strided_solve<T, LANES, L, true>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
-  else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  if (pn) strided_solve<T, LANES, L, true>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
+  else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
 }
 
@@ -1108,6 +1132,140 @@ __global__ void proc_rows_batch_kernel(const PairParams<T>* __restrict__ params,
   } else {
     row_load<T, L, false>(p, line, E, H, qn, ibn, ibl);
     row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+  }
+}
+
+// Carry chains across the LPL lanes of one line (a warp holds 32 / LPL
+// lines; shuffles of width LPL keep the lines apart).
+template <typename T, int LPL>
+__device__ __forceinline__ T group_chain_forward(T a, HiLo<T> pm, int sl) {
+  const unsigned FULL = 0xffffffffu;
+  T pp = pm.hi;
+#pragma unroll
+  for (int d = 1; d < LPL; d <<= 1) {
+    const T a_up = __shfl_up_sync(FULL, a, d, LPL);
+    const T p_up = __shfl_up_sync(FULL, pp, d, LPL);
+    if (sl >= d) {
+      a = (d == 1) ? fma2(HiLo<T>{pp, pm.lo}, a_up, a) : fma(pp, a_up, a);
+      pp = pp * p_up;
+    }
+  }
+  const T yin = __shfl_up_sync(FULL, a, 1, LPL);
+  return sl == 0 ? T(0) : yin;
+}
+
+template <typename T, int LPL>
+__device__ __forceinline__ T group_chain_backward(T b, HiLo<T> pm, int sl) {
+  const unsigned FULL = 0xffffffffu;
+  T qq = pm.hi;
+#pragma unroll
+  for (int d = 1; d < LPL; d <<= 1) {
+    const T b_dn = __shfl_down_sync(FULL, b, d, LPL);
+    const T q_dn = __shfl_down_sync(FULL, qq, d, LPL);
+    if (sl + d < LPL) {
+      b = (d == 1) ? fma2(HiLo<T>{qq, pm.lo}, b_dn, b) : fma(qq, b_dn, b);
+      qq = qq * q_dn;
+    }
+  }
+  const T win = __shfl_down_sync(FULL, b, 1, LPL);
+  return sl == LPL - 1 ? T(0) : win;
+}
+
+// x lines of per-node grids in a batch, LPL lanes per line and L nodes per
+// lane (LPL * L >= N): short lines share a warp so that every lane still
+// streams L nodes of each array.  line_start as for proc_rows_batch_kernel.
+// Whole segments inside the line move as 16-byte vectors; the segment
+// holding the line end is read and written element by element, so no
+// access leaves the line.  Lines past the last one take part in the
+// shuffles without touching memory.
+template <typename T, int L, int LPL>
+__global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ params,
+                                          const long long* __restrict__ line_start, int ngrids) {
+  constexpr int LPW = 32 / LPL;  // lines per warp
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % LPL;
+  const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long total = line_start[ngrids];
+  if (gwarp * LPW >= total) return;  // whole warp leaves together
+  const long long gline = gwarp * LPW + lane / LPL;
+  const bool valid = gline < total;
+  const long long gl = valid ? gline : total - 1;
+  int lo = 0, hi = ngrids;  // line_start[lo] <= gl < line_start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (line_start[mid] <= gl) lo = mid;
+    else hi = mid;
+  }
+  const PairParams<T>& p = params[lo];
+  const long long line = gl - line_start[lo];
+  const int jo = p.o_lo + (int)(line % p.n_o);
+  const int ko = p.o2_lo + (int)(line / p.n_o);
+  const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const int j0 = sl * L;
+  const int N = p.N;
+  const bool full = j0 + L <= N;
+
+  T E[L], H[L], qn[L], ibn[L], ibl[L], y[L];
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = T(0);
+    H[t] = T(0);
+    qn[t] = T(0);
+    ibn[t] = T(0);
+    ibl[t] = T(0);
+  }
+  if (valid) {
+    if (full) {
+      load_seg<T, L>(p.e_in + base + j0, E);
+      load_seg<T, L>(p.h_in + base + j0, H);
+      load_seg<T, L>(p.nq + base + j0, qn);
+      load_seg<T, L>(p.nib + base + j0, ibn);
+      if constexpr (use_hilo<T>()) load_seg<T, L>(p.nibl + base + j0, ibl);
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        if (j0 + t < N) {
+          const long long at = base + j0 + t;
+          E[t] = p.e_in[at];
+          H[t] = p.h_in[at];
+          qn[t] = p.nq[at];
+          ibn[t] = p.nib[at];
+          if constexpr (use_hilo<T>()) ibl[t] = p.nibl[at];
+        }
+      }
+    }
+  }
+  const unsigned FULL = 0xffffffffu;
+  T hm1 = __shfl_up_sync(FULL, H[L - 1], 1, LPL);
+  HiLo<T> ib_prev = {__shfl_up_sync(FULL, ibn[L - 1], 1, LPL), T(0)};
+  if constexpr (use_hilo<T>()) ib_prev.lo = __shfl_up_sync(FULL, ibl[L - 1], 1, LPL);
+  if (sl == 0) {
+    hm1 = T(0);
+    ib_prev = {T(0), T(0)};
+  }
+  const HiLo<T> pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
+  const T yin = group_chain_forward<T, LPL>(y[L - 1], pf, sl);
+  const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
+  const T win = group_chain_backward<T, LPL>(y[0], pb, sl);
+  phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T wnext = (t + 1 < L) ? y[t + 1] : win;
+    H[t] = fma(p.kd, wnext - y[t], H[t]);
+    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
+  if (!valid) return;
+  if (full) {
+    store_seg<T, L>(p.e_out + base + j0, E);
+    store_seg<T, L>(p.h_out + base + j0, H);
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t < N) {
+        p.e_out[base + j0 + t] = E[t];
+        p.h_out[base + j0 + t] = H[t];
+      }
+    }
   }
 }
 

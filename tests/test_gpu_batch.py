@@ -48,7 +48,7 @@ def test_batch_matches_oracle_and_single(scheme, prec):
     steps = 9
     sims = [make_sim(sp, scheme, prec) for sp in specs]
     batch = Batch(sims)
-    batch.set_config(y=(16, 16), z=(16, 16))   # the handles' own segment length
+    batch.set_config(y=(16, 16), z=(16, 16), x_pack=0)   # the handles' own segment lengths
     batch.step(4)
     batch.step(steps - 4)            # a second call replays the same graph
     assert batch.launches_per_step() >= 2
@@ -100,15 +100,16 @@ def test_tuned_batch_matches_oracle(prec):
     specs = small_batch(77, 6)
     cfg = run_against_oracle(specs, "fadi", prec, 7, lambda b: None)
     assert cfg["y"][1] in (8, 16, 32) and cfg["z"][1] in (8, 16, 32)
-    assert cfg["x_warps_per_block"] in (4, 8, 16)
+    assert cfg["x_warps_per_block"] in (4, 8, 16) and cfg["x_pack"] in (0, 1)
 
 
-@pytest.mark.parametrize("prec,shape", [("f32", (32, 8)), ("f32", (16, 32)), ("f32", (32, 16)),
-                                        ("f64", (8, 32)), ("f64", (16, 8)), ("f64", (8, 16))])
-def test_fixed_batch_shapes_match_oracle(prec, shape):
+@pytest.mark.parametrize("prec,shape,xpack", [("f32", (32, 8), 1), ("f32", (16, 32), 0), ("f32", (32, 16), 1),
+                                              ("f64", (8, 32), 0), ("f64", (16, 8), 1), ("f64", (8, 16), 1)])
+def test_fixed_batch_shapes_match_oracle(prec, shape, xpack):
     specs = small_batch(91, 5)
-    cfg = run_against_oracle(specs, "flod", prec, 6, lambda b: b.set_config(y=shape, z=shape, x_warps_per_block=4))
-    assert cfg["y"] == shape and cfg["z"] == shape
+    cfg = run_against_oracle(specs, "flod", prec, 6,
+                             lambda b: b.set_config(y=shape, z=shape, x_warps_per_block=4, x_pack=xpack))
+    assert cfg["y"] == shape and cfg["z"] == shape and cfg["x_pack"] == xpack
 
 
 def test_tuner_cache_file(tmp_path, monkeypatch):
@@ -123,7 +124,7 @@ def test_tuner_cache_file(tmp_path, monkeypatch):
     b1.close()
     lines = path.read_text().splitlines()
     assert len(lines) == 1 and lines[0].split()[1:] == [str(v) for v in (*cfg1["y"], *cfg1["z"],
-                                                                       cfg1["x_warps_per_block"])]
+                                                                       cfg1["x_warps_per_block"], cfg1["x_pack"])]
     sims2 = [make_sim(sp, "fadi", "f32") for sp in specs]
     b2 = Batch(sims2)
     b2.step(1)
