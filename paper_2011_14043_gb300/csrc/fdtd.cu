@@ -990,17 +990,10 @@ bool graph_usable(const fdtd_t* h) {
 // them before the next procedure; a point source is added by kernels that
 // read each step's value from a device table indexed by a device step
 // counter.  Same kernels, same arguments, same results as one_step.
+int ensure_branches(fdtd_t* h);
+
 int step_graph(fdtd_t* h, int64_t nsteps) {
-  if (!h->g_run) {
-    CK(cudaStreamCreateWithFlags(&h->g_run, cudaStreamNonBlocking));
-    for (int b = 0; b < 3; ++b) {
-      CK(cudaStreamCreateWithFlags(&h->g_br[b], cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&h->g_join[b], cudaEventDisableTiming));
-    }
-    CK(cudaEventCreateWithFlags(&h->g_in, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->g_out, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->g_fork, cudaEventDisableTiming));
-  }
+  if (int rc = ensure_branches(h)) return rc;
   const bool src = h->src_comp >= 0;
   std::vector<const void*> ptrs(h->f, h->f + 6);
   if (!h->g_exec || ptrs != h->g_bound) {
@@ -1099,6 +1092,41 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
   h->launches += nsteps * h->g_kernels;
   h->steps += nsteps;
   return FDTD_OK;
+}
+
+// The three pairs of one procedure touch disjoint arrays: launch(q) for
+// q = 0..2 on three branch streams forked from and joined back into the
+// handle's stream (launches inside launch() go to h->stream, which points
+// at the branch meanwhile).
+int ensure_branches(fdtd_t* h) {
+  if (h->g_run) return FDTD_OK;
+  CK(cudaStreamCreateWithFlags(&h->g_run, cudaStreamNonBlocking));
+  for (int b = 0; b < 3; ++b) {
+    CK(cudaStreamCreateWithFlags(&h->g_br[b], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->g_join[b], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&h->g_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->g_out, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->g_fork, cudaEventDisableTiming));
+  return FDTD_OK;
+}
+
+template <typename F>
+int fork_pairs(fdtd_t* h, F&& launch) {
+  int rc = ensure_branches(h);
+  if (rc) return rc;
+  cudaStream_t home = h->stream;
+  CK(cudaEventRecord(h->g_fork, home));
+  for (int q = 0; q < 3 && rc == FDTD_OK; ++q) {
+    CK(cudaStreamWaitEvent(h->g_br[q], h->g_fork, 0));
+    h->stream = h->g_br[q];
+    rc = launch(q);
+    h->stream = home;
+    CK(cudaEventRecord(h->g_join[q], h->g_br[q]));
+    CK(cudaStreamWaitEvent(home, h->g_join[q], 0));
+  }
+  h->stream = home;
+  return rc;
 }
 
 int one_step(fdtd_t* h) {
@@ -2614,14 +2642,12 @@ int adj_forward_step(fdtd_adj_t* a, void* const* st, long long n, bool objective
   const double post_b = 0.5 * h->dt * source_value(h, n + 1);
   auto proc = [&](int slot, void* const* rec) -> int {
     const ProcCoef& P = h->proc[slot];
-    for (int q = 0; q < 3; ++q) {
+    return fork_pairs(h, [&](int q) -> int {
       const PairGeom& g = h->geom[P.op][q];
       fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, st, st);
       if (rec) p.d_out = (T*)rec[g.ec];
-      int rc = launch_pair<T>(h, g, p);
-      if (rc) return rc;
-    }
-    return FDTD_OK;
+      return launch_pair<T>(h, g, p);
+    });
   };
   int rc = proc(0, rec_a);
   if (rc) return rc;
@@ -2648,10 +2674,10 @@ template <typename T>
 int adj_procedure(fdtd_adj_t* a, int slot, void* const* rec, int only_axis = -1) {
   fdtd_t* h = a->h;
   const ProcCoef& P = h->proc[slot];
-  for (int q = 0; q < 3; ++q) {
+  auto pair = [&](int q) -> int {
     const PairGeom& g = h->geom[P.op][q];
-    if (g.empty()) continue;
-    if (only_axis >= 0 && (g.rows || (g.axis == AX_Y ? 0 : 1) != only_axis)) continue;
+    if (g.empty()) return FDTD_OK;
+    if (only_axis >= 0 && (g.rows || (g.axis == AX_Y ? 0 : 1) != only_axis)) return FDTD_OK;
     fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, -1.0, 1.0, a->lam, a->lam);
     const T ks = p.ks, kd = p.kd;
     p.ks = -kd;  // transposed couplings
@@ -2685,8 +2711,15 @@ int adj_procedure(fdtd_adj_t* a, int slot, void* const* rec, int only_axis = -1)
       else return FDTD_ERR_UNSUPPORTED;
     }
     CK(cudaGetLastError());
+    return FDTD_OK;
+  };
+  if (only_axis >= 0) {  // tuning: one direction, on the handle's stream
+    for (int q = 0; q < 3; ++q)
+      if (int rc = pair(q)) return rc;
+    return FDTD_OK;
   }
-  return FDTD_OK;
+  // the three transposed pairs write disjoint adjoint and gradient arrays
+  return fork_pairs(h, pair);
 }
 
 template <typename T>
