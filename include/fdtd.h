@@ -106,8 +106,11 @@ int fdtd_get_dt(const fdtd_t* h, double* dt);
 /* Per-cell relative permittivity / permeability (host, nz*ny*nx doubles,
  * each > 0 and finite; NULL means 1 everywhere).  eps at an E sample is the
  * mean of the in-domain cells sharing that edge; mu at an H sample the mean
- * of the cells sharing that face.  Non-uniform mu returns
- * FDTD_ERR_UNSUPPORTED.  Only valid before the first fdtd_step. */
+ * of the cells sharing that face.  Non-uniform mu runs the general-media
+ * kernels (a coupling and an off-diagonal per H face) and is built for grids
+ * with nx, ny, nz <= 256 (FDTD_ERR_UNSUPPORTED otherwise); batches and the
+ * reverse pass take uniform mu only.  Only valid before the first
+ * fdtd_step. */
 int fdtd_set_material(fdtd_t* h, const double* eps_r_cell, const double* mu_r_cell);
 
 /* Set one physical field component at the current time (compact Yee shape,

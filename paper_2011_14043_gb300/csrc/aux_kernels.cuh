@@ -42,7 +42,8 @@ __global__ void explicit_pair_kernel(const PairParams<T> p, int rows) {
       p.e_out[at] = p.e_in[at];
     }
     const T enext = (j + 1 < p.N) ? p.e_in[at + p.ls] : T(0);
-    p.h_out[at] = hf + p.kd * (enext - p.e_in[at]);
+    const T kd = p.nkd ? p.kd_scale * p.nkd[at] : p.kd;  // per-node mu: the face's coupling
+    p.h_out[at] = hf + kd * (enext - p.e_in[at]);
   }
 }
 

@@ -65,6 +65,9 @@ struct PairCoef {
   void* nib = nullptr;    //   1/beta_j (hi)
   void* nibl = nullptr;   //   1/beta_j (lo, FP32 only)
   double ks = 0, offh = 0, offl = 0;  // per-node: scaled-row coupling, off-diagonal
+  void* nkd = nullptr;    // per-node mu: H coupling of each face (field layout, T)
+  void* noffh = nullptr;  //   off-diagonal of each face, hi
+  void* noffl = nullptr;  //   off-diagonal of each face, lo (FP32 only)
 };
 
 struct StridedCfg {
@@ -108,6 +111,9 @@ struct fdtd_s {
   double eps_r = 1.0, mu_r = 1.0;          // uniform media
   double* eps_node[3] = {nullptr, nullptr, nullptr};  // per-node eps_r at E samples (device)
   std::vector<double> eps_host[3];  // the same on the host, only while coefficients are built
+  bool mu_var = false;              // per-node mu (general media kernels)
+  double* mu_node[3] = {nullptr, nullptr, nullptr};   // per-face mu_r at H samples (device)
+  std::vector<double> mu_host[3];   // the same on the host, only while coefficients are built
   bool poisoned = false;
   bool pending_init = true;   // FADI/FLOD2: state holds the physical field
   bool output_valid = false;  // scratch holds the physical field of this step
@@ -283,12 +289,40 @@ void free_coef(ProcCoef& pc) {
     if (c.nq) cudaFree(c.nq);
     if (c.nib) cudaFree(c.nib);
     if (c.nibl) cudaFree(c.nibl);
+    if (c.nkd) cudaFree(c.nkd);
+    if (c.noffh) cudaFree(c.noffh);
+    if (c.noffl) cudaFree(c.noffl);
     c = PairCoef();
   }
   pc.valid = false;
 }
 
 // eps_r at every E sample: mean of the in-domain cells sharing the edge.
+// mu_r at the H samples of component c (HX, HY, HZ): the mean of the two
+// cells sharing the face (cells outside the domain skipped).
+void face_mu(const fdtd_t* h, const double* mr, int c, std::vector<double>& out) {
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  out.assign((size_t)h->count, 1.0);
+  int sx, sy, sz;
+  comp_extent(c, nx, ny, nz, &sx, &sy, &sz);
+  for (int k = 0; k < sz; ++k)
+    for (int j = 0; j < sy; ++j)
+      for (int i = 0; i < sx; ++i) {
+        double s = 0;
+        int n = 0;
+        for (int a = -1; a <= 0; ++a) {
+          int ci = i, cj = j, ck = k;
+          if (c == HX) ci = i + a;   // Hx (i, j+1/2, k+1/2): cells (i-1..i, j, k)
+          if (c == HY) cj = j + a;   // Hy (i+1/2, j, k+1/2): cells (i, j-1..j, k)
+          if (c == HZ) ck = k + a;   // Hz (i+1/2, j+1/2, k): cells (i, j, k-1..k)
+          if (ci < 0 || cj < 0 || ck < 0 || ci >= nx || cj >= ny || ck >= nz) continue;
+          s += mr[((size_t)ck * ny + cj) * nx + ci];
+          ++n;
+        }
+        out[(size_t)k * h->plane + (size_t)j * h->pitch + i] = n ? s / n : 1.0;
+      }
+}
+
 void edge_eps(const fdtd_t* h, const double* er, int c, std::vector<double>& out) {
   const int nx = h->nx, ny = h->ny, nz = h->nz;
   out.assign((size_t)h->count, 0.0);
@@ -420,6 +454,15 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       c.offl = f32 ? (double)(float)(off - c.offh) : 0.0;
       std::vector<double> nq((size_t)h->count, 0.0), nib((size_t)h->count, 0.0), nibl;
       if (f32) nibl.assign((size_t)h->count, 0.0);
+      // per-node mu: each face f (between nodes f and f+1) has its own
+      // coupling kd_f and off-diagonal -|ks| |kd_f| / 2
+      std::vector<double> nkd, noffh, noffl;
+      if (h->mu_var) {
+        nkd.assign((size_t)h->count, 0.0);
+        noffh.assign((size_t)h->count, 0.0);
+        if (f32) noffl.assign((size_t)h->count, 0.0);
+      }
+      const double* mr = h->mu_var ? h->mu_host[g.hc - 3].data() : nullptr;
       const double* er = h->eps_host[g.ec].data();
       const long long nl = g.n_lines();
       for (long long line = 0; line < nl; ++line) {
@@ -435,12 +478,40 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
           base = (long long)o * g.os + i;
         }
         double ibm = 0;
+        if (!h->mu_var) {
+          for (int j = 1; j <= g.N - 1; ++j) {
+            const long long at = base + (long long)j * g.ls;
+            const double b = std::fabs(hh) / (2.0 * kEps0 * er[at]);
+            const double q = rnd(1.0 / b);
+            const double diag = q / 2.0 + kk;
+            const double beta = diag - off * off * ibm;
+            const double ib = 1.0 / beta;
+            nq[at] = q;
+            nib[at] = rnd(ib);
+            if (f32) nibl[at] = (double)(float)(ib - nib[at]);
+            ibm = ib;
+          }
+          continue;
+        }
+        // kk_f = |ks| |kd_f| of the faces, from the kd_f the kernel uses
+        std::vector<double> kkf((size_t)g.N, 0.0);
+        for (int f = 0; f < g.N; ++f) {
+          const long long at = base + (long long)f * g.ls;
+          const double kdf = rnd(g.sign * (hh / (2.0 * kMu0 * mr[at])) / de);
+          const double kkv = std::fabs(c.ks) * std::fabs(kdf);
+          const double offf = -kkv / 2.0;
+          kkf[(size_t)f] = kkv;
+          nkd[at] = kdf;
+          noffh[at] = rnd(offf);
+          if (f32) noffl[at] = (double)(float)(offf - noffh[at]);
+        }
         for (int j = 1; j <= g.N - 1; ++j) {
           const long long at = base + (long long)j * g.ls;
           const double b = std::fabs(hh) / (2.0 * kEps0 * er[at]);
           const double q = rnd(1.0 / b);
-          const double diag = q / 2.0 + kk;
-          const double beta = diag - off * off * ibm;
+          const double diag = q / 2.0 + (kkf[(size_t)j] + kkf[(size_t)j - 1]) / 2.0;
+          const double offm = -kkf[(size_t)j - 1] / 2.0;  // face j-1, between nodes j-1 and j
+          const double beta = diag - offm * offm * ibm;
           const double ib = 1.0 / beta;
           nq[at] = q;
           nib[at] = rnd(ib);
@@ -452,6 +523,11 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       if (rc) return rc;
       if ((rc = upload_any(h, &c.nib, nib))) return rc;
       if (f32 && (rc = upload_any(h, &c.nibl, nibl))) return rc;
+      if (h->mu_var) {
+        if ((rc = upload_any(h, &c.nkd, nkd))) return rc;
+        if ((rc = upload_any(h, &c.noffh, noffh))) return rc;
+        if (f32 && (rc = upload_any(h, &c.noffl, noffl))) return rc;
+      }
     }
   }
   P.valid = true;
@@ -522,6 +598,10 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.offh = (T)c.offh;
   p.offl = (T)c.offl;
   p.d_out = nullptr;
+  p.nkd = (const T*)c.nkd;
+  p.noffh = (const T*)c.noffh;
+  p.noffl = (const T*)c.noffl;
+  p.kd_scale = (T)(sgn * kd_mul);
   (void)h;
   return p;
 }
@@ -739,9 +819,41 @@ int resolve_events(fdtd_t* h) {
   return FDTD_OK;
 }
 
+// General media (per-node mu): y/z lines 16 lanes x 8 nodes, x lines one
+// warp per line (lines of at most 256 cells, checked by set_material).
+template <typename T>
+int launch_pair_gm(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
+  if (g.rows) {
+    const int wpb = 8;
+    const unsigned blocks = (unsigned)((g.n_lines() + wpb - 1) / wpb);
+    switch (pick_rows_L(g.N)) {
+      case 1: fdtd::proc_rows_gm_kernel<T, 1><<<blocks, wpb * 32, 0, h->stream>>>(p); break;
+      case 2: fdtd::proc_rows_gm_kernel<T, 2><<<blocks, wpb * 32, 0, h->stream>>>(p); break;
+      case 4: fdtd::proc_rows_gm_kernel<T, 4><<<blocks, wpb * 32, 0, h->stream>>>(p); break;
+      case 8: fdtd::proc_rows_gm_kernel<T, 8><<<blocks, wpb * 32, 0, h->stream>>>(p); break;
+      default: return FDTD_ERR_UNSUPPORTED;
+    }
+  } else {
+    constexpr int LANES = 16, L = 8;
+    const int P = segments(g.N, L, LANES);
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, fdtd::proc_strided_gm_kernel<T, LANES, L>));
+    if (P > 32 || P * LANES > fa.maxThreadsPerBlock) return FDTD_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((g.lane_hi + LANES - 1) / LANES), (unsigned)g.n_o);
+    const size_t smem = 6 * (size_t)(P | 1) * LANES * sizeof(T);
+    fdtd::proc_strided_gm_kernel<T, LANES, L><<<grid, P * LANES, smem, h->stream>>>(p);
+  }
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
 template <typename T>
 int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   if (g.empty()) return FDTD_OK;
+  if (p.nkd) {
+    h->launches++;
+    return launch_pair_gm<T>(h, g, p);
+  }
   const bool pn = h->per_node;
   const int cls = g.axis == AX_Y ? 0 : (g.axis == AX_Z ? 1 : 2);
   int ev0 = -1, ev1 = -1;
@@ -1357,7 +1469,7 @@ int energy_of(fdtd_t* h, void* const* arr, double* out) {
   }
   for (int c = 0; c < 6; ++c) {
     const double w = c < 3 ? kEps0 * (h->per_node ? 1.0 : h->eps_r) : kMu0 * h->mu_r;
-    const double* wv = (c < 3 && h->per_node) ? h->eps_node[c] : nullptr;
+    const double* wv = c < 3 ? (h->per_node ? h->eps_node[c] : nullptr) : (h->mu_var ? h->mu_node[c - 3] : nullptr);
     h->launches++;
     fdtd::weighted_sumsq_kernel<T><<<blocks, 256, 0, h->stream>>>((const T*)arr[c], wv, w, h->count,
                                                                   h->d_partial + (size_t)c * blocks);
@@ -1508,8 +1620,10 @@ int fdtd_destroy(fdtd_t* h) {
     if (h->scratch[c]) cudaFree(h->scratch[c]);
   }
   for (auto& p : h->proc) free_coef(p);
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < 3; ++c) {
     if (h->eps_node[c]) cudaFree(h->eps_node[c]);
+    if (h->mu_node[c]) cudaFree(h->mu_node[c]);
+  }
   if (h->d_probe) cudaFree(h->d_probe);
   if (h->d_stash) cudaFree(h->d_stash);
   if (h->d_partial) cudaFree(h->d_partial);
@@ -1568,27 +1682,45 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
       if (mu[q] != m0) m_uniform = false;
     }
   }
-  if (!m_uniform) return FDTD_ERR_UNSUPPORTED;
-  for (int c = 0; c < 3; ++c)
+  // per-node mu runs the general-media kernels, built for lines of at most
+  // 256 cells along y and z and 256 along x
+  if (!m_uniform && (h->nx > 256 || h->ny > 256 || h->nz > 256)) return FDTD_ERR_UNSUPPORTED;
+  graph_release(h);
+  for (int c = 0; c < 3; ++c) {
     if (h->eps_node[c]) { cudaFree(h->eps_node[c]); h->eps_node[c] = nullptr; }
-  h->mu_r = m0;
+    if (h->mu_node[c]) { cudaFree(h->mu_node[c]); h->mu_node[c] = nullptr; }
+  }
+  h->mu_var = !m_uniform;
+  h->mu_r = h->mu_var ? 1.0 : m0;
   // tune[1] bit 1 keeps per-node coefficients even for a uniform eps
-  h->per_node = !e_uniform || (h->desc.tune[1] & 2) != 0;
+  h->per_node = !e_uniform || h->mu_var || (h->desc.tune[1] & 2) != 0;
   h->eps_r = h->per_node ? 1.0 : e0;
   h->shape_tuned = false;
-  graph_release(h);
   int rc = FDTD_OK;
   if (h->per_node) {
+    std::vector<double> ones;
+    if (!eps) ones.assign(nc, 1.0);
     for (int c = 0; c < 3; ++c) {
-      edge_eps(h, eps, c, h->eps_host[c]);
+      edge_eps(h, eps ? eps : ones.data(), c, h->eps_host[c]);
       CK(dev_malloc((void**)&h->eps_node[c], sizeof(double) * h->eps_host[c].size()));
       CK(cudaMemcpyAsync(h->eps_node[c], h->eps_host[c].data(), sizeof(double) * h->eps_host[c].size(),
                          cudaMemcpyHostToDevice, h->stream));
     }
+    if (h->mu_var) {
+      for (int c = 0; c < 3; ++c) {
+        face_mu(h, mu, HX + c, h->mu_host[c]);
+        CK(dev_malloc((void**)&h->mu_node[c], sizeof(double) * h->mu_host[c].size()));
+        CK(cudaMemcpyAsync(h->mu_node[c], h->mu_host[c].data(), sizeof(double) * h->mu_host[c].size(),
+                           cudaMemcpyHostToDevice, h->stream));
+      }
+    }
     CK(cudaStreamSynchronize(h->stream));
   }
   rc = build_all_coefs(h);
-  for (int c = 0; c < 3; ++c) std::vector<double>().swap(h->eps_host[c]);
+  for (int c = 0; c < 3; ++c) {
+    std::vector<double>().swap(h->eps_host[c]);
+    std::vector<double>().swap(h->mu_host[c]);
+  }
   h->output_valid = false;
   if (rc) return rc;
   return refresh_src_scale(h);
@@ -2386,7 +2518,7 @@ int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batc
     if (h->poisoned) return FDTD_ERR_STATE;
     if (h->scheme != handles[0]->scheme || h->prec != handles[0]->prec) return FDTD_ERR_INVALID_ARG;
     if (h->stream != (cudaStream_t)stream) return FDTD_ERR_INVALID_ARG;
-    if (h->src_comp >= 0 || h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
+    if (h->src_comp >= 0 || h->nprobes > 0 || h->mu_var) return FDTD_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (handles[j] == h) return FDTD_ERR_INVALID_ARG;
   }
@@ -2924,7 +3056,7 @@ int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t c
   if (!h || !block || !out || nsteps < 1 || checkpoint_every < 1) return FDTD_ERR_INVALID_ARG;
   *out = nullptr;
   if (h->poisoned) return FDTD_ERR_STATE;
-  if (h->scheme != FDTD_FADI || !h->per_node) return FDTD_ERR_UNSUPPORTED;
+  if (h->scheme != FDTD_FADI || !h->per_node || h->mu_var) return FDTD_ERR_UNSUPPORTED;
   if (!h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
   if (h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
   const int i0 = block[0], i1 = block[1], j0 = block[2], j1 = block[3], k0 = block[4], k1 = block[5];

@@ -80,6 +80,13 @@ struct PairParams {
   int* err;              // set to 1 when a bounded device wait gives up
   T* d_out;              // per-node kernels: when set, also E_in - E_out per E node
                          // (the reverse pass's record of the procedure)
+  // per-node mu (general media): face f between nodes f and f+1 (stored at
+  // node f) has its own H coupling kd_f = kd_scale * nkd[f] and off-diagonal
+  // noffh[f] + noffl[f]; nullptr when mu is uniform
+  const T* nkd;
+  const T* noffh;
+  const T* noffl;
+  T kd_scale;
 };
 
 // ---------------------------------------------------------------------------
@@ -1259,6 +1266,215 @@ __global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ para
     store_seg<T, L>(p.e_out + base + j0, E);
     store_seg<T, L>(p.h_out + base + j0, H);
   } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t < N) {
+        p.e_out[base + j0 + t] = E[t];
+        p.h_out[base + j0 + t] = H[t];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// General media: per-node eps and mu.  The scaled symmetric rows of the
+// per-node form keep their shape, but each face has its own off-diagonal
+// off_f = -|ks| |kd_f| / 2 and H coupling kd_f: m_j = off_{j-1} / beta_{j-1},
+// c_j = off_j / beta_j.  offh/offl[t]: face j0 + t; off_prev: face j0 - 1.
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__device__ __forceinline__ HiLo<T> gm_m(int t, const T (&ibn)[L], const T (&ibl)[L], HiLo<T> ib_prev,
+                                        const T (&offh)[L], const T (&offl)[L], HiLo<T> off_prev) {
+  if (t == 0) return dd_mul(off_prev, ib_prev);
+  return dd_mul(HiLo<T>{offh[t - 1], offl[t - 1]}, HiLo<T>{ibn[t - 1], ibl[t - 1]});
+}
+template <typename T, int L>
+__device__ __forceinline__ HiLo<T> gm_c(int t, const T (&ibn)[L], const T (&ibl)[L], const T (&offh)[L],
+                                        const T (&offl)[L]) {
+  return dd_mul(HiLo<T>{offh[t], offl[t]}, HiLo<T>{ibn[t], ibl[t]});
+}
+
+template <typename T, int L>
+__device__ __forceinline__ HiLo<T> gm_forward(const PairParams<T>& p, const T (&E)[L], const T (&H)[L], T hm1,
+                                              const T (&qn)[L], const T (&ibn)[L], const T (&ibl)[L],
+                                              HiLo<T> ib_prev, const T (&offh)[L], const T (&offl)[L],
+                                              HiLo<T> off_prev, T (&y)[L]) {
+  T pf = T(1), hprev = hm1;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T r = fma(qn[t], E[t], p.ks * (H[t] - hprev));
+    hprev = H[t];
+    const HiLo<T> m = gm_m<T, L>(t, ibn, ibl, ib_prev, offh, offl, off_prev);
+    y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
+    pf *= -m.hi;
+  }
+  return {pf, T(0)};
+}
+
+template <typename T, int L>
+__device__ __forceinline__ HiLo<T> gm_backward(T yin, const T (&ibn)[L], const T (&ibl)[L], HiLo<T> ib_prev,
+                                               const T (&offh)[L], const T (&offl)[L], HiLo<T> off_prev,
+                                               T (&y)[L]) {
+  T q = T(1);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    q *= -gm_m<T, L>(t, ibn, ibl, ib_prev, offh, offl, off_prev).hi;
+    y[t] = fma(q, yin, y[t]);
+  }
+  T pb = T(1), wn = T(0);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    const HiLo<T> c = gm_c<T, L>(t, ibn, ibl, offh, offl);
+    T u;
+    if constexpr (use_hilo<T>()) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ibl[t]));
+    else u = -c.hi * wn;
+    y[t] = fma(y[t], ibn[t], u);
+    wn = y[t];
+    pb *= -c.hi;
+  }
+  return {pb, T(0)};
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void gm_fix(T win, const T (&ibn)[L], const T (&ibl)[L], const T (&offh)[L],
+                                       const T (&offl)[L], T (&y)[L]) {
+  T q = T(1);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    q *= -gm_c<T, L>(t, ibn, ibl, offh, offl).hi;
+    y[t] = fma(q, win, y[t]);
+  }
+}
+
+// Lines along y or z in general media (one block per LANES lines, loads
+// straight from HBM).
+template <typename T, int LANES, int L>
+__global__ void proc_strided_gm_kernel(const PairParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sh = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x % LANES;
+  const int s = threadIdx.x / LANES;
+  const int P = blockDim.x / LANES;
+  const int i = blockIdx.x * LANES + lane;
+  const int o = p.o_lo + blockIdx.y;
+  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
+  const long long base = (long long)o * p.os + i;
+  const int j0 = s * L;
+  const int N = p.N;
+  const long long ls = p.ls;
+
+  T E[L], H[L], y[L], qn[L], ibn[L], ibl[L], offh[L], offl[L], kd[L];
+  HiLo<T> ib_prev = {T(0), T(0)}, off_prev = {T(0), T(0)};
+  T hm1 = T(0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = H[t] = qn[t] = ibn[t] = ibl[t] = offh[t] = offl[t] = kd[t] = T(0);
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int j = j0 + t;
+      if (j < N) {
+        const long long at = base + (long long)j * ls;
+        E[t] = p.e_in[at];
+        H[t] = p.h_in[at];
+        qn[t] = p.nq[at];
+        ibn[t] = p.nib[at];
+        offh[t] = p.noffh[at];
+        kd[t] = p.nkd[at];
+        if constexpr (use_hilo<T>()) {
+          ibl[t] = p.nibl[at];
+          offl[t] = p.noffl[at];
+        }
+      }
+    }
+    if (j0 > 0 && j0 - 1 < N) {
+      const long long at = base + (long long)(j0 - 1) * ls;
+      hm1 = p.h_in[at];
+      ib_prev.hi = p.nib[at];
+      off_prev.hi = p.noffh[at];
+      if constexpr (use_hilo<T>()) {
+        ib_prev.lo = p.nibl[at];
+        off_prev.lo = p.noffl[at];
+      }
+    }
+  }
+  const int PW = pow2_at_least(P);
+  const HiLo<T> pf = gm_forward<T, L>(p, E, H, hm1, qn, ibn, ibl, ib_prev, offh, offl, off_prev, y);
+  const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], pf, (int)threadIdx.x, (int)blockDim.x);
+  const HiLo<T> pb = gm_backward<T, L>(yin, ibn, ibl, ib_prev, offh, offl, off_prev, y);
+  const T win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb, (int)threadIdx.x, (int)blockDim.x);
+  gm_fix<T, L>(win, ibn, ibl, offh, offl, y);
+  if (!active) return;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const int j = j0 + t;
+    if (j < N) {
+      const long long at = base + (long long)j * ls;
+      const T wnext = (t + 1 < L) ? y[t + 1] : win;
+      p.e_out[at] = fma(p.alpha, y[t], p.beta * E[t]);
+      p.h_out[at] = fma(p.kd_scale * kd[t], wnext - y[t], H[t]);
+    }
+  }
+}
+
+// x lines in general media: one warp per line, L = nodes per lane (32 L >= N;
+// the row pitch is >= 32 L, so whole-segment loads stay inside the row).
+template <typename T, int L>
+__global__ void proc_rows_gm_kernel(const PairParams<T> p) {
+  const unsigned FULL = 0xffffffffu;
+  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
+  const int lane = threadIdx.x & 31;
+  const int jo = p.o_lo + (int)(line % p.n_o);
+  const int ko = p.o2_lo + (int)(line / p.n_o);
+  const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const int j0 = lane * L;
+  const int N = p.N;
+  T E[L], H[L], y[L], qn[L], ibn[L], ibl[L], offh[L], offl[L], kd[L];
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = H[t] = qn[t] = ibn[t] = ibl[t] = offh[t] = offl[t] = kd[t] = T(0);
+  }
+  if (j0 < N) {
+    load_seg<T, L>(p.e_in + base + j0, E);
+    load_seg<T, L>(p.h_in + base + j0, H);
+    load_seg<T, L>(p.nq + base + j0, qn);
+    load_seg<T, L>(p.nib + base + j0, ibn);
+    load_seg<T, L>(p.noffh + base + j0, offh);
+    load_seg<T, L>(p.nkd + base + j0, kd);
+    if constexpr (use_hilo<T>()) {
+      load_seg<T, L>(p.nibl + base + j0, ibl);
+      load_seg<T, L>(p.noffl + base + j0, offl);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    if (j0 + t >= N) E[t] = H[t] = qn[t] = ibn[t] = ibl[t] = offh[t] = offl[t] = kd[t] = T(0);
+  }
+  T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
+  HiLo<T> ib_prev = {__shfl_up_sync(FULL, ibn[L - 1], 1), __shfl_up_sync(FULL, ibl[L - 1], 1)};
+  HiLo<T> off_prev = {__shfl_up_sync(FULL, offh[L - 1], 1), __shfl_up_sync(FULL, offl[L - 1], 1)};
+  if (lane == 0) {
+    hm1 = T(0);
+    ib_prev = {T(0), T(0)};
+    off_prev = {T(0), T(0)};
+  }
+  const HiLo<T> pf = gm_forward<T, L>(p, E, H, hm1, qn, ibn, ibl, ib_prev, offh, offl, off_prev, y);
+  const T yin = warp_chain_forward<T>(y[L - 1], pf);
+  const HiLo<T> pb = gm_backward<T, L>(yin, ibn, ibl, ib_prev, offh, offl, off_prev, y);
+  const T win = warp_chain_backward<T>(y[0], pb);
+  gm_fix<T, L>(win, ibn, ibl, offh, offl, y);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T wnext = (t + 1 < L) ? y[t + 1] : win;
+    H[t] = fma(p.kd_scale * kd[t], wnext - y[t], H[t]);
+    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
+  if (j0 + L <= N) {
+    store_seg<T, L>(p.e_out + base + j0, E);
+    store_seg<T, L>(p.h_out + base + j0, H);
+  } else if (j0 < N) {
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       if (j0 + t < N) {

@@ -281,3 +281,54 @@ def test_graph_steps_bit_identical_to_stream_steps(scheme, media, prec):
     P = oracle_problem(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, eps=eps, source=src)
     ref, _, _ = S.run_fundamental(P, scheme, u0, steps)
     check(a, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["fadi", "flod", "fss", "flod2"])
+def test_general_media_eps_and_mu_vs_oracle(scheme, prec):
+    """Per-cell eps and mu (mu averaged over the two cells of each H face):
+    every scheme, ragged grid, a dipole and a probe, against the oracle."""
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 26, 21, 18
+    d = (1e-3, 0.9e-3, 1.2e-3)
+    g = G.Grid(nx, ny, nz, *d)
+    dt = 5.0 * g.dt_cfl()
+    rng = np.random.default_rng(61)
+    eps = rng.uniform(1.0, 5.0, (nz, ny, nx))
+    mu = rng.uniform(1.0, 3.0, (nz, ny, nx))
+    u0 = random_fields(nx, ny, nz, seed=62)
+    steps = 10
+    cur = W.dipole_current((np.arange(steps + 1) + 0.5) * dt * 30) * 1e-4
+    src = ("ez", 12, 10, 9, cur)
+    P = oracle_problem(nx, ny, nz, *d, dt, eps=eps, source=src)
+    P = S.Problem(g, dt, eps_r_cell=eps, mu_r_cell=mu, source=P.source)
+    probes = [("hy", 7, 8, 5)] if scheme != "flod2" else []
+    ref, _, series = S.run_fundamental(P, scheme, u0, steps, probes=probes)
+    sim = Simulation(nx, ny, nz, *d, scheme=scheme, precision=prec, dt=dt)
+    sim.set_material(eps, mu)
+    sim.set_fields(u0)
+    sim.set_source(*src)
+    pids = [sim.add_probe(*p) for p in probes]
+    sim.step(steps)
+    out = {c: sim.get_field(c).astype(np.float64) for c in G.COMPS}
+    check(out, ref, prec)
+    for pid, s_ref in zip(pids, series):
+        got = sim.get_probe(pid, steps)
+        assert np.max(np.abs(got - s_ref)) <= TOL[prec] * 10 * np.max(np.abs(s_ref))
+    assert sim.energy()[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec] * 10)
+    sim.close()
+
+
+def test_general_media_is_rejected_where_not_built():
+    """Batches and the reverse pass take uniform mu only; non-uniform mu needs
+    lines of at most 256 cells."""
+    from paper_2011_14043_gb300 import Batch, FdtdError, Simulation
+    mu = np.ones((8, 9, 10))
+    mu[2:4, 3:5, 4:6] = 2.0
+    a = Simulation(10, 9, 8, 1e-3, scheme="fadi", precision="f32", cfl=3.0)
+    a.set_material(None, mu)
+    with pytest.raises(FdtdError):
+        Batch([a])
+    big = Simulation(300, 4, 4, 1e-3, scheme="flod", precision="f32", cfl=3.0)
+    with pytest.raises(FdtdError):
+        big.set_material(None, np.ones((4, 4, 300)) + np.arange(300) * 1e-3)
