@@ -70,19 +70,48 @@ def workload_fields(n):
     return W.mode_sum_fields(modes, n, n, n)
 
 
+def kernel_sources_sha1() -> str:
+    """sha1 of the line kernels and of the host code that picks them."""
+    import hashlib
+    h = hashlib.sha1()
+    for name in ("line_kernels.cuh", "fdtd.cu"):
+        with open(os.path.join(ROOT, "paper_2011_14043_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def recorded_traffic(kernel_class: str):
     """DRAM bytes per launch of the kernel of one line direction from the
     committed ncu capture (profiles/dram_traffic.json), or None when the
-    kernels changed since that capture."""
-    import hashlib
+    kernels or their launch choices changed since that capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        src = os.path.join(ROOT, "paper_2011_14043_gb300", "csrc", "line_kernels.cuh")
-        if hashlib.sha1(open(src, "rb").read()).hexdigest() != rec["line_kernels_sha1"]:
+        if kernel_sources_sha1() != rec["sources_sha1"]:
             return None
         return rec["classes"][kernel_class]["traffic_bytes_per_launch"]
     except Exception:
         return None
+
+
+# FP64 operations of the line solve per node of one pair (uniform media):
+# RHS 1 sub + 1 FMA, forward sweep 1 FMA, forward carry fix 1 FMA, backward
+# sweep 1 mul + 1 FMA, backward carry fix 1 FMA, H update 1 sub + 1 FMA,
+# E update 1 mul + 1 FMA: 7 FMAs + 4 adds/muls = 18 flops (an FMA counts 2),
+# 11 FP64 instructions.  Six pairs per FADI step; the carry scans add about
+# one flop per node and are left out.
+FP64_FLOPS_PER_CELL_STEP = 6 * 18
+FP64_INSTR_PER_CELL_STEP = 6 * 11
+
+
+def fp64_alu_roofline(cell_steps_per_s: float) -> dict:
+    """The FP64 form against the device's measured FP64 FMA rate."""
+    from paper_2011_14043_gb300 import probe_fp64_fma
+    peak = probe_fp64_fma(20000) / 1e9
+    achieved = FP64_FLOPS_PER_CELL_STEP * cell_steps_per_s / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+            "peak_kind": "measured: FP64 FMA microbenchmark (fdtd_probe_fp64_fma)",
+            "flops_per_cell_step": FP64_FLOPS_PER_CELL_STEP,
+            "fp64_pipe_frac": FP64_INSTR_PER_CELL_STEP * cell_steps_per_s / (peak * 1e9 / 2)}
 
 
 def measured_peaks():
@@ -543,7 +572,8 @@ def main():
         r64 = run_gpu(a, "f64", fields, time_kernels=False)
         v64 = cells * a.steps / (r64["ms"] / 1e3)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / a.steps, "steps": a.steps,
-                        "hbm_frac": 192.0 * cells * a.steps / (r64["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+                        "hbm_frac": 192.0 * cells * a.steps / (r64["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "roofline": fp64_alu_roofline(v64)}
     if not args.no_e2e:
         e = run_e2e(args, "f32", fields)
         ev = ws * cells * args.steps / e["s"]

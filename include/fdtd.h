@@ -68,11 +68,12 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * dt_CFL = 1 / (c0 * sqrt(1/dx^2 + 1/dy^2 [+ 1/dz^2 when nz > 1])),
  * c0 = 299792458 m/s.  tune[] are kernel-shape overrides (0 = automatic):
  * tune[0] nodes per thread of the non-persistent y/z-line kernels (8, 16 or
- * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel;
+ * 32); tune[1] bit 0 set: do not use the persistent TMA-fed y/z kernel
+ * (FP32 fields; FP64 fields always run the direct-load y/z kernel);
  * tune[1] bit 1 set: per-node (inhomogeneous-media) coefficients even when
  * fdtd_set_material receives a uniform eps (needed by fdtd_adj_create);
- * tune[1] bit 2 set: the TMA-fed kernel writes its outputs with register
- * stores instead of TMA stores; tune[1] bit 3 set: fdtd_step launches the
+ * tune[1] bit 2 set: the TMA-fed kernel stages its outputs in shared memory
+ * and writes them with TMA stores instead of register stores; tune[1] bit 3 set: fdtd_step launches the
  * kernels one by one instead of replaying a captured step graph. */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
@@ -293,6 +294,15 @@ int fdtd_debug_fail_alloc(int64_t n);
  * arrives first and the call returns FDTD_OK.  limit_ns in (0, 1e10];
  * synchronises stream (NULL = legacy default stream). */
 int fdtd_selftest_bounded_wait(int64_t limit_ns, int arrive, void* stream);
+
+/* FP64 FMA throughput of the current device, measured: a kernel of 8
+ * blocks of 256 threads per SM, each thread running 8 independent chains of
+ * `iters` FMAs, timed with CUDA events after one shorter warm-up launch.
+ * *flops_per_s = 2 x FMAs / time.  The FP64 form of the line solve is bound
+ * by this rate rather than by HBM, so it is the denominator of that form's
+ * ALU roofline.  iters in [1, 1e6] (about 4.5 s on a GB300 at 1e6); synchronises stream (NULL = legacy
+ * default stream). */
+int fdtd_probe_fp64_fma(int64_t iters, double* flops_per_s, void* stream);
 
 /* Static description of an error code. */
 const char* fdtd_strerror(int code);

@@ -18,7 +18,7 @@ import numpy as np
 from . import _lib
 from ._lib import COMPS, PRECISIONS, SCHEMES, FdtdDesc, FdtdError, FdtdStats, check, lib
 
-__all__ = ["Simulation", "Batch", "FdtdError", "comp_shape", "build", "energy_noalloc"]
+__all__ = ["Simulation", "Batch", "FdtdError", "comp_shape", "build", "energy_noalloc", "probe_fp64_fma"]
 
 
 def comp_shape(comp: str, nx: int, ny: int, nz: int) -> tuple:
@@ -36,6 +36,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 def _torch():
     import torch
     return torch
+
+
+def probe_fp64_fma(iters: int = 20000) -> float:
+    """Measured FP64 FMA throughput of the current device in FLOP/s (an FMA
+    counts 2): the ALU roofline of the FP64 line solve."""
+    v = ctypes.c_double()
+    check(lib().fdtd_probe_fp64_fma(int(iters), ctypes.byref(v), None), "fdtd_probe_fp64_fma")
+    return v.value
 
 
 def energy_noalloc(fields: dict, nx, ny, nz, dx, dy, dz, eps_r=1.0, mu_r=1.0, out=None, stream=None):

@@ -33,7 +33,7 @@ EXPORTS = (
     "fdtd_strerror", "fdtd_set_timing", "fdtd_get_stats", "fdtd_reset_stats",
     "fdtd_energy_noalloc", "fdtd_batch_create", "fdtd_batch_step", "fdtd_batch_destroy",
     "fdtd_batch_launches", "fdtd_batch_get_config", "fdtd_batch_set_config", "fdtd_adj_create", "fdtd_adj_forward", "fdtd_adj_backward", "fdtd_adj_memory",
-    "fdtd_adj_destroy", "fdtd_selftest_bounded_wait", "fdtd_debug_fail_alloc",
+    "fdtd_adj_destroy", "fdtd_selftest_bounded_wait", "fdtd_debug_fail_alloc", "fdtd_probe_fp64_fma",
 )
 
 
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         "fdtd_adj_destroy": (i32, [vp]),
         "fdtd_selftest_bounded_wait": (i32, [i64, i32, vp]),
         "fdtd_debug_fail_alloc": (i32, [i64]),
+        "fdtd_probe_fp64_fma": (i32, [i64, dp, vp]),
         "fdtd_energy_noalloc": (i32, [i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, i32, ctypes.POINTER(vp),
                                       ctypes.POINTER(ctypes.c_double), vp]),

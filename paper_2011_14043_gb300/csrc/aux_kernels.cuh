@@ -150,4 +150,22 @@ __global__ void weighted_sumsq_kernel(const T* x, const double* wv, double w, lo
   }
 }
 
+// FP64 FMA throughput probe: every thread runs 8 independent chains of
+// `iters` FMAs x <- x a + b (|a| < 1, so the values stay bounded); the sum is
+// stored only under a condition the host makes false, which keeps the work
+// from being optimised away.
+__global__ void fp64_fma_probe_kernel(double* out, long long iters, double a, double b, double never) {
+  double x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = 1e-3 * (threadIdx.x + 1) + c;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sum += x[c];
+  if (sum == never) out[0] = sum;
+}
+
 }  // namespace fdtd

@@ -716,9 +716,12 @@ constexpr int tma_L() { return 16; }
 int tma_L_rt(const fdtd_t*) { return 16; }
 
 
+// FP32 fields only: in FP64 the direct-load kernel (16 lines x 16 nodes per
+// thread, more resident warps) measured 14 % faster per step at 256^3 than
+// the TMA-fed kernel, whose 8-line FP64 tiles keep 8 warps per SM.
 bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
   // the coefficient tables' carry products are built for the strided L
-  return h->use_tma && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 &&
+  return h->use_tma && h->prec == FDTD_F32 && !h->per_node && !g.rows && g.N >= 2 && g.N <= 256 &&
          h->strided_cfg[g.axis == AX_Y ? 0 : 1].L == tma_L_rt(h) && tensor_map_encoder() != nullptr;
 }
 
@@ -784,9 +787,11 @@ int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& 
   q.zbox = kind;
   q.tiles_x = (g.lane_hi + LANES - 1) / LANES;
   q.n_tiles = q.tiles_x * g.n_o;
-  // outputs staged in shared memory and written by TMA stores (6 % faster per
-  // launch at 256^3 than register stores); tune[1] bit 2: register stores
-  const bool st = (h->desc.tune[1] & 4) == 0;
+  // outputs written from registers: with the three pairs of a procedure on
+  // parallel branches the step is 1.8 % faster at 256^3 than with the
+  // outputs staged in shared memory and written by TMA stores, although one
+  // launch alone is 5 % slower; tune[1] bit 2: TMA stores
+  const bool st = (h->desc.tune[1] & 4) != 0;
   const size_t smem = tma_smem_bytes<T>(LANES, BN, P, NST) + (st ? 2 * (size_t)BN * LANES * sizeof(T) : 0);
   auto kern = st ? fdtd::proc_strided_tma_st_kernel<T, LANES, L, MINB, NST>
                  : fdtd::proc_strided_tma_kernel<T, LANES, L, MINB, NST>;
@@ -876,15 +881,14 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
       case 32: launch_rows_L<T, 32>(h, g, p, pn); break;
       default: return FDTD_ERR_UNSUPPORTED;
     }
-  } else if (tma_eligible(h, g) && p.e_in == p.e_out && p.e_in == (const T*)h->f[g.ec] &&
+  } else if (sizeof(T) == 4 && tma_eligible(h, g) && p.e_in == p.e_out && p.e_in == (const T*)h->f[g.ec] &&
              p.h_in == (const T*)h->f[g.hc]) {
-    int rc;
     // 16-line tiles, two blocks per SM, two-stage ring (measured at 256^3:
     // a three-stage ring 9 % slower, three blocks per SM 12 % slower, 32-line
     // tiles with one block per SM equal)
-    if constexpr (sizeof(T) == 8) rc = launch_strided_tma<T, 8, 2, 2>(h, g, p);
-    else rc = launch_strided_tma<T, 16, 2, 2>(h, g, p);
-    if (rc) return rc;
+    if constexpr (sizeof(T) == 4) {
+      if (int rc = launch_strided_tma<T, 16, 2, 2>(h, g, p)) return rc;
+    }
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];
     if (!cfg.ok) return FDTD_ERR_UNSUPPORTED;
@@ -1110,8 +1114,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
   std::vector<const void*> ptrs(h->f, h->f + 6);
   if (!h->g_exec || ptrs != h->g_bound) {
     graph_release(h);
-    if (h->prec == FDTD_F64) CK((ensure_tma_attr<double, 8, 2, 2>()));
-    else CK((ensure_tma_attr<float, 16, 2, 2>()));
+    if (h->prec == FDTD_F32) CK((ensure_tma_attr<float, 16, 2, 2>()));
     static const int seq_fss[3] = {0, 1, 0};
     static const int seq_two[2] = {0, 1};
     const int* seq = h->scheme == FDTD_FSS ? seq_fss : seq_two;
@@ -1517,6 +1520,42 @@ int fdtd_selftest_bounded_wait(int64_t limit_ns, int arrive, void* stream) {
     return FDTD_ERR_CUDA;
   }
   return v == 0 ? FDTD_OK : FDTD_ERR_TIMEOUT;
+}
+
+int fdtd_probe_fp64_fma(int64_t iters, double* flops_per_s, void* stream) {
+  if (iters < 1 || iters > 1000000LL || !flops_per_s) return FDTD_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* d_out = nullptr;
+  if (e == cudaSuccess && dev_malloc((void**)&d_out, sizeof(double)) != cudaSuccess) return FDTD_ERR_OOM;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  // 8 blocks of 256 threads per SM (64 warps), 8 independent chains each
+  const int blocks = 8 * sms, threads = 256;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    fdtd::fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(d_out, iters / 8 + 1, 0.999999, 1e-6, -1.0);  // warm-up
+    e = cudaEventRecord(e0, st);
+  }
+  if (e == cudaSuccess) {
+    fdtd::fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(d_out, iters, 0.999999, 1e-6, -1.0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess || ms <= 0.f) {
+    fprintf(stderr, "fdtd: CUDA error: %s\n", cudaGetErrorString(e));
+    return FDTD_ERR_CUDA;
+  }
+  *flops_per_s = 2.0 * 8.0 * (double)iters * (double)blocks * threads / (ms * 1e-3);
+  return FDTD_OK;
 }
 
 const char* fdtd_strerror(int code) {

@@ -78,3 +78,10 @@ def test_null_handle_and_pointers(L):
 @pytest.mark.parametrize("limit", [0, -5, 10_000_000_001])
 def test_bounded_wait_selftest_rejects_bad_limits(L, limit):
     assert L.fdtd_selftest_bounded_wait(limit, 0, None) == -1
+
+
+@pytest.mark.parametrize("iters", [0, -1, 1_000_001])
+def test_fp64_probe_rejects_bad_arguments(L, iters):
+    v = ctypes.c_double()
+    assert L.fdtd_probe_fp64_fma(iters, ctypes.byref(v), None) == -1
+    assert L.fdtd_probe_fp64_fma(10, None, None) == -1

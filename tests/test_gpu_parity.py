@@ -180,19 +180,19 @@ def test_device_buffers_path():
     check(out, ref, "f64")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f32"])
 @pytest.mark.parametrize("dims", [(70, 45, 33), (40, 256, 37), (37, 41, 256)])
 def test_tma_path_bit_identical_to_direct_path(prec, dims):
-    """The persistent TMA-fed y/z kernel (TMA stores by default, register
-    stores with tune[1] bit 2) and the direct-load kernel run the same
-    arithmetic in the same order: results must agree bit for bit."""
+    """The persistent TMA-fed y/z kernel of FP32 fields (register stores by
+    default, TMA stores with tune[1] bit 2) and the direct-load kernel run
+    the same arithmetic in the same order: results must agree bit for bit."""
     nx, ny, nz = dims
     g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
     dt = 7.0 * g.dt_cfl()
     u0 = random_fields(nx, ny, nz, seed=nx + ny + nz)
     a, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 3, tune=(16, 0))
     b, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 3, tune=(16, 1))
-    c2, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 3, tune=(16, 4))  # register stores
+    c2, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "fadi", prec, u0, 3, tune=(16, 4))  # TMA stores
     for c in G.COMPS:
         assert np.array_equal(a[c], b[c]), c
         assert np.array_equal(c2[c], b[c]), c
