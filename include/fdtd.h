@@ -58,6 +58,9 @@ extern "C" {
 #define FDTD_ERR_UNSTABLE (-5)      /* non-finite field or invariant growth */
 #define FDTD_ERR_UNSUPPORTED (-6)   /* valid request this build does not implement */
 #define FDTD_ERR_STATE (-7)         /* call not valid in the handle's state */
+#define FDTD_ERR_BOUNDS (-8)        /* bounds-checked build (-DFDTD_BOUNDS) only: a kernel
+                                       index fell outside its array; the access was
+                                       skipped and the results are not valid */
 
 typedef enum { FDTD_FADI = 0, FDTD_FLOD = 1, FDTD_FSS = 2, FDTD_FLOD2 = 3 } fdtd_scheme;
 typedef enum { FDTD_F64 = 0, FDTD_F32 = 1 } fdtd_precision;

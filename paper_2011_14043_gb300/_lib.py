@@ -19,6 +19,7 @@ ERRORS = {
     -5: "FDTD_ERR_UNSTABLE",
     -6: "FDTD_ERR_UNSUPPORTED",
     -7: "FDTD_ERR_STATE",
+    -8: "FDTD_ERR_BOUNDS",
 }
 
 SCHEMES = {"fadi": 0, "flod": 1, "fss": 2, "flod2": 3}
@@ -66,14 +67,17 @@ _lib = None
 
 
 def lib() -> ctypes.CDLL:
-    """The loaded library; raises if it has not been built."""
+    """The loaded library (FDTD_LIBRARY in the environment names another
+    build of it, e.g. the bounds-checked one); raises if it has not been
+    built."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+    path = os.environ.get("FDTD_LIBRARY") or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing "
                           "(run paper_2011_14043_gb300.build.build())")
-    L = ctypes.CDLL(LIB_PATH)
+    L = ctypes.CDLL(path)
     vp = ctypes.c_void_p
     i32 = ctypes.c_int
     i64 = ctypes.c_int64

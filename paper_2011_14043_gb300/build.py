@@ -14,6 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libfdtd.so")
+# the bounds-checked debug build (-DFDTD_BOUNDS): every kernel line, tile or
+# element range is checked against its array's extent (FDTD_ERR_BOUNDS)
+BOUNDS_LIB_PATH = os.path.join(BUILD_DIR, "libfdtd_bounds.so")
 SOURCES = [os.path.join(HERE, "csrc", "fdtd.cu"), os.path.join(HERE, "csrc", "energy_noalloc.cu")]
 DEPENDS = SOURCES + [
     os.path.join(HERE, "csrc", "line_kernels.cuh"),
@@ -33,21 +36,23 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found (set CUDA_HOME or NVCC)")
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(path: str = LIB_PATH) -> bool:
+    if not os.path.exists(path):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return all(os.path.getmtime(p) <= t for p in DEPENDS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build ``libfdtd.so`` if missing or stale; returns its path."""
-    if not force and up_to_date():
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Build ``libfdtd.so`` (or, with bounds, the bounds-checked
+    ``libfdtd_bounds.so``) if missing or stale; returns its path."""
+    path = BOUNDS_LIB_PATH if bounds else LIB_PATH
+    if not force and up_to_date(path):
+        return path
     os.makedirs(BUILD_DIR, exist_ok=True)
-    tmp = LIB_PATH + ".tmp"
+    tmp = path + ".tmp"
     cmd = [nvcc_path(), ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp] + SOURCES
+           "-shared", "-o", tmp] + (["-DFDTD_BOUNDS"] if bounds else []) + SOURCES
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd))
@@ -56,8 +61,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
     if verbose:
         print(res.stdout + res.stderr)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 if __name__ == "__main__":

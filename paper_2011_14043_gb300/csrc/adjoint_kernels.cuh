@@ -54,8 +54,8 @@ __global__ void adj_strided_kernel(const PairParams<T> p, const AdjExtra<T> x) {
   const int P = blockDim.x / LANES;
   const int i = blockIdx.x * LANES + lane;
   const int o = p.o_lo + blockIdx.y;
-  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
   const long long base = (long long)o * p.os + i;
+  const bool active = (i >= p.lane_lo) && (i < p.lane_hi) && strided_line_ok(p, base);
   const int j0 = s * L;
   const int N = p.N;
   const long long ls = p.ls;
@@ -134,6 +134,7 @@ __global__ void adj_rows_kernel(const PairParams<T> p, const AdjExtra<T> x) {
   const HiLo<T> pb = phase_backward<T, L, 2>(p, j0, yin, ibn, ibl, ib_prev, y);
   const T win = warp_chain_backward<T>(y[0], pb);
   phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
+  if (!row_ok<T, L>(p, base)) return;
   if (j0 + L <= N) {
     // whole segment: record, gradient and outputs as 16-byte vectors
     T dd[L];
@@ -246,6 +247,7 @@ __global__ void init_grad_kernel(const PairParams<T> p, int rows, const T* lam, 
       base = (long long)o * p.os + i;
     }
     const long long at = base + (long long)j * p.ls;
+    if (!FDTD_IN_RANGE(at - p.ls, at + 1, p.n_elem)) continue;
     const double er = eps_r[at];
     const double dh = (double)p.h_in[at] - (double)p.h_in[at - p.ls];
     grad[at] += coef * (double)lam[at] * dh / (er * er);
@@ -263,6 +265,10 @@ __global__ void cell_grad_kernel(const double* gx, const double* gy, const doubl
     const int i = (int)(c % nx);
     const int j = (int)((c / nx) % ny);
     const int k = (int)(c / ((long long)nx * ny));
+    // the samples read below lie between these two offsets
+    if (!FDTD_IN_RANGE((long long)k * plane + (long long)j * pitch + i,
+                       (long long)(k + 1) * plane + (long long)(j + 1) * pitch + i + 2, plane * (nz + 1)))
+      continue;
     double acc = 0.0;
     // 1 / (in-domain cells along an axis next to node n): cells n-1 and n,
     // so the share of one sample is the product of two factors 1 or 1/2

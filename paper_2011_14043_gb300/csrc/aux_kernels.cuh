@@ -34,6 +34,7 @@ __global__ void explicit_pair_kernel(const PairParams<T> p, int rows) {
       base = (long long)o * p.os + i;
     }
     const long long at = base + (long long)j * p.ls;
+    if (!FDTD_IN_RANGE(at - (j >= 1 ? p.ls : 0), at + (j + 1 < p.N ? p.ls : 0) + 1, p.n_elem)) continue;
     const T hf = p.h_in[at];
     if (j >= 1) {
       const T kb = PER_NODE ? p.ks / p.nq[at] : p.kb;   // s b_j / d_eta (h > 0)
@@ -83,7 +84,9 @@ __global__ void unpack_kernel(const T* __restrict__ src, T* __restrict__ dst, in
     const long long r = e / sx;
     const int j = (int)(r % sy);
     const int k = (int)(r / sy);
-    dst[(long long)k * plane + (long long)j * pitch + i] = src[e];
+    const long long at = (long long)k * plane + (long long)j * pitch + i;
+    if (!FDTD_IN_RANGE(at, at + 1, (long long)sz * plane)) continue;
+    dst[at] = src[e];
   }
 }
 
@@ -96,7 +99,9 @@ __global__ void pack_kernel(const T* __restrict__ src, T* __restrict__ dst, int 
     const long long r = e / sx;
     const int j = (int)(r % sy);
     const int k = (int)(r / sy);
-    dst[e] = src[(long long)k * plane + (long long)j * pitch + i];
+    const long long at = (long long)k * plane + (long long)j * pitch + i;
+    if (!FDTD_IN_RANGE(at, at + 1, (long long)sz * plane)) continue;
+    dst[e] = src[at];
   }
 }
 

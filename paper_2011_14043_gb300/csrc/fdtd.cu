@@ -13,6 +13,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <array>
@@ -155,6 +156,15 @@ struct fdtd_s {
 namespace {
 
 int single_tune(fdtd_t* h);
+
+// NVTX range over a scope: host-side annotations for profilers (ncu's
+// --nvtx filters); without a tool attached the calls return at once.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 // Every device allocation of the library goes through dev_malloc.  A test
 // hook (fdtd_debug_fail_alloc) can make the n-th next one fail as an
@@ -602,7 +612,7 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.noffh = (const T*)c.noffh;
   p.noffl = (const T*)c.noffl;
   p.kd_scale = (T)(sgn * kd_mul);
-  (void)h;
+  p.n_elem = h->count;
   return p;
 }
 
@@ -913,6 +923,7 @@ template <typename T>
 int run_procedure(fdtd_t* h, int slot, double sgn, double alpha, double beta, double kd_mul,
                   void* const* in, void* const* out) {
   const ProcCoef& P = h->proc[slot];
+  NvtxScope range(P.op == 0 ? "procedure A" : "procedure B");
   for (int q = 0; q < 3; ++q) {
     const PairGeom& g = h->geom[P.op][q];
     fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], sgn, alpha, beta, kd_mul, in, out);
@@ -1151,6 +1162,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
     };
     cudaStream_t home = h->stream;
     const long long before = h->launches;
+    NvtxScope range("step graph capture");
     CK(cudaStreamBeginCapture(h->g_run, cudaStreamCaptureModeThreadLocal));
     int rc = FDTD_OK;
     for (int k = 0; k < nproc && rc == FDTD_OK; ++k) {
@@ -1201,7 +1213,10 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
     fdtd::step_counter_kernel<<<1, 32, 0, h->g_run>>>(h->d_step, h->steps, 0);
     CK(cudaGetLastError());
   }
-  for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(h->g_exec, h->g_run));
+  {
+    NvtxScope range("step graph replays");
+    for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(h->g_exec, h->g_run));
+  }
   CK(cudaEventRecord(h->g_out, h->g_run));
   CK(cudaStreamWaitEvent(h->stream, h->g_out, 0));
   h->launches += nsteps * h->g_kernels;
@@ -1321,6 +1336,11 @@ int check_device_flag(fdtd_t* h) {
   int v = 0;
   CK(cudaMemcpyAsync(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+#ifdef FDTD_BOUNDS
+  int b = 0;
+  CK(cudaMemcpyFromSymbol(&b, fdtd::g_bounds_err, sizeof(int)));
+  if (b) return FDTD_ERR_BOUNDS;
+#endif
   return v ? FDTD_ERR_TIMEOUT : FDTD_OK;
 }
 
@@ -1448,7 +1468,8 @@ __global__ void zero_walls_kernel(T* e, int comp, int nx, int ny, int nz, long l
     if (comp == 0) wall = (j == 0 || j == ny || k == 0 || k == nz);
     else if (comp == 1) wall = (i == 0 || i == nx || k == 0 || k == nz);
     else wall = (i == 0 || i == nx || j == 0 || j == ny);
-    if (wall) e[k * plane + j * pitch + i] = T(0);
+    const long long at = k * plane + j * pitch + i;
+    if (wall && FDTD_IN_RANGE(at, at + 1, plane * (nz + 1))) e[at] = T(0);
   }
 }
 
@@ -1568,6 +1589,7 @@ const char* fdtd_strerror(int code) {
     case FDTD_ERR_UNSTABLE: return "non-finite field or invariant";
     case FDTD_ERR_UNSUPPORTED: return "unsupported in this build";
     case FDTD_ERR_STATE: return "call not valid in the handle's state";
+    case FDTD_ERR_BOUNDS: return "a kernel index fell outside its array (bounds-checked build)";
     default: return "unknown error";
   }
 }
@@ -1857,6 +1879,7 @@ int fdtd_add_probe(fdtd_t* h, int comp, int i, int j, int k, int* id) {
 
 int fdtd_step(fdtd_t* h, int64_t nsteps) {
   if (!h || nsteps < 0) return FDTD_ERR_INVALID_ARG;
+  NvtxScope range("fdtd_step");
   if (h->poisoned) return FDTD_ERR_STATE;
   if (nsteps == 0) return FDTD_OK;
   int rc = scheme_init(h);
@@ -1888,6 +1911,7 @@ int fdtd_get_probe(fdtd_t* h, int id, double* out, int64_t n) {
 }
 
 int fdtd_energy(fdtd_t* h, double out[2]) {
+  NvtxScope range("fdtd_energy");
   if (!h || !out) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
   if (int rc0 = check_device_flag(h)) return rc0;
@@ -2604,6 +2628,7 @@ int fdtd_batch_destroy(fdtd_batch_t* b) {
 
 int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps) {
   if (!b || nsteps < 0) return FDTD_ERR_INVALID_ARG;
+  NvtxScope range("fdtd_batch_step");
   for (fdtd_t* h : b->h) {
     if (h->poisoned) return FDTD_ERR_STATE;
     if (h->src_comp >= 0 || h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
@@ -3190,6 +3215,7 @@ int fdtd_adj_forward(fdtd_adj_t* a, double* objective) {
   fdtd_t* h = a->h;
   if (h->poisoned) return FDTD_ERR_STATE;
   if (a->forward_done || !h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
+  NvtxScope range("adjoint forward");
   int rc = h->prec == FDTD_F64 ? adj_forward_t<double>(a) : adj_forward_t<float>(a);
   if (rc) return rc;
   a->forward_done = true;
@@ -3202,6 +3228,7 @@ int fdtd_adj_backward(fdtd_adj_t* a, double jbar, double* grad_eps_r, int on_dev
   fdtd_t* h = a->h;
   if (h->poisoned) return FDTD_ERR_STATE;
   if (!a->forward_done) return FDTD_ERR_STATE;
+  NvtxScope range("adjoint backward");
   int rc = h->prec == FDTD_F64 ? adj_backward_t<double>(a, jbar) : adj_backward_t<float>(a, jbar);
   if (rc) return rc;
   const size_t n = sizeof(double) * (size_t)h->nx * h->ny * h->nz;

@@ -46,6 +46,26 @@
 
 namespace fdtd {
 
+// Bounds-checked debug build (-DFDTD_BOUNDS): every line, tile or element a
+// kernel is about to touch is checked against its array's extent; a range
+// outside it is recorded in g_bounds_err (read by the host's device-flag
+// check, FDTD_ERR_BOUNDS) and the accesses are skipped.  Each check covers a
+// whole line: its accesses are base + j ls for j in a known range, so the
+// first and the last one bound the rest.  Without the macro the checks are
+// the constant true.  TMA copies need none: the tensor map bounds them.
+#ifdef FDTD_BOUNDS
+__device__ int g_bounds_err = 0;
+// [lo, hi) inside [0, n)?
+__device__ __forceinline__ bool in_range(long long lo, long long hi, long long n) {
+  if (lo >= 0 && lo <= hi && hi <= n) return true;
+  atomicExch(&g_bounds_err, 1);
+  return false;
+}
+#define FDTD_IN_RANGE(lo, hi, n) ::fdtd::in_range((lo), (hi), (n))
+#else
+#define FDTD_IN_RANGE(lo, hi, n) true
+#endif
+
 template <typename T>
 struct PairParams {
   const T* e_in;
@@ -87,7 +107,20 @@ struct PairParams {
   const T* noffh;
   const T* noffl;
   T kd_scale;
+  long long n_elem;      // elements of every field-layout array (bounds-checked builds)
 };
+
+// Bounds of one line for the checked build: a strided line touches its
+// nodes 0 .. N-1 at base + j ls; an x line (row) is read and written as 32 L
+// consecutive elements from base.
+template <typename T>
+__device__ __forceinline__ bool strided_line_ok(const PairParams<T>& p, long long base) {
+  return FDTD_IN_RANGE(base, base + (long long)(p.N - 1) * p.ls + 1, p.n_elem);
+}
+template <typename T, int L>
+__device__ __forceinline__ bool row_ok(const PairParams<T>& p, long long base) {
+  return FDTD_IN_RANGE(base, base + 32LL * L, p.n_elem);
+}
 
 // ---------------------------------------------------------------------------
 // Segment arithmetic shared by all kernels
@@ -405,8 +438,8 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
   const int P = blockDim.x / LANES;
   const int i = blockIdx.x * LANES + lane;
   const int o = p.o_lo + blockIdx.y;
-  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
   const long long base = (long long)o * p.os + i;
+  const bool active = (i >= p.lane_lo) && (i < p.lane_hi) && strided_line_ok(p, base);
   const int j0 = s * L;
   const int N = p.N;
   const long long ls = p.ls;
@@ -607,8 +640,8 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     const int x0 = (tile % q.tiles_x) * LANES;
     const int o = p.o_lo + tile / q.tiles_x;
     const int i = x0 + lane;
-    const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
     const long long base = (long long)o * p.os + i;
+    const bool active = (i >= p.lane_lo) && (i < p.lane_hi) && strided_line_ok(p, base);
 
     const T* sE = buf + (2 * stage + 0) * stage_elems;
     const T* sH = buf + (2 * stage + 1) * stage_elems;
@@ -898,6 +931,7 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
   const int jo = p.o_lo + (int)(line % p.n_o);
   const int ko = p.o2_lo + (int)(line / p.n_o);
   const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const bool ok = row_ok<T, L>(p, base);
   const int j0 = lane * L;
   const int N = p.N;
   T y[L];
@@ -927,7 +961,7 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
       D[t] = E[t] - e_new;
       E[t] = e_new;
     }
-    if (p.d_out) {
+    if (p.d_out && ok) {
       if (j0 + L <= N) {
         store_seg<T, L>(p.d_out + base + j0, D);
       } else {
@@ -958,6 +992,7 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
   }
   // values beyond N are exactly zero, so whole segments inside the padded
   // row are stored as vectors; the segment holding the line end element-wise
+  if (!ok) return;
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
     store_seg<T, L>(p.h_out + base + j0, H);
@@ -990,7 +1025,7 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
     ibn[t] = T(0);
     ibl[t] = T(0);
   }
-  if (j0 < p.N) {  // lanes wholly past the line end touch no memory
+  if (j0 < p.N && row_ok<T, L>(p, base)) {  // lanes wholly past the line end touch no memory
     load_seg<T, L>(p.e_in + base + j0, E);
     load_seg<T, L>(p.h_in + base + j0, H);
     if constexpr (PER_NODE) {
@@ -1068,8 +1103,8 @@ __global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ para
   const int s = tid / LANES;
   const int i = tile.x0 + lane;
   const int o = tile.o;
-  const bool active = have && (i >= p.lane_lo) && (i < p.lane_hi);
   const long long base = (long long)o * p.os + i;
+  const bool active = have && (i >= p.lane_lo) && (i < p.lane_hi) && strided_line_ok(p, base);
   const int j0 = s * L;
   const int N = p.N;
   const long long ls = p.ls;
@@ -1195,8 +1230,8 @@ __global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ para
   const long long total = line_start[ngrids];
   if (gwarp * LPW >= total) return;  // whole warp leaves together
   const long long gline = gwarp * LPW + lane / LPL;
-  const bool valid = gline < total;
-  const long long gl = valid ? gline : total - 1;
+  const bool in_batch = gline < total;
+  const long long gl = in_batch ? gline : total - 1;
   int lo = 0, hi = ngrids;  // line_start[lo] <= gl < line_start[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -1210,6 +1245,7 @@ __global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ para
   const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
   const int j0 = sl * L;
   const int N = p.N;
+  const bool valid = in_batch && FDTD_IN_RANGE(base, base + N, p.n_elem);
   const bool full = j0 + L <= N;
 
   T E[L], H[L], qn[L], ibn[L], ibl[L], y[L];
@@ -1357,8 +1393,8 @@ __global__ void proc_strided_gm_kernel(const PairParams<T> p) {
   const int P = blockDim.x / LANES;
   const int i = blockIdx.x * LANES + lane;
   const int o = p.o_lo + blockIdx.y;
-  const bool active = (i >= p.lane_lo) && (i < p.lane_hi);
   const long long base = (long long)o * p.os + i;
+  const bool active = (i >= p.lane_lo) && (i < p.lane_hi) && strided_line_ok(p, base);
   const int j0 = s * L;
   const int N = p.N;
   const long long ls = p.ls;
@@ -1429,6 +1465,7 @@ __global__ void proc_rows_gm_kernel(const PairParams<T> p) {
   const int jo = p.o_lo + (int)(line % p.n_o);
   const int ko = p.o2_lo + (int)(line / p.n_o);
   const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const bool ok = row_ok<T, L>(p, base);
   const int j0 = lane * L;
   const int N = p.N;
   T E[L], H[L], y[L], qn[L], ibn[L], ibl[L], offh[L], offl[L], kd[L];
@@ -1436,7 +1473,7 @@ __global__ void proc_rows_gm_kernel(const PairParams<T> p) {
   for (int t = 0; t < L; ++t) {
     E[t] = H[t] = qn[t] = ibn[t] = ibl[t] = offh[t] = offl[t] = kd[t] = T(0);
   }
-  if (j0 < N) {
+  if (j0 < N && ok) {
     load_seg<T, L>(p.e_in + base + j0, E);
     load_seg<T, L>(p.h_in + base + j0, H);
     load_seg<T, L>(p.nq + base + j0, qn);
@@ -1471,6 +1508,7 @@ __global__ void proc_rows_gm_kernel(const PairParams<T> p) {
     H[t] = fma(p.kd_scale * kd[t], wnext - y[t], H[t]);
     E[t] = fma(p.alpha, y[t], p.beta * E[t]);
   }
+  if (!ok) return;
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
     store_seg<T, L>(p.h_out + base + j0, H);
