@@ -233,8 +233,9 @@ __global__ void init_grad_kernel(const PairParams<T> p, int rows, const T* lam, 
   const long long total = n_lines * (p.N - 1);
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int j = 1 + (int)(g % (p.N - 1));
-    const long long line = g / (p.N - 1);
+    // consecutive threads take consecutive x (as in explicit_pair_kernel)
+    const int j = 1 + (rows ? (int)(g % (p.N - 1)) : (int)(g / n_lines));
+    const long long line = rows ? g / (p.N - 1) : g % n_lines;
     long long base;
     if (rows) {
       const int jo = p.o_lo + (int)(line % p.n_o);

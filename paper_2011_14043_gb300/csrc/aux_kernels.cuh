@@ -20,8 +20,10 @@ __global__ void explicit_pair_kernel(const PairParams<T> p, int rows) {
   const long long total = n_lines * p.N;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(g % p.N);
-    const long long line = g / p.N;
+    // consecutive threads take consecutive x: nodes of an x line, or the
+    // same node of neighbouring y/z lines
+    const int j = rows ? (int)(g % p.N) : (int)(g / n_lines);
+    const long long line = rows ? g / p.N : g % n_lines;
     long long base;
     if (rows) {
       const int jo = p.o_lo + (int)(line % p.n_o);
