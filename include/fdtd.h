@@ -76,8 +76,9 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * tune[1] bit 1 set: per-node (inhomogeneous-media) coefficients even when
  * fdtd_set_material receives a uniform eps (needed by fdtd_adj_create);
  * tune[1] bit 2 set: the TMA-fed kernel stages its outputs in shared memory
- * and writes them with TMA stores instead of register stores; tune[1] bit 3 set: fdtd_step launches the
- * kernels one by one instead of replaying a captured step graph. */
+ * and writes them with TMA stores instead of register stores; tune[1] bit 3
+ * set: fdtd_step launches the kernels one by one instead of replaying a
+ * captured step graph. */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of
