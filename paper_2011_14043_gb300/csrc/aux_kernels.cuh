@@ -76,34 +76,55 @@ __global__ void step_counter_kernel(long long* step, long long value, int mode) 
 }
 
 // Compact [sz][sy][sx] <-> padded (plane, pitch) layout of one component,
-// for host copies staged through a contiguous device buffer.
+// for host copies staged through a contiguous device buffer: one row (fixed
+// j, k) per block iteration, threads along x (no per-element division).
 template <typename T>
 __global__ void unpack_kernel(const T* __restrict__ src, T* __restrict__ dst, int sx, int sy, int sz,
                               long long pitch, long long plane) {
-  const long long n = (long long)sx * sy * sz;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % sx);
-    const long long r = e / sx;
-    const int j = (int)(r % sy);
-    const int k = (int)(r / sy);
-    const long long at = (long long)k * plane + (long long)j * pitch + i;
-    if (!FDTD_IN_RANGE(at, at + 1, (long long)sz * plane)) continue;
-    dst[at] = src[e];
+  const long long rows = (long long)sy * sz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long long at = (r / sy) * plane + (r % sy) * pitch;
+    if (!FDTD_IN_RANGE(at, at + sx, (long long)sz * plane)) continue;
+    for (int i = threadIdx.x; i < sx; i += blockDim.x) dst[at + i] = src[r * sx + i];
   }
 }
 
 template <typename T>
 __global__ void pack_kernel(const T* __restrict__ src, T* __restrict__ dst, int sx, int sy, int sz, long long pitch,
                             long long plane) {
-  const long long n = (long long)sx * sy * sz;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % sx);
-    const long long r = e / sx;
+  const long long rows = (long long)sy * sz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long long at = (r / sy) * plane + (r % sy) * pitch;
+    if (!FDTD_IN_RANGE(at, at + sx, (long long)sz * plane)) continue;
+    for (int i = threadIdx.x; i < sx; i += blockDim.x) dst[r * sx + i] = src[at + i];
+  }
+}
+
+// Zero the tangential E of component comp (0..2: Ex, Ey, Ez) on the PEC
+// walls: whole rows on the y or z walls, the two end samples i = 0 and
+// i = nx of the other rows for Ey and Ez (walls normal to x).
+template <typename T>
+__global__ void zero_walls_kernel(T* e, int comp, int nx, int ny, int nz, long long pitch, long long plane) {
+  int sx, sy, sz;
+  if (comp == 0) { sx = nx; sy = ny + 1; sz = nz + 1; }
+  else if (comp == 1) { sx = nx + 1; sy = ny; sz = nz + 1; }
+  else { sx = nx + 1; sy = ny + 1; sz = nz; }
+  const long long rows = (long long)sy * sz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int j = (int)(r % sy);
     const int k = (int)(r / sy);
-    const long long at = (long long)k * plane + (long long)j * pitch + i;
-    if (!FDTD_IN_RANGE(at, at + 1, (long long)sz * plane)) continue;
-    dst[e] = src[at];
+    const long long at = (long long)k * plane + (long long)j * pitch;
+    if (!FDTD_IN_RANGE(at, at + sx, plane * (nz + 1))) continue;
+    bool whole;
+    if (comp == 0) whole = (j == 0 || j == ny || k == 0 || k == nz);
+    else if (comp == 1) whole = (k == 0 || k == nz);
+    else whole = (j == 0 || j == ny);
+    if (whole) {
+      for (int i = threadIdx.x; i < sx; i += blockDim.x) e[at + i] = T(0);
+    } else if (comp != 0 && threadIdx.x == 0) {
+      e[at] = T(0);
+      e[at + nx] = T(0);
+    }
   }
 }
 

@@ -1383,8 +1383,7 @@ int ensure_stage(fdtd_t* h) {
 }
 
 int stage_unpack(fdtd_t* h, int sx, int sy, int sz, void* dst_padded) {
-  const long long n = (long long)sx * sy * sz;
-  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((long long)sy * sz, 152LL * 16));
   if (h->prec == FDTD_F64)
     fdtd::unpack_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)h->stage, (double*)dst_padded, sx, sy,
                                                                sz, h->pitch, h->plane);
@@ -1396,8 +1395,7 @@ int stage_unpack(fdtd_t* h, int sx, int sy, int sz, void* dst_padded) {
 }
 
 int stage_pack(fdtd_t* h, int sx, int sy, int sz, const void* src_padded) {
-  const long long n = (long long)sx * sy * sz;
-  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+  const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((long long)sy * sz, 152LL * 16));
   if (h->prec == FDTD_F64)
     fdtd::pack_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)src_padded, (double*)h->stage, sx, sy, sz,
                                                              h->pitch, h->plane);
@@ -1452,34 +1450,16 @@ int copy_in_component(fdtd_t* h, int comp, const void* src, void* dst_padded, in
   return FDTD_OK;
 }
 
-template <typename T>
-__global__ void zero_walls_kernel(T* e, int comp, int nx, int ny, int nz, long long pitch, long long plane) {
-  int sx, sy, sz;
-  if (comp == 0) { sx = nx; sy = ny + 1; sz = nz + 1; }
-  else if (comp == 1) { sx = nx + 1; sy = ny; sz = nz + 1; }
-  else { sx = nx + 1; sy = ny + 1; sz = nz; }
-  const long long total = (long long)sx * sy * sz;
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(g % sx);
-    const int j = (int)((g / sx) % sy);
-    const int k = (int)(g / ((long long)sx * sy));
-    bool wall;
-    if (comp == 0) wall = (j == 0 || j == ny || k == 0 || k == nz);
-    else if (comp == 1) wall = (i == 0 || i == nx || k == 0 || k == nz);
-    else wall = (i == 0 || i == nx || j == 0 || j == ny);
-    const long long at = k * plane + j * pitch + i;
-    if (wall && FDTD_IN_RANGE(at, at + 1, plane * (nz + 1))) e[at] = T(0);
-  }
-}
 
 int zero_walls(fdtd_t* h, int comp, void* arr) {
   if (comp >= 3) return FDTD_OK;
   h->launches++;
   if (h->prec == FDTD_F64)
-    zero_walls_kernel<double><<<256, 256, 0, h->stream>>>((double*)arr, comp, h->nx, h->ny, h->nz, h->pitch, h->plane);
+    fdtd::zero_walls_kernel<double><<<1216, 256, 0, h->stream>>>((double*)arr, comp, h->nx, h->ny, h->nz, h->pitch,
+                                                                 h->plane);
   else
-    zero_walls_kernel<float><<<256, 256, 0, h->stream>>>((float*)arr, comp, h->nx, h->ny, h->nz, h->pitch, h->plane);
+    fdtd::zero_walls_kernel<float><<<1216, 256, 0, h->stream>>>((float*)arr, comp, h->nx, h->ny, h->nz, h->pitch,
+                                                                h->plane);
   CK(cudaGetLastError());
   return FDTD_OK;
 }
