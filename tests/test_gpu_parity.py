@@ -96,7 +96,8 @@ def test_degenerate_tiny_grids(dims, scheme):
     check(out, ref, "f64")
 
 
-@pytest.mark.parametrize("dims", [(300, 3, 3), (3, 300, 3), (3, 3, 300), (1000, 2, 2)])
+@pytest.mark.parametrize("dims", [(300, 3, 3), (3, 300, 3), (3, 3, 300), (1000, 2, 2),
+                                  (1024, 3, 3), (3, 1024, 3), (3, 3, 1024)])
 def test_long_lines(dims):
     """Long lines along each axis (many segments; x rows up to 32 nodes/lane)."""
     nx, ny, nz = dims
@@ -332,3 +333,34 @@ def test_general_media_is_rejected_where_not_built():
     big = Simulation(300, 4, 4, 1e-3, scheme="flod", precision="f32", cfl=3.0)
     with pytest.raises(FdtdError):
         big.set_material(None, np.ones((4, 4, 300)) + np.arange(300) * 1e-3)
+
+
+@pytest.mark.parametrize("dims", [(3, 1024, 3), (3, 3, 1024), (1024, 3, 3)])
+def test_longest_lines_in_inhomogeneous_media(dims):
+    """Per-node media at the longest supported lines (32 segments of 32 nodes
+    along y or z, 32 nodes per lane along x), with a source, vs the oracle."""
+    nx, ny, nz = dims
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 6.0 * g.dt_cfl()
+    eps = np.random.default_rng(sum(dims)).uniform(1.0, 5.0, (nz, ny, nx))
+    u0 = random_fields(nx, ny, nz, seed=sum(dims) + 1)
+    P = oracle_problem(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, eps=eps)
+    ref, _, _ = S.run_fundamental(P, "flod", u0, 3)
+    for prec in ("f64", "f32"):
+        out, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, "flod", prec, u0, 3, eps=eps)
+        check(out, ref, prec)
+
+
+@pytest.mark.parametrize("dims,code", [((1025, 4, 4), -1), ((4, 1025, 4), -6), ((4, 4, 1025), -6)])
+def test_lines_past_the_limit_are_rejected(dims, code):
+    """Lines longer than 1024 cells are refused at creation, as the header
+    states: nx > 1024 is an invalid argument, ny or nz > 1024 (more than 32
+    segments of 32 nodes) FDTD_ERR_UNSUPPORTED; the library stays usable."""
+    from paper_2011_14043_gb300 import FdtdError, Simulation
+    with pytest.raises(FdtdError) as e:
+        Simulation(*dims, 1e-3, scheme="fadi", precision="f32", cfl=2.0)
+    assert e.value.code == code
+    sim = Simulation(8, 8, 8, 1e-3, scheme="fadi", precision="f32", cfl=2.0)
+    sim.step(2)
+    sim.synchronize()
+    sim.close()
