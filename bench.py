@@ -175,7 +175,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_gpu(args, prec, fields, time_kernels=True):
+def run_gpu(args, prec, fields, time_kernels=True, keep_fields=False):
     """Device-resident timing of K steps on the library's default path (each
     step a replay of a captured graph whose three pair launches per procedure
     run on parallel branches), CUDA events on the handle's stream around the
@@ -209,8 +209,39 @@ def run_gpu(args, prec, fields, time_kernels=True):
         st = sim.stats()
         sim.set_timing(False)
     energy = sim.energy()
+    out = None
+    if keep_fields:
+        out = {c: sim.get_field(c, device=True).clone() for c in fields}
+    total_steps = sim.steps_done
     sim.close()
-    return {"ms": ms, "launches": launches, "stats": st, "energy": energy}
+    return {"ms": ms, "launches": launches, "stats": st, "energy": energy, "fields": out,
+            "total_steps": total_steps}
+
+
+def device_rel_err(a: dict, b: dict) -> float:
+    """Relative L2 of fields a against fields b (device tensors) in the vacuum
+    energy norm: E weighted by eps0, H by mu0."""
+    mu0 = 1.25663706212e-6
+    eps0 = 1.0 / (mu0 * 299792458.0 ** 2)
+    num = den = 0.0
+    for c in a:
+        w = eps0 if c.startswith("e") else mu0
+        d = a[c].double() - b[c].double()
+        num += w * float((d * d).sum())
+        den += w * float((b[c].double() ** 2).sum())
+    return math.sqrt(num / den)
+
+
+def fp64_reference_fields(args, fields, steps):
+    """The FP64 GPU path after `steps` steps of the same workload."""
+    from paper_2011_14043_gb300 import Simulation
+    n = args.n
+    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision="f64", cfl=args.cfl, tune=tuple(args.tune))
+    sim.set_fields(fields)
+    sim.step(steps)
+    out = {c: sim.get_field(c, device=True).clone() for c in fields}
+    sim.close()
+    return out
 
 
 def run_e2e(args, prec, fields):
@@ -527,7 +558,7 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.4)
-    r32 = run_gpu(args, "f32", fields)
+    r32 = run_gpu(args, "f32", fields, keep_fields=(rank == 0 and not args.no_fp64))
     clocks = sampler.stop()
     ms, value = replica_throughput(r32["ms"], cells * args.steps, ws, "cuda")
 
@@ -571,6 +602,13 @@ def main():
         a.steps = max(3, min(args.steps, 20))
         r64 = run_gpu(a, "f64", fields, time_kernels=False)
         v64 = cells * a.steps / (r64["ms"] / 1e3)
+        ref = fp64_reference_fields(args, fields, r32["total_steps"])
+        line["accuracy"] = {"fp32_vs_fp64_rel_l2": device_rel_err(r32["fields"], ref),
+                            "steps": r32["total_steps"],
+                            "norm": "relative L2 in the vacuum energy norm, FP32 GPU path against the FP64 GPU "
+                                    "path after the same steps from the same initial field"}
+        del ref
+        r32["fields"] = None
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / a.steps, "steps": a.steps,
                         "hbm_frac": 192.0 * cells * a.steps / (r64["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
                         "roofline": fp64_alu_roofline(v64)}
