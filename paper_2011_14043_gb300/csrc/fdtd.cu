@@ -268,6 +268,18 @@ int pick_rows_L(int N) {
   return -1;
 }
 
+// Nodes per lane (L) and lanes per line of a handle's x lines.  FP64 fields
+// on uniform media with 32 < N <= 256 take 16 nodes on 4, 8 or 16 lanes
+// (proc_rows_lpl_kernel: fewer shuffles and FP64 scan operations than one
+// warp per line); every other case one warp per line with the smallest L
+// that covers the line.  The uniform-media coefficient tables are built for
+// this L.
+int rows_lanes(const fdtd_t* h, int N) {
+  if (h->prec != FDTD_F64 || h->per_node || N <= 32 || N > 256) return 32;
+  return N <= 64 ? 4 : (N <= 128 ? 8 : 16);
+}
+int rows_L(const fdtd_t* h, int N) { return rows_lanes(h, N) < 32 ? 16 : pick_rows_L(N); }
+
 // segments per line for a block of LANES-wide segments: ceil(N / L) rounded
 // up so that the block is a whole number of warps (extra segments lie past
 // the line end and hold zeros)
@@ -387,7 +399,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       const double off = -bd / 2.0;
       const double diag = 0.5 + bd;
       const int N = std::max(g.N, 1);
-      const int L = g.rows ? std::max(1, pick_rows_L(N)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
+      const int L = g.rows ? std::max(1, rows_L(h, N)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
       c.L = L;
       // covers every segment a kernel may form: P*L <= N + 4L - 1 with L <= 32
       c.tlen = ((std::max(N + 160, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
@@ -639,6 +651,17 @@ void launch_rows_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>
     fdtd::proc_rows_kernel<T, L, false><<<blocks, wpb * 32, 0, h->stream>>>(p);
 }
 
+// x lines of FP64 uniform media: 16 nodes per lane, lanes lanes per line.
+template <typename T>
+void launch_rows_lpl(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, int lanes) {
+  const int wpb = 8;
+  const long long warps = (g.n_lines() * lanes + 31) / 32;
+  const unsigned blocks = (unsigned)((warps + wpb - 1) / wpb);
+  if (lanes == 4) fdtd::proc_rows_lpl_kernel<T, 16, 4><<<blocks, wpb * 32, 0, h->stream>>>(p);
+  else if (lanes == 8) fdtd::proc_rows_lpl_kernel<T, 16, 8><<<blocks, wpb * 32, 0, h->stream>>>(p);
+  else fdtd::proc_rows_lpl_kernel<T, 16, 16><<<blocks, wpb * 32, 0, h->stream>>>(p);
+}
+
 // (LANES, L) of the y/z line kernels.  A block holds every segment of LANES
 // lines, so P * LANES threads with P = ceil(N / L); the choice must fit the
 // register file (checked against the compiled kernel's attributes).
@@ -879,7 +902,9 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
     CK(cudaEventRecord(h->ev_pool[ev0], h->stream));
   }
   h->launches++;
-  if (g.rows) {
+  if (sizeof(T) == 8 && g.rows && rows_lanes(h, g.N) < 32) {
+    if constexpr (sizeof(T) == 8) launch_rows_lpl<T>(h, g, p, rows_lanes(h, g.N));
+  } else if (g.rows) {
     switch (pick_rows_L(g.N)) {
       case 1: launch_rows_L<T, 1>(h, g, p, pn); break;
       case 2: launch_rows_L<T, 2>(h, g, p, pn); break;
@@ -2078,7 +2103,7 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
         if (only_kind >= 0 && kind != only_kind) continue;
         int L, lanes = 0, Pseg = 0;
         if (g.rows) {
-          L = pick_rows_L(g.N);
+          L = rows_L(h, g.N);  // the L of the grid's coefficient tables
           // per-node media take any L: short lines share a warp (8 or 16
           // lanes per line) so that every lane streams 8 nodes
           if (h->per_node && g.N <= 256 && cfg.xpack) {

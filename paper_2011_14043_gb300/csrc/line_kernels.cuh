@@ -111,15 +111,15 @@ struct PairParams {
 };
 
 // Bounds of one line for the checked build: a strided line touches its
-// nodes 0 .. N-1 at base + j ls; an x line (row) is read and written as 32 L
-// consecutive elements from base.
+// nodes 0 .. N-1 at base + j ls; an x line (row) is read and written in
+// whole segments of L elements from base, the last one holding node N-1.
 template <typename T>
 __device__ __forceinline__ bool strided_line_ok(const PairParams<T>& p, long long base) {
   return FDTD_IN_RANGE(base, base + (long long)(p.N - 1) * p.ls + 1, p.n_elem);
 }
 template <typename T, int L>
 __device__ __forceinline__ bool row_ok(const PairParams<T>& p, long long base) {
-  return FDTD_IN_RANGE(base, base + 32LL * L, p.n_elem);
+  return FDTD_IN_RANGE(base, base + (long long)((p.N + L - 1) / L) * L, p.n_elem);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +375,10 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
     tid = (int)threadIdx.x;
     nthr = (int)blockDim.x;
   }
-  const bool conv = (j0 >= p.jc) && (j0 + L <= p.N);
+  // FP64 fields always read the tables: the converged constants equal the
+  // table entries, and a warp whose segments took both branches would issue
+  // the FP64 arithmetic of both on the FP64 pipe that bounds the solve
+  const bool conv = use_hilo<T>() && (j0 >= p.jc) && (j0 + L <= p.N);
   HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
     pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
@@ -972,8 +975,9 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     }
   } else {
     // homogeneous media: lanes in the converged interior use the limit
-    // constants, lanes near the walls read the tables
-    const bool conv = (j0 >= p.jc) && (j0 + L <= N);
+    // constants, lanes near the walls read the tables (FP64 fields: every
+    // lane reads the tables, as in strided_solve)
+    const bool conv = use_hilo<T>() && (j0 >= p.jc) && (j0 + L <= N);
     HiLo<T> pf, pb;
     if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
     else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
@@ -1211,6 +1215,81 @@ __device__ __forceinline__ T group_chain_backward(T b, HiLo<T> pm, int sl) {
   }
   const T win = __shfl_down_sync(FULL, b, 1, LPL);
   return sl == LPL - 1 ? T(0) : win;
+}
+
+// x lines of uniform media, LPL lanes per line (32 / LPL lines per warp) and
+// L nodes per lane, for FP64 fields, whose FP64 pipe bounds the solve.  Every
+// lane reads its coefficients from the tables (MODE 0): a warp spans whole
+// lines, so lanes at the walls and lanes in the converged interior would
+// otherwise take different branches, and the warp would issue the FP64
+// arithmetic of both.  The carry chains take log2(LPL) shuffle steps.  The
+// coefficient tables are built for this L.
+template <typename T, int L, int LPL>
+__global__ void proc_rows_lpl_kernel(const PairParams<T> p) {
+  constexpr int LPW = 32 / LPL;  // lines per warp
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % LPL;
+  const long long n = (long long)p.n_o * p.n_o2;
+  const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gwarp * LPW >= n) return;  // whole warp leaves together
+  const long long gline = gwarp * LPW + lane / LPL;
+  const bool in_grid = gline < n;
+  const long long line = in_grid ? gline : n - 1;
+  const int jo = p.o_lo + (int)(line % p.n_o);
+  const int ko = p.o2_lo + (int)(line / p.n_o);
+  const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const bool ok = in_grid && row_ok<T, L>(p, base);
+  const int j0 = sl * L;
+  const int N = p.N;
+
+  T E[L], H[L], qn[L], ibn[L], ibl[L], y[L];
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    E[t] = T(0);
+    H[t] = T(0);
+    qn[t] = T(0);
+    ibn[t] = T(0);
+    ibl[t] = T(0);
+  }
+  if (ok && j0 < N) {
+    load_seg<T, L>(p.e_in + base + j0, E);
+    load_seg<T, L>(p.h_in + base + j0, H);
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t >= N) {
+        E[t] = T(0);
+        H[t] = T(0);
+      }
+    }
+  }
+  T hm1 = __shfl_up_sync(FULL, H[L - 1], 1, LPL);
+  if (sl == 0) hm1 = T(0);
+  const HiLo<T> ib_prev = {T(0), T(0)};
+  const HiLo<T> pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
+  const T yin = group_chain_forward<T, LPL>(y[L - 1], pf, sl);
+  const HiLo<T> pb = phase_backward<T, L, 0>(p, j0, yin, ibn, ibl, ib_prev, y);
+  const T win = group_chain_backward<T, LPL>(y[0], pb, sl);
+  phase_fix<T, L, 0>(p, j0, win, ibn, ibl, y);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T wnext = (t + 1 < L) ? y[t + 1] : win;
+    H[t] = fma(p.kd, wnext - y[t], H[t]);
+    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
+  if (!ok) return;
+  if (j0 + L <= N) {
+    store_seg<T, L>(p.e_out + base + j0, E);
+    store_seg<T, L>(p.h_out + base + j0, H);
+  } else if (j0 < N) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t < N) {
+        p.e_out[base + j0 + t] = E[t];
+        p.h_out[base + j0 + t] = H[t];
+      }
+    }
+  }
 }
 
 // x lines of per-node grids in a batch, LPL lanes per line and L nodes per
