@@ -268,17 +268,25 @@ int pick_rows_L(int N) {
   return -1;
 }
 
-// Nodes per lane (L) and lanes per line of a handle's x lines.  FP64 fields
-// on uniform media with 32 < N <= 256 take 16 nodes on 4, 8 or 16 lanes
-// (proc_rows_lpl_kernel: fewer shuffles and FP64 scan operations than one
-// warp per line); every other case one warp per line with the smallest L
-// that covers the line.  The uniform-media coefficient tables are built for
-// this L.
-int rows_lanes(const fdtd_t* h, int N) {
-  if (h->prec != FDTD_F64 || h->per_node || N <= 32 || N > 256) return 32;
-  return N <= 64 ? 4 : (N <= 128 ? 8 : 16);
+// FP64 fields on uniform media, pairs of at least this many lines: the solve
+// is bound by the FP64 pipe, so every lane reads the coefficient tables
+// (PairParams::tables_only) and x lines of 32 < N <= 256 take 16 nodes on 4,
+// 8 or 16 lanes (proc_rows_lpl_kernel).  Smaller pairs are bound by latency,
+// where the converged constants (no loads) and short per-lane chains win.
+constexpr long long kFp64ThroughputLines = 4096;
+
+bool fp64_throughput_pair(const fdtd_t* h, const PairGeom& g) {
+  return h->prec == FDTD_F64 && !h->per_node && g.n_lines() >= kFp64ThroughputLines;
 }
-int rows_L(const fdtd_t* h, int N) { return rows_lanes(h, N) < 32 ? 16 : pick_rows_L(N); }
+
+// Nodes per lane (L) and lanes per line of a pair's x lines: the shape above,
+// else one warp per line with the smallest L that covers the line.  The
+// uniform-media coefficient tables are built for this L.
+int rows_lanes(const fdtd_t* h, const PairGeom& g) {
+  if (!fp64_throughput_pair(h, g) || g.N <= 32 || g.N > 256) return 32;
+  return g.N <= 64 ? 4 : (g.N <= 128 ? 8 : 16);
+}
+int rows_L(const fdtd_t* h, const PairGeom& g) { return rows_lanes(h, g) < 32 ? 16 : pick_rows_L(g.N); }
 
 // segments per line for a block of LANES-wide segments: ceil(N / L) rounded
 // up so that the block is a whole number of warps (extra segments lie past
@@ -399,7 +407,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       const double off = -bd / 2.0;
       const double diag = 0.5 + bd;
       const int N = std::max(g.N, 1);
-      const int L = g.rows ? std::max(1, rows_L(h, N)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
+      const int L = g.rows ? std::max(1, rows_L(h, g)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
       c.L = L;
       // covers every segment a kernel may form: P*L <= N + 4L - 1 with L <= 32
       c.tlen = ((std::max(N + 160, 32 * std::max(1, pick_rows_L(N))) + 31) / 32) * 32;
@@ -625,6 +633,7 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.noffl = (const T*)c.noffl;
   p.kd_scale = (T)(sgn * kd_mul);
   p.n_elem = h->count;
+  p.tables_only = fp64_throughput_pair(h, g) ? 1 : 0;
   return p;
 }
 
@@ -902,8 +911,8 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
     CK(cudaEventRecord(h->ev_pool[ev0], h->stream));
   }
   h->launches++;
-  if (sizeof(T) == 8 && g.rows && rows_lanes(h, g.N) < 32) {
-    if constexpr (sizeof(T) == 8) launch_rows_lpl<T>(h, g, p, rows_lanes(h, g.N));
+  if (sizeof(T) == 8 && g.rows && rows_lanes(h, g) < 32) {
+    if constexpr (sizeof(T) == 8) launch_rows_lpl<T>(h, g, p, rows_lanes(h, g));
   } else if (g.rows) {
     switch (pick_rows_L(g.N)) {
       case 1: launch_rows_L<T, 1>(h, g, p, pn); break;
@@ -2103,7 +2112,7 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
         if (only_kind >= 0 && kind != only_kind) continue;
         int L, lanes = 0, Pseg = 0;
         if (g.rows) {
-          L = rows_L(h, g.N);  // the L of the grid's coefficient tables
+          L = rows_L(h, g);  // the L of the grid's coefficient tables
           // per-node media take any L: short lines share a warp (8 or 16
           // lanes per line) so that every lane streams 8 nodes
           if (h->per_node && g.N <= 256 && cfg.xpack) {

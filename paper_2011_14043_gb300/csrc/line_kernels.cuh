@@ -108,6 +108,8 @@ struct PairParams {
   const T* noffl;
   T kd_scale;
   long long n_elem;      // elements of every field-layout array (bounds-checked builds)
+  int tables_only;       // uniform media: every lane reads the tables (no converged-
+                         // constant branch); set for FP64 fields on large pairs
 };
 
 // Bounds of one line for the checked build: a strided line touches its
@@ -375,10 +377,11 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
     tid = (int)threadIdx.x;
     nthr = (int)blockDim.x;
   }
-  // FP64 fields always read the tables: the converged constants equal the
-  // table entries, and a warp whose segments took both branches would issue
-  // the FP64 arithmetic of both on the FP64 pipe that bounds the solve
-  const bool conv = use_hilo<T>() && (j0 >= p.jc) && (j0 + L <= p.N);
+  // p.tables_only (FP64 fields on large pairs): every lane reads the tables.
+  // The converged constants equal the table entries, and a warp whose
+  // segments took both branches would issue the FP64 arithmetic of both on
+  // the FP64 pipe that bounds the solve
+  const bool conv = !p.tables_only && (j0 >= p.jc) && (j0 + L <= p.N);
   HiLo<T> pf, pb;
   if constexpr (PER_NODE) {
     pf = phase_forward<T, L, 2>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
@@ -975,9 +978,9 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     }
   } else {
     // homogeneous media: lanes in the converged interior use the limit
-    // constants, lanes near the walls read the tables (FP64 fields: every
-    // lane reads the tables, as in strided_solve)
-    const bool conv = use_hilo<T>() && (j0 >= p.jc) && (j0 + L <= N);
+    // constants, lanes near the walls read the tables (with p.tables_only
+    // every lane reads the tables, as in strided_solve)
+    const bool conv = !p.tables_only && (j0 >= p.jc) && (j0 + L <= N);
     HiLo<T> pf, pb;
     if (conv) pf = phase_forward<T, L, 1>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
     else pf = phase_forward<T, L, 0>(p, j0, E, H, hm1, qn, ibn, ibl, ib_prev, y);
