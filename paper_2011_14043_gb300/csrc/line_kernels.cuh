@@ -38,8 +38,6 @@
 //   proc_rows_kernel         lines along x (contiguous): one warp per line,
 //                            lane l owns nodes/faces [l L, l L + L) loaded as
 //                            16-byte vectors; carries go through shuffles.
-//   proc_rows_lpl_kernel     x lines of FP64 fields on large pairs: 16 nodes
-//                            per lane on 4, 8 or 16 lanes per line.
 #pragma once
 
 #include <cuda.h>
