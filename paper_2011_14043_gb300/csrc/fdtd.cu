@@ -468,7 +468,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       int rc = upload_any(h, &c.tab, tab);
       if (rc) return rc;
     } else {
-      // Per-node media: rows scaled by 1/b_j (symmetric form),
+      // Per-node media: rows scaled by 1/b_j (a symmetric matrix),
       //   q_j w_j / 2 - (|ks| |kd| / 2) (w_{j+1} - 2 w_j + w_{j-1}) = q_j E_j + ks (H_j - H_{j-1}),
       // q_j = 1/|b_j|, ks = s sign(h) / d_eta.  Every line is factored in FP64
       // from exactly the q_j, ks, kd the kernel uses (rounded to the field
