@@ -139,7 +139,12 @@ int fdtd_set_state(fdtd_t* h, int comp, const void* data, int on_device);
  * is the current I [A] used by step n, i.e. I(t_n + dt/2); steps beyond
  * count use 0.  It enters as f_E = -I/(A eps) with A the sample's dual-face
  * area; each procedure of length h adds (h/2) f to the original-form
- * right-hand side (the paper omits sources; this is the reading used).
+ * right-hand side (the paper omits sources; this is the reading used), with
+ * f of the step's own sample, except in FDTD_FLOD2: its B procedure, centred
+ * on t_{n+1}, takes the mean of current[n] and current[n+1], and its input
+ * and output processing (Eqs. 22, 23) the sample of the step that follows
+ * them.  With these placements each scheme converges to the semi-discrete
+ * Yee system with its current at the temporal order of Table I.
  * One source per handle; a new call replaces it; count == 0 removes it. */
 int fdtd_set_source(fdtd_t* h, int comp, int i, int j, int k, const double* current, int64_t count);
 

@@ -14,9 +14,18 @@ Sources (the paper omits them, Sec. II): a current I(t) on one E sample
 contributes f_E = -I(t) / (A * eps) with A the sample's dual-face area.  Each
 procedure of length h adds (h/2) f(t_n + dt/2) to its original-form right-hand
 side; the weights of one step sum to dt.  In fundamental form this becomes
-+(h/4) f in the implicit right-hand side (FLOD, FSS, FLOD2) or, for FADI,
++(h/4) f in the implicit right-hand side (FLOD, FSS) or, for FADI,
 +(dt/2) f added to the auxiliary state after each procedure (it is part of
-the auxiliary variable v of Eqs. 2 and 8).
+the auxiliary variable v of Eqs. 2 and 8).  Every sample of the current is
+taken at a half-integer time t_n + dt/2.  LOD2 is the one exception to the
+mid-step sampling: its input and output processing (Eqs. 19-20) make it a
+similarity transform of Strang splitting with B on the outside, so the B
+sub-step of its main loop is centred on t_{n+1} and takes the mean of the
+samples at t_n + dt/2 and t_n + 3dt/2; its input and output processing,
+each a quarter step that runs once, take the sample of the step that
+follows them.  With these placements every scheme converges, as dt -> 0 at
+a fixed time, to the semi-discrete Yee system with its current at the order
+Table I gives (first for LOD1, second for ADI, SS2 and LOD2).
 """
 from __future__ import annotations
 
@@ -103,14 +112,35 @@ def orig_ss2_step(P: Problem, u: dict, n: int) -> dict:
     return _cn_substep(P, u2, "A", "A", P.dt / 4, f)
 
 
-def orig_lod2_input(P: Problem, u0: dict) -> dict:
-    """LOD2 input processing, Eq. 19: (I - dt/4 B) u^{1/4} = (I + dt/4 B) u^0."""
-    return _cn_substep(P, u0, "B", "B", P.dt / 4, None)
+def orig_lod2_input(P: Problem, u0: dict, n0: int = 0) -> dict:
+    """LOD2 input processing, Eq. 19: (I - dt/4 B) u^{n0+1/4} = (I + dt/4 B) u^{n0}
+    (+ (dt/4) f(t_{n0} + dt/2))."""
+    return _cn_substep(P, u0, "B", "B", P.dt / 4, P.f((n0 + 0.5) * P.dt))
 
 
-def orig_lod2_output(P: Problem, u: dict) -> dict:
-    """LOD2 output processing, Eq. 20: (I + dt/4 B) u^{n+1} = (I - dt/4 B) u^{n+5/4}."""
-    return _cn_substep(P, u, "B", "B", -P.dt / 4, None)
+def orig_lod2_step(P: Problem, u: dict, n: int) -> dict:
+    """LOD2 main loop, Eq. 18 (the LOD1 step of Eq. 11): the A sub-step takes
+    f(t_n + dt/2), the B sub-step (centred on t_{n+1}) the mean of f(t_n + dt/2)
+    and f(t_n + 3dt/2)."""
+    tau = P.dt / 2
+    fa = P.f((n + 0.5) * P.dt)
+    fb = _mean_f(P, n)
+    uh = _cn_substep(P, u, "A", "A", tau, fa)
+    return _cn_substep(P, uh, "B", "B", tau, fb)
+
+
+def orig_lod2_output(P: Problem, u: dict, n_next: int = 0) -> dict:
+    """LOD2 output processing, Eq. 20: (I + dt/4 B) u^{n+1} = (I - dt/4 B) u^{n+5/4}
+    (- (dt/4) f(t_{n+1} + dt/2)); ``n_next`` = n + 1."""
+    return _cn_substep(P, u, "B", "B", -P.dt / 4, P.f((n_next + 0.5) * P.dt))
+
+
+def _mean_f(P: Problem, n: int):
+    """(f(t_n + dt/2) + f(t_n + 3dt/2)) / 2, or None without a source."""
+    fa = P.f((n + 0.5) * P.dt)
+    if fa is None:
+        return None
+    return scale(add(fa, P.f((n + 1.5) * P.dt)), 0.5)
 
 
 def run_original(P: Problem, scheme: str, u0: dict, steps: int) -> dict:
@@ -127,8 +157,8 @@ def run_original(P: Problem, scheme: str, u0: dict, steps: int) -> dict:
     elif scheme == "lod2":
         u = orig_lod2_input(P, u)
         for n in range(steps):
-            u = orig_lod1_step(P, u, n)
-        u = orig_lod2_output(P, u)
+            u = orig_lod2_step(P, u, n)
+        u = orig_lod2_output(P, u, steps)
     else:
         raise ValueError(scheme)
     return u
@@ -255,15 +285,29 @@ def fss_step(P: Problem, u: dict, n: int) -> dict:
     return u3
 
 
-def flod2_input(P: Problem, u0: dict) -> dict:
-    """Eq. 22: (1/2 I - dt/8 B) v = u^0, u^{1/4} = v - u^0 (procedure length dt/2)."""
-    return procedure(P, u0, "B", P.dt / 2)[0]
+def flod2_input(P: Problem, u0: dict, n0: int = 0) -> dict:
+    """Eq. 22: (1/2 I - dt/8 B) v = u^{n0} (+ (dt/8) f(t_{n0} + dt/2)),
+    u^{n0+1/4} = v - u^{n0} (procedure length dt/2)."""
+    f = P.f((n0 + 0.5) * P.dt)
+    return procedure(P, u0, "B", P.dt / 2, rhs_src=None if f is None else scale(f, P.dt / 8))[0]
 
 
-def flod2_output(P: Problem, u: dict) -> dict:
-    """Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4}, u^{n+1} = v - u^{n+5/4}
-    (a procedure of length -dt/2)."""
-    return procedure(P, u, "B", -P.dt / 2)[0]
+def flod2_step(P: Problem, u: dict, n: int) -> dict:
+    """Eq. 21: the FLOD procedures with +(dt/4) f in each implicit right-hand
+    side, f(t_n + dt/2) for A and the mean of f(t_n + dt/2), f(t_n + 3dt/2)
+    for B (the sub-step centred on t_{n+1})."""
+    fa = P.f((n + 0.5) * P.dt)
+    fb = _mean_f(P, n)
+    uh, _, _ = procedure(P, u, "A", P.dt, rhs_src=None if fa is None else scale(fa, P.dt / 4))
+    u1, _, _ = procedure(P, uh, "B", P.dt, rhs_src=None if fb is None else scale(fb, P.dt / 4))
+    return u1
+
+
+def flod2_output(P: Problem, u: dict, n_next: int = 0) -> dict:
+    """Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4} (- (dt/8) f(t_{n+1} + dt/2)),
+    u^{n+1} = v - u^{n+5/4} (a procedure of length -dt/2); n_next = n + 1."""
+    f = P.f((n_next + 0.5) * P.dt)
+    return procedure(P, u, "B", -P.dt / 2, rhs_src=None if f is None else scale(f, -P.dt / 8))[0]
 
 
 def run_fundamental(P: Problem, scheme: str, u0: dict, steps: int, probes=()):
@@ -275,16 +319,18 @@ def run_fundamental(P: Problem, scheme: str, u0: dict, steps: int, probes=()):
     if scheme == "flod2":
         u = flod2_input(P, u)
     for n in range(steps):
-        if scheme in ("flod", "flod2"):
+        if scheme == "flod":
             u = flod_step(P, u, n)
+        elif scheme == "flod2":
+            u = flod2_step(P, u, n)
         elif scheme == "fss":
             u = fss_step(P, u, n)
         else:
             raise ValueError(scheme)
-        out = flod2_output(P, u) if (scheme == "flod2" and probes) else u
+        out = flod2_output(P, u, n + 1) if (scheme == "flod2" and probes) else u
         for p, (c, i, j, k) in enumerate(probes):
             series[p][n] = out[c][k, j, i]
-    field_out = flod2_output(P, u) if scheme == "flod2" else u
+    field_out = flod2_output(P, u, steps) if scheme == "flod2" else u
     return field_out, u, series
 
 

@@ -1007,6 +1007,21 @@ int procedure_ex(fdtd_t* h, int slot, double sgn, double alpha, double beta, dou
                              : run_procedure<float>(h, slot, sgn, alpha, beta, kd_mul, in, out);
 }
 
+// The forward procedure with a right-hand-side source made of two terms
+// (c fa + c fb), each added as its own rounded value before the solve and
+// again to the new E: the FLOD2 B procedure, whose source is the mean of the
+// samples on either side of t_{n+1}.  The graph path adds the same terms in
+// the same order.
+int procedure_two_terms(fdtd_t* h, int slot, double ta, double tb) {
+  int rc;
+  if ((rc = add_point(h, h->f[h->src_comp < 0 ? 0 : h->src_comp], ta))) return rc;
+  if ((rc = add_point(h, h->f[h->src_comp < 0 ? 0 : h->src_comp], tb))) return rc;
+  rc = procedure_ex(h, slot, 1.0, 1.0, -1.0, 1.0, h->f, h->f);
+  if (rc) return rc;
+  if ((rc = add_point(h, h->f[h->src_comp < 0 ? 0 : h->src_comp], ta))) return rc;
+  return add_point(h, h->f[h->src_comp < 0 ? 0 : h->src_comp], tb);
+}
+
 int ensure_scratch(fdtd_t* h) {
   for (int c = 0; c < 6; ++c) {
     if (!h->scratch[c]) {
@@ -1071,8 +1086,9 @@ int scheme_init(fdtd_t* h) {
   if (h->scheme == FDTD_FADI) {
     rc = h->prec == FDTD_F64 ? fadi_init_t<double>(h) : fadi_init_t<float>(h);
   } else if (h->scheme == FDTD_FLOD2) {
-    // Eq. 22: (1/2 I - dt/8 B) v = u^0, u^{1/4} = v - u^0  (procedure of length dt/2)
-    rc = procedure(h, 2, 0.0, 0.0);
+    // Eq. 22: (1/2 I - dt/8 B) v = u^n + (dt/8) f(t_n + dt/2), u^{n+1/4} = v - u^n
+    // (procedure of length dt/2; n = the steps taken so far)
+    rc = procedure(h, 2, 0.125 * h->dt * source_value(h, h->steps), 0.0);
   }
   if (rc) return rc;
   h->pending_init = false;
@@ -1129,7 +1145,7 @@ int ensure_probe_capacity(fdtd_t* h, long long need) {
 //   FLOD  P_A(dt), P_B(dt) with +(dt/4) f in each implicit RHS (Eq. 15);
 //   FSS   P_A(dt/2), P_B(dt), P_A(dt/2) with +(h/4) f (Eq. 17);
 //   FLOD2 FLOD main iterations (Eq. 21).
-int physical_to_scratch(fdtd_t* h);
+int physical_to_scratch(fdtd_t* h, long long n_next = -1);
 
 // Drop the captured step.  Replays still in flight on the (non-blocking)
 // replay stream finish first: callers go on to rewrite or free buffers the
@@ -1168,6 +1184,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
     // each procedure (0 = none), and the step offset of the value after it
     const double dt = h->dt;
     double pre[3] = {0, 0, 0}, post[3] = {0, 0, 0};
+    double pre2[3] = {0, 0, 0}, post2[3] = {0, 0, 0};   // second terms, step offset 1
     int post_off[3] = {0, 0, 0};
     if (h->scheme == FDTD_FADI) {
       post[0] = 0.5 * dt;
@@ -1177,6 +1194,12 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
       pre[0] = post[0] = 0.125 * dt;
       pre[1] = post[1] = 0.25 * dt;
       pre[2] = post[2] = 0.125 * dt;
+    } else if (h->scheme == FDTD_FLOD2) {
+      // B: (dt/4) of the mean of f(t_n + dt/2) and f(t_n + 3dt/2), as two
+      // terms (dt/8) f of offsets 0 and 1 (procedure_two_terms)
+      pre[0] = post[0] = 0.25 * dt;
+      pre[1] = post[1] = 0.125 * dt;
+      pre2[1] = post2[1] = 0.125 * dt;
     } else {
       pre[0] = post[0] = 0.25 * dt;
       pre[1] = post[1] = 0.25 * dt;
@@ -1201,6 +1224,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
     int rc = FDTD_OK;
     for (int k = 0; k < nproc && rc == FDTD_OK; ++k) {
       if (add_src(pre[k], 0) != cudaSuccess) rc = FDTD_ERR_CUDA;
+      if (rc == FDTD_OK && add_src(pre2[k], 1) != cudaSuccess) rc = FDTD_ERR_CUDA;
       if (rc == FDTD_OK && cudaEventRecord(h->g_fork, h->g_run) != cudaSuccess) rc = FDTD_ERR_CUDA;
       const ProcCoef& P = h->proc[seq[k]];
       for (int q = 0; q < 3 && rc == FDTD_OK; ++q) {
@@ -1220,6 +1244,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
           rc = FDTD_ERR_CUDA;
       }
       if (rc == FDTD_OK && add_src(post[k], post_off[k]) != cudaSuccess) rc = FDTD_ERR_CUDA;
+      if (rc == FDTD_OK && add_src(post2[k], 1) != cudaSuccess) rc = FDTD_ERR_CUDA;
     }
     if (rc == FDTD_OK && src) {
       fdtd::step_counter_kernel<<<1, 32, 0, h->g_run>>>(h->d_step, 0, 1);
@@ -1310,7 +1335,14 @@ int one_step(fdtd_t* h) {
     case FDTD_FLOD:
     case FDTD_FLOD2: {
       if ((rc = procedure(h, 0, 0.25 * dt * f, 0.0))) return rc;
-      if ((rc = procedure(h, 1, 0.25 * dt * f, 0.0))) return rc;
+      if (h->scheme == FDTD_FLOD) {
+        if ((rc = procedure(h, 1, 0.25 * dt * f, 0.0))) return rc;
+      } else {
+        // FLOD2's B procedure is centred on t_{n+1}: (dt/4) of the mean of
+        // the samples at t_n + dt/2 and t_n + 3dt/2
+        const double fn = source_value(h, n + 1);
+        if ((rc = procedure_two_terms(h, 1, 0.125 * dt * f, 0.125 * dt * fn))) return rc;
+      }
       if (h->nprobes) {
         if (h->scheme == FDTD_FLOD) {
           if ((rc = probes(h, 2))) return rc;
@@ -1318,7 +1350,7 @@ int one_step(fdtd_t* h) {
           // probes of the FLOD2 physical field: output processing (Eq. 23)
           // of the new state into scratch, sampled there
           h->output_valid = false;
-          if ((rc = physical_to_scratch(h))) return rc;
+          if ((rc = physical_to_scratch(h, n + 1))) return rc;
           if ((rc = probes(h, 2, 0.0, h->scratch))) return rc;
         }
       }
@@ -1339,8 +1371,10 @@ int one_step(fdtd_t* h) {
 }
 
 // Physical field into scratch (FADI: (I + dt/2 B)^{-1}(v - pending source),
-// from Eqs. 2a, 8a, 9; FLOD2: output processing Eq. 23).
-int physical_to_scratch(fdtd_t* h) {
+// from Eqs. 2a, 8a, 9; FLOD2: output processing Eq. 23).  n_next: index of
+// the step that would come next (-1: the steps taken so far).
+int physical_to_scratch(fdtd_t* h, long long n_next) {
+  if (n_next < 0) n_next = h->steps;
   if (h->output_valid) return FDTD_OK;
   int rc = copy_state_to_scratch(h);
   if (rc) return rc;
@@ -1349,14 +1383,20 @@ int physical_to_scratch(fdtd_t* h) {
       // u = (I + dt/2 B)^{-1} (v - (dt/2) f_pending), from Eqs. 2a, 8a and 9:
       // the B pairs' line systems with the couplings of a procedure of length
       // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
-      const double fp = source_value(h, h->steps);
+      const double fp = source_value(h, n_next);
       if ((rc = add_point(h, h->scratch[h->src_comp < 0 ? 0 : h->src_comp], -0.5 * h->dt * fp))) return rc;
       rc = procedure_ex(h, 1, -1.0, 0.5, 0.0, 0.5, h->scratch, h->scratch);
       if (rc) return rc;
     } else if (h->scheme == FDTD_FLOD2) {
-      // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4}, u^{n+1} = v - u^{n+5/4}
+      // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4} - (dt/8) f(t_{n+1} + dt/2),
+      // u^{n+1} = v - u^{n+5/4}; the source term is added before the solve
+      // and once more to the new E (which subtracts the E the solve saw)
+      const double r = -0.125 * h->dt * source_value(h, n_next);
+      void* at = h->scratch[h->src_comp < 0 ? 0 : h->src_comp];
+      if ((rc = add_point(h, at, r))) return rc;
       rc = procedure_ex(h, 2, -1.0, 1.0, -1.0, 1.0, h->scratch, h->scratch);
       if (rc) return rc;
+      if ((rc = add_point(h, at, r))) return rc;
     }
   }
   h->output_valid = true;

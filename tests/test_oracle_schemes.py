@@ -99,8 +99,6 @@ def test_split_operators_sum_to_curl():
 @pytest.mark.parametrize("source", [False, True])
 @pytest.mark.parametrize("orig,fund", [("adi", "fadi"), ("lod1", "flod"), ("ss2", "fss"), ("lod2", "flod2")])
 def test_fundamental_equals_original(orig, fund, source):
-    if source and orig == "lod2":
-        pytest.skip("LOD2 input/output processing is defined without sources")
     P, u0 = make_problem(21, nx=6, ny=5, nz=7, cfl=6.0, source=source)
     uo = S.run_original(P, orig, u0, 12)
     uf, _, _ = S.run_fundamental(P, fund, u0, 12)
