@@ -165,7 +165,14 @@ int fdtd_get_probe(fdtd_t* h, int id, double* out, int64_t n);
 /* FP64 reductions: out[0] = field energy 1/2 dV sum(eps E^2 + mu H^2) of the
  * physical field; out[1] = the same quadratic form of the scheme state (the
  * exactly conserved invariant of a source-free run: equal to out[0] for
- * FLOD/FSS).  Returns FDTD_ERR_UNSTABLE if either is not finite. */
+ * FLOD/FSS).  Returns FDTD_ERR_UNSTABLE (out still filled) if either is not
+ * finite, or if a run with no source has let out[1] grow past its reference
+ * by more than 1e-8 (FDTD_F64) or 1e-2 (FDTD_F32) relative (measured
+ * roundoff drift is about 1e-13 / 1e-5 per thousand steps).  The reference
+ * is the invariant of the state the run started from: taken at the first
+ * fdtd_step or fdtd_energy after fdtd_set_field, fdtd_set_source or
+ * fdtd_set_material; fdtd_set_state keeps it (restoring a checkpoint of the
+ * same run). */
 int fdtd_energy(fdtd_t* h, double out[2]);
 
 /* Number of steps taken. */
@@ -213,7 +220,11 @@ int fdtd_reset_stats(fdtd_t* h);
  * Limit: nz <= 4096 (nz + 1 planes per component); larger nz returns
  * FDTD_ERR_INVALID_ARG with a message on stderr.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current), so make that first call before any stream capture.
+ * that device current) and caches it for the process, so make that first
+ * call before any stream capture, and do not use this entry point after
+ * cudaDeviceReset (the cached address may then be stale).  A CUDA error
+ * already pending when the call starts is reported as FDTD_ERR_CUDA and
+ * left pending; nothing is launched then.
  * All calls share the array: calls whose kernels overlap on the GPU (other
  * streams or threads) race on it. */
 int fdtd_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, double eps_r, double mu_r,

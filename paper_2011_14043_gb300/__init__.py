@@ -49,26 +49,40 @@ def probe_fp64_fma(iters: int = 20000) -> float:
 def energy_noalloc(fields: dict, nx, ny, nz, dx, dy, dz, eps_r=1.0, mu_r=1.0, out=None, stream=None):
     """Field energy of six CUDA tensors (compact Yee shapes) through
     ``fdtd_energy_noalloc``, which allocates no device memory: for callers
-    that cannot allocate where they need the number.  ``out`` is a one-element
-    float64 CUDA tensor (allocated here if omitted, by the caller's side);
-    the result is written there asynchronously on ``stream``."""
+    that cannot allocate where they need the number.  ``out`` is a contiguous
+    float64 CUDA tensor of at least one element on the fields' device
+    (allocated here if omitted, by the caller's side); the result is written
+    to its first element asynchronously on ``stream`` (default: the current
+    stream of the fields' device).  Every argument is checked before anything
+    is launched: tensors on different devices, or an ``out`` of another dtype
+    or on the host, raise ValueError."""
     torch = _torch()
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or not out.is_cuda \
+                or not out.is_contiguous() or out.numel() < 1:
+            raise ValueError("out: need a contiguous float64 CUDA tensor with at least one element")
     ts = [fields[c] for c in COMPS]
+    if not all(isinstance(t, torch.Tensor) for t in ts):
+        raise ValueError("fields must be torch tensors")
     if len({t.dtype for t in ts}) != 1 or ts[0].dtype not in (torch.float32, torch.float64):
         raise ValueError("fields must share one dtype, float32 or float64")
     for c, t in zip(COMPS, ts):
         if not (t.is_cuda and t.is_contiguous()) or tuple(t.shape) != comp_shape(c, nx, ny, nz):
             raise ValueError(f"{c}: need a contiguous CUDA tensor of shape {comp_shape(c, nx, ny, nz)}")
+    dev = ts[0].device
+    if any(t.device != dev for t in ts) or (out is not None and out.device != dev):
+        raise ValueError("the six fields and out must be on one CUDA device")
     prec = PRECISIONS["f64" if ts[0].dtype == torch.float64 else "f32"]
-    if out is None:
-        out = torch.empty(1, dtype=torch.float64, device=ts[0].device)
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    ptrs = (ctypes.c_void_p * 6)(*[t.data_ptr() for t in ts])
-    check(lib().fdtd_energy_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz), float(eps_r),
-                                    float(mu_r), prec, ptrs, ctypes.cast(ctypes.c_void_p(out.data_ptr()),
-                                                                         ctypes.POINTER(ctypes.c_double)),
-                                    ctypes.c_void_p(int(stream))), "fdtd_energy_noalloc")
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        ptrs = (ctypes.c_void_p * 6)(*[t.data_ptr() for t in ts])
+        check(lib().fdtd_energy_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                        float(eps_r), float(mu_r), prec, ptrs,
+                                        ctypes.cast(ctypes.c_void_p(out.data_ptr()), ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.c_void_p(int(stream))), "fdtd_energy_noalloc")
     return out
 
 

@@ -38,7 +38,10 @@ double* g_scratch_dev[kMaxDevices] = {nullptr};
 
 // Device address of g_energy_scratch on the current device.  The host-side
 // name is only a stand-in, so the address is looked up once per device with
-// that device current, then cached.
+// that device current, then cached.  The cache assumes the device's context
+// lives as long as the process: after cudaDeviceReset (or a reset of the
+// primary context) the module is loaded again and the cached address may no
+// longer be valid, so this entry point must not be used after such a reset.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDTD_ERR_CUDA;
@@ -123,7 +126,16 @@ int run(int nx, int ny, int nz, double dv, double eps_r, double mu_r, const void
     F.sz[c] = ext[c][2];
     F.w[c] = c < 3 ? eps0 * eps_r : kMu0 * mu_r;
   }
+  // An error left pending by someone else is reported, not taken over: it
+  // stays pending for its owner, and nothing is launched.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    fprintf(stderr, "fdtd_energy_noalloc: a CUDA error is already pending (%s); nothing launched\n",
+            cudaGetErrorString(pending));
+    return FDTD_ERR_CUDA;
+  }
   plane_sumsq_kernel<T><<<dim3((unsigned)(nz + 1), 6), 256, 0, stream>>>(F, scratch);
+  if (cudaGetLastError() != cudaSuccess) return FDTD_ERR_CUDA;
   plane_total_kernel<T><<<1, 256, 0, stream>>>(F, scratch, 0.5 * dv, out_device);
   return cudaGetLastError() == cudaSuccess ? FDTD_OK : FDTD_ERR_CUDA;
 }

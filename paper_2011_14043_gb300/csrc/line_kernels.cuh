@@ -632,8 +632,14 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
   for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
     const int stage = k % NST;
     if (!mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs)) {
-      // Give up: flag it, let the other stages' copies (if any) land, return.
+      // Give up: flag it, then drain before the block's shared memory is
+      // released.  The timed-out stage's own bulk copy may still be in
+      // flight, so it gets a second bounded wait; then the other stages'
+      // copies (if any) land.  A copy still outstanding after that second
+      // limit is left in flight; the host reports FDTD_ERR_TIMEOUT and the
+      // step's results are not valid.
       if (threadIdx.x == 0) atomicExch(p.err, 1);
+      mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs);
       for (int d = 1; d < NST; ++d) {
         const int other = tile + d * (int)gridDim.x;
         const int st = (k + d) % NST;
@@ -765,8 +771,11 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
   for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
     const int stage = k % NST;
     if (!mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs)) {
-      // Give up: flag it, let the other stages' copies and our own stores land, return.
+      // Give up: flag it, drain as the register-store kernel does (a second
+      // bounded wait on the timed-out stage, then the other stages' copies),
+      // let our own stores land, return.
       if (threadIdx.x == 0) atomicExch(p.err, 1);
+      mbar_wait_bounded(&bars[stage], (parity >> stage) & 1u, kWaitLimitNs);
       for (int d = 1; d < NST; ++d) {
         const int other = tile + d * (int)gridDim.x;
         const int st = (k + d) % NST;

@@ -85,3 +85,31 @@ def test_fp64_probe_rejects_bad_arguments(L, iters):
     v = ctypes.c_double()
     assert L.fdtd_probe_fp64_fma(iters, ctypes.byref(v), None) == -1
     assert L.fdtd_probe_fp64_fma(10, None, None) == -1
+
+
+def test_energy_noalloc_binding_checks_before_launching(monkeypatch):
+    """The Python face of fdtd_energy_noalloc validates every tensor before
+    anything reaches the library: an `out` on the host or of another dtype,
+    or fields that are not CUDA tensors, raise ValueError (the library is
+    replaced by a stub that fails the test if called)."""
+    import torch
+    import paper_2011_14043_gb300 as P
+
+    def no_call():
+        raise AssertionError("the library must not be reached")
+
+    monkeypatch.setattr(P, "lib", no_call)
+    nx, ny, nz = 3, 4, 5
+    fields = {c: torch.zeros(P.comp_shape(c, nx, ny, nz), dtype=torch.float64) for c in P.COMPS}
+    with pytest.raises(ValueError, match="out"):
+        P.energy_noalloc(fields, nx, ny, nz, 1e-3, 1e-3, 1e-3, out=torch.zeros(1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="out"):
+        P.energy_noalloc(fields, nx, ny, nz, 1e-3, 1e-3, 1e-3, out=torch.zeros(1, dtype=torch.float32))
+    with pytest.raises(ValueError, match="out"):
+        P.energy_noalloc(fields, nx, ny, nz, 1e-3, 1e-3, 1e-3, out=torch.zeros(0, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        P.energy_noalloc(fields, nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    mixed = dict(fields)
+    mixed["hz"] = mixed["hz"].float()
+    with pytest.raises(ValueError, match="dtype"):
+        P.energy_noalloc(mixed, nx, ny, nz, 1e-3, 1e-3, 1e-3)

@@ -80,3 +80,34 @@ def test_injected_allocation_failures_are_reported_and_cleaned_up(prec):
     e, out = run_sequence(prec)
     assert e == ref_e
     assert np.array_equal(out, ref_out)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["flod", "fadi"])
+def test_invariant_growth_is_reported_as_unstable(scheme, prec):
+    """A source-free run conserves the scheme invariant exactly (every
+    procedure is a Cayley transform of an energy-skew operator): growth past
+    the reference taken when the run started is FDTD_ERR_UNSTABLE.  Growth is
+    planted from the host by scaling one E component of the state (a restored
+    "checkpoint" that is not one; fdtd_set_state keeps the reference), and a
+    legitimate new start (fdtd_set_field) takes a new reference."""
+    from paper_2011_14043_gb300 import FdtdError, Simulation
+    from gpu_helpers import random_fields
+    nx, ny, nz = 20, 18, 16
+    u0 = random_fields(nx, ny, nz, seed=5)
+    sim = Simulation(nx, ny, nz, 1e-3, scheme=scheme, precision=prec, cfl=6.0)
+    sim.set_fields(u0)
+    sim.step(20)
+    e_ok = sim.energy()
+    ex = sim.get_state("ex")
+    sim.set_state("ex", ex * 1.5)
+    sim.step(2)
+    with pytest.raises(FdtdError) as err:
+        sim.energy()
+    assert err.value.code == -5
+    # a new start from fields takes a new reference: no error
+    sim.set_fields(u0)
+    sim.step(20)
+    e_again = sim.energy()
+    assert e_again[1] == pytest.approx(e_ok[1], rel=1e-12 if prec == "f64" else 1e-4)
+    sim.close()

@@ -1,6 +1,9 @@
 """Full-size parity: cavity-mode workloads at their real sizes and step counts
 against the exact closed-form modal evolution of the oracle (oracle/modal.py,
-pinned to the stepper in test_oracle_modal.py), element by element.
+pinned to the stepper in test_oracle_modal.py), element by element; the
+eps-block dipole recipe (FLOD, FSS) and every instance of the 64-cavity batch
+at their full sizes against the FP64 oracle stepper over the steps it
+finishes in about a minute.
 
 Also checks the exactly conserved FADI invariant W(v) at full size."""
 import json
@@ -141,3 +144,66 @@ def test_batch_64_cavities_500_steps():
            smallest=[w.nx, w.ny, w.nz], f64_vs_oracle=err_oracle)
     assert max(errs) <= 1e-4
     assert err_oracle <= 1e-12
+
+
+def oracle_blocks(n, steps, scheme, seed=3):
+    """The FP64 oracle on the eps-block dipole recipe (zero initial field)."""
+    from oracle import schemes as S
+    from gpu_helpers import oracle_problem
+    d = 0.5e-3
+    g = G.Grid(n, n, n, d, d, d)
+    dt = 8.0 * g.dt_cfl()
+    eps = W.eps_blocks(seed, n, n, n, 1.0, 10.0)
+    cur = W.dipole_current((np.arange(steps) + 0.5) * dt)
+    P = oracle_problem(n, n, n, d, d, d, dt, eps=eps, source=("ez", n // 2, n // 2, n // 2, cur))
+    ref, _, _ = S.run_fundamental(P, scheme, W.zero_fields(n, n, n), steps)
+    return ref
+
+
+def check_components(out, ref, tol, floor=1e-4):
+    """Every component carrying at least `floor` of the energy within `tol`
+    relative L2 of the oracle's, and the whole field in the energy norm."""
+    err = energy_norm_rel(out, ref)
+    comps = per_comp_rel(out, ref, floor=floor)
+    assert err <= tol, err
+    for c, e in comps.items():
+        assert e <= tol, (c, e)
+    return err, comps
+
+
+@pytest.mark.parametrize("scheme", ["flod", "fss"])
+def test_blocks_256_vs_oracle(scheme):
+    """The full FLOD / FSS recipe (256^3, 0.5 mm cells, eps_r blocks U[1,10],
+    CFL 8, z dipole at the centre; Eqs. 15 and 17) element by element against
+    the FP64 oracle after 10 steps (what the numpy oracle finishes in about a
+    minute on the host): FP64 to 1e-12 and FP32 to 1e-4, the whole field and
+    every component carrying at least 1e-4 of the energy."""
+    steps = 10
+    ref = oracle_blocks(256, steps, scheme)
+    res = {}
+    for prec in ("f64", "f32"):
+        out = run_blocks(256, steps, prec, scheme)
+        res[prec] = check_components(out, ref, TOL[prec])
+    report(f"blocks256_{scheme}_vs_oracle", steps=steps,
+           f64=res["f64"][0], f32=res["f32"][0], f32_per_comp=res["f32"][1])
+
+
+def test_batch_64_every_instance_vs_oracle():
+    """Every one of the 64 cavities of the batch (uneven sizes, CFL numbers and
+    eps_r blocks, 8-mode field) against the FP64 oracle after 5 FADI steps of
+    the batch: FP64 to 1e-12 and FP32 to 1e-4 per instance, whole field and
+    every component carrying at least 1e-4 of the energy."""
+    from oracle import schemes as S
+    steps = 5
+    wls = W.workload_batch(seed=4, count=64, steps=500)
+    f64, dts = run_batch(wls, "f64", steps)
+    f32, _ = run_batch(wls, "f32", steps)
+    worst = {"f64": 0.0, "f32": 0.0}
+    for q, w in enumerate(wls):
+        g = G.Grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+        P = S.Problem(g, dts[q], eps_r_cell=w.eps_r)
+        ref, _, _ = S.run_fundamental(P, "fadi", w.fields, steps)
+        for prec, out in (("f64", f64[q]), ("f32", f32[q])):
+            err, _ = check_components(out, ref, TOL[prec])
+            worst[prec] = max(worst[prec], err)
+    report("batch64_every_instance_vs_oracle", steps=steps, worst_f64=worst["f64"], worst_f32=worst["f32"])
