@@ -37,7 +37,8 @@ def from_vec(grid: Grid, x: np.ndarray) -> dict:
 
 
 def assemble(grid: Grid, mat: dict):
-    """Dense A (Eq. 33) and B (Eq. 34)."""
+    """Dense A (Eq. 33) and B (Eq. 34) (with the split loss diagonal in a
+    lossy medium)."""
     off, n = layout(grid)
     nx, ny, nz = grid.nx, grid.ny, grid.nz
     dx, dy, dz = grid.dx, grid.dy, grid.dz
@@ -70,6 +71,18 @@ def assemble(grid: Grid, mat: dict):
             r = idx("ez", k, j, i); e = mat["ez"][k, j, i]
             A[r, idx("hy", k, j, i)] += 1 / (e * dx); A[r, idx("hy", k, j, i - 1)] -= 1 / (e * dx)
             B[r, idx("hx", k, j, i)] -= 1 / (e * dy); B[r, idx("hx", k, j - 1, i)] += 1 / (e * dy)
+    if "sigma" in mat:
+        # lossy media: -(1/2) sigma/eps on the diagonal of every interior E
+        # row, in A and in B alike
+        for c, inside in (("ex", lambda k, j, i: 1 <= j <= ny - 1 and 1 <= k <= nz - 1),
+                          ("ey", lambda k, j, i: 1 <= i <= nx - 1 and 1 <= k <= nz - 1),
+                          ("ez", lambda k, j, i: 1 <= i <= nx - 1 and 1 <= j <= ny - 1)):
+            for k, j, i in loop(c):
+                if inside(k, j, i):
+                    r = idx(c, k, j, i)
+                    g = 0.5 * mat["sigma"][c][k, j, i] / mat[c][k, j, i]
+                    A[r, r] -= g
+                    B[r, r] -= g
     for k, j, i in loop("hx"):
         r = idx("hx", k, j, i); m = mat["hx"][k, j, i]
         A[r, idx("ey", k + 1, j, i)] += 1 / (m * dz); A[r, idx("ey", k, j, i)] -= 1 / (m * dz)

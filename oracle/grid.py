@@ -4,6 +4,15 @@ Sec. III of the paper: lossless isotropic medium, u = (Ex, Ey, Ez, Hx, Hy, Hz),
 splitting operators A (Eq. 33) and B (Eq. 34) built from first differences
 d_x, d_y, d_z, and b = dt/(2 eps), d = dt/(2 mu) (Eq. 36).
 
+Lossy media (the paper assumes a lossless medium when it writes A and B;
+its splitting formulae of Sec. II hold for any linear operators): an
+electric conductivity sigma adds -sigma/eps E to dE/dt.  That diagonal term
+is split evenly between the two operators, A_s = A - (1/2) diag(sigma/eps)
+and B_s = B - (1/2) diag(sigma/eps) on the E rows, so that every E
+component, which has one line pair in A and one in B, loses half in each
+procedure.  In a procedure of length h the implicit diagonal becomes
+1/2 + b sigma / 4 (b = h / (2 eps)).
+
 Readings of what the paper leaves open (each is a documented choice):
 * differences are the standard Yee second-order central differences between
   staggered samples (sample layout in ``workloads``);
@@ -108,8 +117,10 @@ def _avg(cells: np.ndarray, pad: tuple, windows) -> np.ndarray:
     return s / n
 
 
-def material_at_samples(grid: Grid, eps_r_cell=None, mu_r_cell=None) -> dict:
-    """Absolute eps at every E sample and mu at every H sample."""
+def material_at_samples(grid: Grid, eps_r_cell=None, mu_r_cell=None, sigma_cell=None) -> dict:
+    """Absolute eps at every E sample and mu at every H sample; with a
+    per-cell conductivity [S/m], also mat["sigma"][ec] at every E sample (the
+    mean of the in-domain cells sharing the edge, as for eps)."""
     nx, ny, nz = grid.nx, grid.ny, grid.nz
     er = np.ones((nz, ny, nx)) if eps_r_cell is None else np.asarray(eps_r_cell, dtype=np.float64)
     mr = np.ones((nz, ny, nx)) if mu_r_cell is None else np.asarray(mu_r_cell, dtype=np.float64)
@@ -130,6 +141,16 @@ def material_at_samples(grid: Grid, eps_r_cell=None, mu_r_cell=None) -> dict:
                                             (b, slice(1, ny + 2), slice(0, nx + 1)),
                                             (b, slice(0, ny + 1), slice(1, nx + 2)),
                                             (b, slice(1, ny + 2), slice(1, nx + 2))])
+    if sigma_cell is not None:
+        sg = np.asarray(sigma_cell, dtype=np.float64)
+        out["sigma"] = {
+            "ex": _avg(sg, (1, 1, 0), [(slice(0, nz + 1), slice(0, ny + 1), b), (slice(1, nz + 2), slice(0, ny + 1), b),
+                                      (slice(0, nz + 1), slice(1, ny + 2), b), (slice(1, nz + 2), slice(1, ny + 2), b)]),
+            "ey": _avg(sg, (1, 0, 1), [(slice(0, nz + 1), b, slice(0, nx + 1)), (slice(1, nz + 2), b, slice(0, nx + 1)),
+                                      (slice(0, nz + 1), b, slice(1, nx + 2)), (slice(1, nz + 2), b, slice(1, nx + 2))]),
+            "ez": _avg(sg, (0, 1, 1), [(b, slice(0, ny + 1), slice(0, nx + 1)), (b, slice(1, ny + 2), slice(0, nx + 1)),
+                                      (b, slice(0, ny + 1), slice(1, nx + 2)), (b, slice(1, ny + 2), slice(1, nx + 2))]),
+        }
     # Hx face (i, j+1/2, k+1/2): cells (i-1..i, j, k)
     out["hx"] = MU0 * _avg(mr, (0, 0, 1), [(b, b, slice(0, nx + 1)), (b, b, slice(1, nx + 2))])
     # Hy face (i+1/2, j, k+1/2): cells (i, j-1..j, k)
@@ -169,13 +190,16 @@ def diff_e_to_h(e: np.ndarray, axis: int, spacing: float) -> np.ndarray:
 
 
 def apply_op(grid: Grid, mat: dict, op: str, u: dict) -> dict:
-    """O u for O = A (Eq. 33) or B (Eq. 34), PEC walls applied."""
+    """O u for O = A (Eq. 33) or B (Eq. 34), PEC walls applied; in a lossy
+    medium each operator also carries -(1/2)(sigma/eps) E on its E rows."""
     out = {c: np.zeros(grid.shape(c)) for c in COMPS}
     for ec, hc, ax, sgn in PAIRS[op]:
         a = AXIS[ax]
         sp = grid.spacing[ax]
         out[ec] += sgn * diff_h_to_e(u[hc], a, sp, grid.shape(ec)) / mat[ec]
         out[hc] += sgn * diff_e_to_h(u[ec], a, sp) / mat[hc]
+        if "sigma" in mat:
+            out[ec] -= 0.5 * mat["sigma"][ec] / mat[ec] * u[ec]
     for ec in E_COMPS:
         out[ec] *= grid.e_interior_mask(ec)
     return out
@@ -209,10 +233,13 @@ def line_operator_coeffs(gE: np.ndarray, gH: np.ndarray, axis: int, spacing: flo
     return lower, centre, upper
 
 
-def solve_lines(alpha: float, lower, centre, upper, rhs_e: np.ndarray, axis: int) -> np.ndarray:
+def solve_lines(alpha, lower, centre, upper, rhs_e: np.ndarray, axis: int) -> np.ndarray:
     """Solve alpha*w - (lower, centre, upper)-operator w = rhs along ``axis``
-    for the interior nodes; w = 0 on the two end nodes (PEC)."""
+    for the interior nodes; w = 0 on the two end nodes (PEC).  alpha is a
+    number or an array of the E component's shape (one diagonal per node)."""
     r = np.moveaxis(rhs_e, axis, -1)
+    if np.ndim(alpha):
+        alpha = np.moveaxis(alpha, axis, -1)[..., 1:-1]
     x = thomas(-lower, alpha - centre, -upper, r[..., 1:-1])
     w = np.zeros_like(r)
     w[..., 1:-1] = x
@@ -225,7 +252,8 @@ def solve_implicit(grid: Grid, mat: dict, op: str, tau: float, rhs: dict) -> dic
     For a pair with E row  E - sgn*(tau/eps) d(H) = rE  and H row
     H - sgn*(tau/mu) d(E) = rH, substituting H = rH + sgn*(tau/mu) d(E) gives
     the tridiagonal line system E - (tau/eps) d((tau/mu) d E) = rE + sgn*(tau/eps) d(rH);
-    H is then recovered explicitly.  tau may be negative."""
+    H is then recovered explicitly.  In a lossy medium the E row's diagonal
+    is 1 + tau sigma / (2 eps).  tau may be negative."""
     out = {}
     for ec, hc, ax, sgn in PAIRS[op]:
         a = AXIS[ax]
@@ -235,7 +263,8 @@ def solve_implicit(grid: Grid, mat: dict, op: str, tau: float, rhs: dict) -> dic
         gH = tau / mat[hc]
         rE = (rhs[ec] + sgn * gE * diff_h_to_e(rhs[hc], a, sp, grid.shape(ec))) * mask
         lo, ce, up = line_operator_coeffs(gE, gH, a, sp)
-        w = solve_lines(1.0, lo, ce, up, rE, a) * mask
+        alpha = 1.0 + 0.5 * tau * mat["sigma"][ec] / mat[ec] if "sigma" in mat else 1.0
+        w = solve_lines(alpha, lo, ce, up, rE, a) * mask
         out[ec] = w
         out[hc] = rhs[hc] + sgn * gH * diff_e_to_h(w, a, sp)
     return out

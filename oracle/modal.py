@@ -34,8 +34,11 @@ OFFSET = {"ex": (0.5, 0, 0), "ey": (0, 0.5, 0), "ez": (0, 0, 0.5),
           "hx": (0, 0.5, 0.5), "hy": (0.5, 0, 0.5), "hz": (0.5, 0.5, 0)}
 
 
-def mode_operators(grid: Grid, m: int, n: int, p: int, eps: float = EPS0, mu: float = MU0):
-    """A and B (Eqs. 33-34) restricted to the mode's 6-dimensional space."""
+def mode_operators(grid: Grid, m: int, n: int, p: int, eps: float = EPS0, mu: float = MU0,
+                   sigma: float = 0.0):
+    """A and B (Eqs. 33-34) restricted to the mode's 6-dimensional space; a
+    homogeneous conductivity sigma puts -sigma/(2 eps) on the E diagonal of
+    each (the split loss of oracle.grid)."""
     kx = (2.0 / grid.dx) * math.sin(m * math.pi / grid.nx / 2.0)
     ky = (2.0 / grid.dy) * math.sin(n * math.pi / grid.ny / 2.0)
     kz = (2.0 / grid.dz) * math.sin(p * math.pi / grid.nz / 2.0)
@@ -56,6 +59,8 @@ def mode_operators(grid: Grid, m: int, n: int, p: int, eps: float = EPS0, mu: fl
     B[HX, EZ] = -ky / mu
     B[HY, EX] = -kz / mu
     B[HZ, EY] = -kx / mu
+    for q in (EX, EY, EZ):
+        A[q, q] = B[q, q] = -0.5 * sigma / eps
     return A, B
 
 
@@ -89,12 +94,14 @@ def mode_shape(grid: Grid, comp: str, m: int, n: int, p: int) -> np.ndarray:
     return z[:, None, None] * y[None, :, None] * x[None, None, :]
 
 
-def evolve_modes(grid: Grid, dt: float, scheme: str, modes, steps: int):
-    """6-vectors of every mode after ``steps`` steps.  modes: iterable of
-    (m, n, p, c0) with c0 the initial 6-vector (Ex, Ey, Ez, Hx, Hy, Hz)."""
+def evolve_modes(grid: Grid, dt: float, scheme: str, modes, steps: int, eps: float = EPS0,
+                 sigma: float = 0.0):
+    """6-vectors of every mode after ``steps`` steps (homogeneous eps and
+    conductivity sigma, mu0).  modes: iterable of (m, n, p, c0) with c0 the
+    initial 6-vector (Ex, Ey, Ez, Hx, Hy, Hz)."""
     out = []
     for m, n, p, c0 in modes:
-        A, B = mode_operators(grid, m, n, p)
+        A, B = mode_operators(grid, m, n, p, eps=eps, sigma=sigma)
         G = amplification(scheme, dt, A, B)
         c = np.asarray(c0, dtype=np.float64)
         for _ in range(steps):
@@ -114,10 +121,12 @@ def fields_from_modes(grid: Grid, modal) -> dict:
     return f
 
 
-def field_after(grid: Grid, dt: float, scheme: str, modes, steps: int) -> dict:
+def field_after(grid: Grid, dt: float, scheme: str, modes, steps: int, eps_r: float = 1.0,
+                sigma: float = 0.0) -> dict:
     """Exact field after ``steps`` steps from an initial E that is a sum of
-    cavity modes (H = 0).  modes: objects with m, n, p, amp, pol (the
-    workload generator's records)."""
+    cavity modes (H = 0), in a homogeneous medium (eps_r, conductivity
+    sigma).  modes: objects with m, n, p, amp, pol (the workload generator's
+    records)."""
     init = [(md.m, md.n, md.p, np.array([md.amp * md.pol[0], md.amp * md.pol[1], md.amp * md.pol[2], 0, 0, 0]))
             for md in modes]
-    return fields_from_modes(grid, evolve_modes(grid, dt, scheme, init, steps))
+    return fields_from_modes(grid, evolve_modes(grid, dt, scheme, init, steps, eps=EPS0 * eps_r, sigma=sigma))

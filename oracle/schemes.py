@@ -55,10 +55,11 @@ class Problem:
     eps_r_cell: np.ndarray | None = None
     mu_r_cell: np.ndarray | None = None
     source: Source | None = None
+    sigma_cell: np.ndarray | None = None     # electric conductivity [S/m] per cell (lossy media)
     mat: dict = field(init=False)
 
     def __post_init__(self):
-        self.mat = material_at_samples(self.grid, self.eps_r_cell, self.mu_r_cell)
+        self.mat = material_at_samples(self.grid, self.eps_r_cell, self.mu_r_cell, self.sigma_cell)
 
     def f(self, t: float) -> dict | None:
         """Source vector f = (-J/eps, 0) at time t, or None."""
@@ -178,6 +179,8 @@ def procedure(P: Problem, state: dict, op: str, h: float, rhs_src: dict | None =
       subtract  E <- w - E                                     (Eqs. 40, 47, 50)
 
     with b = h/(2 eps), d = h/(2 mu) (Eq. 36), sgn = +1 for A and -1 for B.
+    In a lossy medium the implicit diagonal is 1/2 + b sigma / 4 (the
+    operator's half of the loss).
     ``rhs_src`` is added to the implicit right-hand side, ``post_src`` to the
     new E state.  Returns (new_state, w, H_before)."""
     g = P.grid
@@ -194,8 +197,9 @@ def procedure(P: Problem, state: dict, op: str, h: float, rhs_src: dict | None =
             r = r + rhs_src[ec]
         r = r * mask
         lo, ce, up = line_operator_coeffs(b, d, a, sp)
+        diag = 0.5 + 0.25 * b * P.mat["sigma"][ec] if "sigma" in P.mat else 0.5
         # 1/2 w - (b/2) d(d dw): the line operator scaled by 1/2
-        w = solve_lines(0.5, 0.5 * lo, 0.5 * ce, 0.5 * up, r, a) * mask
+        w = solve_lines(diag, 0.5 * lo, 0.5 * ce, 0.5 * up, r, a) * mask
         w_all[ec] = w
         new[hc] = state[hc] + sgn * d * diff_e_to_h(w, a, sp)
         e_new = w - state[ec]
