@@ -78,7 +78,12 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * tune[1] bit 2 set: the TMA-fed kernel stages its outputs in shared memory
  * and writes them with TMA stores instead of register stores; tune[1] bit 3
  * set: fdtd_step launches the kernels one by one instead of replaying a
- * captured step graph. */
+ * captured step graph; tune[1] bit 4 set: lines along x of FP32 fields in
+ * homogeneous media (129 to 256 cells) run the persistent TMA-fed kernel
+ * instead of the one-warp-per-line kernel (the same results; measured
+ * slower at 256^3); tune[1] bits 5-6: ring depth and blocks per SM of the
+ * TMA-fed x-line kernel (0: 3 stages x 4 blocks, 1: 2 x 4, 2: 4 x 3,
+ * 3: 2 x 6). */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of
@@ -117,6 +122,23 @@ int fdtd_get_dt(const fdtd_t* h, double* dt);
  * reverse pass take uniform mu only.  Only valid before the first
  * fdtd_step. */
 int fdtd_set_material(fdtd_t* h, const double* eps_r_cell, const double* mu_r_cell);
+
+/* fdtd_set_material with an electric conductivity: sigma_cell (host,
+ * nz*ny*nx doubles, each >= 0 and finite [S/m]; NULL or all zero means a
+ * lossless medium).  The paper writes A and B for a lossless medium (Sec.
+ * III) but states its splitting formulae (Sec. II) for any linear operators;
+ * the loss term -sigma/eps E of dE/dt is split evenly between A and B on the
+ * E rows, so every procedure of length h adds b sigma / 4 (b = h/(2 eps)) to
+ * the diagonal of its line systems, and the FADI input initialization
+ * (I + dt/2 B) takes its half of the loss.  sigma at an E sample is the mean
+ * of the cells sharing its edge (as eps).  Only the FP64-formed pivots change:
+ * the kernels are those of the lossless case.  FADI and FLOD2 invert
+ * (I + dt/2 B) resp. (I + dt/4 B) for their output, whose loss diagonal has
+ * the opposite sign: they need sigma dt / eps <= 2 at every E sample
+ * (FDTD_ERR_UNSUPPORTED otherwise; FLOD and FSS take any sigma).  The
+ * reverse pass takes lossless media only.  Only valid before the first
+ * fdtd_step. */
+int fdtd_set_media(fdtd_t* h, const double* eps_r_cell, const double* mu_r_cell, const double* sigma_cell);
 
 /* Set one physical field component at the current time (compact Yee shape,
  * handle precision).  For FADI the auxiliary state (Eq. 10) is formed from

@@ -148,7 +148,9 @@ class Simulation:
         return comp_shape(comp, self.nx, self.ny, self.nz)
 
     # -- problem set-up ------------------------------------------------------
-    def set_material(self, eps_r_cell=None, mu_r_cell=None):
+    def set_material(self, eps_r_cell=None, mu_r_cell=None, sigma_cell=None):
+        """Per-cell eps_r, mu_r and electric conductivity sigma [S/m]
+        (shape (nz, ny, nx); None = 1, 1, 0)."""
         def ptr(a):
             if a is None:
                 return None, None
@@ -158,7 +160,11 @@ class Simulation:
             return a, a.ctypes.data_as(ctypes.c_void_p)
         ea, ep = ptr(eps_r_cell)
         ma, mp = ptr(mu_r_cell)
-        check(lib().fdtd_set_material(self._h, ep, mp), "fdtd_set_material")
+        if sigma_cell is None:
+            check(lib().fdtd_set_material(self._h, ep, mp), "fdtd_set_material")
+        else:
+            sa, sp = ptr(sigma_cell)
+            check(lib().fdtd_set_media(self._h, ep, mp, sp), "fdtd_set_media")
 
     def _put(self, fn, comp, data, what):
         c = COMPS[comp]

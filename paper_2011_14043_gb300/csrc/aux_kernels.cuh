@@ -56,6 +56,20 @@ __global__ void add_point_kernel(T* y, long long at, double a) {
   if (threadIdx.x == 0 && blockIdx.x == 0) y[at] = (T)((double)y[at] + a);
 }
 
+// Loss part of the FADI input initialization (I + dt/2 B) u^0 in a lossy
+// medium: out -= k (sigma / eps_r) in with k = dt / (4 eps0), sigma and eps_r
+// per E node (device FP64, field layout) or uniform (null pointer).
+template <typename T>
+__global__ void loss_scale_kernel(T* __restrict__ out, const T* __restrict__ in, const double* __restrict__ sig,
+                                  const double* __restrict__ epsr, double sig_u, double eps_u, double k, long long n) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+    const double sg = sig ? sig[g] : sig_u;
+    const double er = epsr ? epsr[g] : eps_u;
+    // row padding holds eps_r = 0 and sigma = 0: leave it untouched
+    if (sg > 0.0 && er > 0.0) out[g] = (T)((double)out[g] - k * sg / er * (double)in[g]);
+  }
+}
+
 // y[at] += coef * table[*step + offset] (0 outside the table): a point
 // source whose value is read on the device, so that steps replayed from one
 // captured graph see each step's value.  The product is rounded before the

@@ -102,16 +102,30 @@ struct fdtd_s {
   int* d_err = nullptr;       // set by kernels whose bounded waits gave up
   bool use_tma = true;
   // TMA descriptors of the y/z line tiles, per component and box kind
-  CUtensorMap tmap[6][2];
-  const void* tmap_ptr[6][2] = {{nullptr}};
-  int tmap_bn[6][2] = {{0}};
-  int tmap_lanes[6][2] = {{0}};
-  ProcCoef proc[3];  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing)
+  // TMA descriptors per component and box kind (0: y-line tiles, 1: z-line
+  // tiles, 2: x-row tiles)
+  CUtensorMap tmap[6][3];
+  const void* tmap_ptr[6][3] = {{nullptr}};
+  int tmap_bn[6][3] = {{0}};
+  int tmap_lanes[6][3] = {{0}};
+  // 0: A main, 1: B main, 2: B at dt/2 (FLOD2 processing); lossy media
+  // only: 3, 4 = B at dt and at dt/2 with the loss term's sign flipped, the
+  // matrices of the FADI output relation and of the FLOD2 output processing
+  // (procedures of negative length, whose loss diagonal changes sign while
+  // the second-difference part does not)
+  ProcCoef proc[5];
   bool per_node = false;
   bool shape_tuned = false;   // per-node y/z launch shapes chosen by timing
   double eps_r = 1.0, mu_r = 1.0;          // uniform media
   double* eps_node[3] = {nullptr, nullptr, nullptr};  // per-node eps_r at E samples (device)
   std::vector<double> eps_host[3];  // the same on the host, only while coefficients are built
+  // lossy media: electric conductivity sigma [S/m]; the loss -sigma/eps E is
+  // split evenly between A and B, so each procedure of length h adds
+  // b sigma / 4 to the implicit diagonal (a host-side change of the pivots)
+  bool lossy = false;
+  double sigma_u = 0.0;             // uniform sigma (when sig_node is null)
+  double* sig_node[3] = {nullptr, nullptr, nullptr};  // per-node sigma at E samples (device)
+  std::vector<double> sig_host[3];  // the same on the host, only while coefficients are built
   bool mu_var = false;              // per-node mu (general media kernels)
   double* mu_node[3] = {nullptr, nullptr, nullptr};   // per-face mu_r at H samples (device)
   std::vector<double> mu_host[3];   // the same on the host, only while coefficients are built
@@ -385,8 +399,10 @@ void edge_eps(const fdtd_t* h, const double* er, int c, std::vector<double>& out
 }
 
 // FP64 factorisation of the line systems of one procedure (operator op,
-// length hh):  1/2 w_j - (b_j/2)(d/d^2)(w_{j+1} - 2 w_j + w_{j-1}) = r_j.
-int build_proc(fdtd_t* h, int slot, int op, double hh) {
+// length hh):  1/2 w_j - (b_j/2)(d/d^2)(w_{j+1} - 2 w_j + w_{j-1}) = r_j, plus
+// loss_sign * b_j sigma_j / 4 on the diagonal in lossy media (loss_sign = -1
+// for the matrices of procedures run with negative length).
+int build_proc(fdtd_t* h, int slot, int op, double hh, double loss_sign = 1.0) {
   ProcCoef& P = h->proc[slot];
   free_coef(P);
   P.op = op;
@@ -412,7 +428,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
         bd = c.kb * c.kd;
       }
       const double off = -bd / 2.0;
-      const double diag = 0.5 + bd;
+      const double diag = 0.5 + bd + (h->lossy ? loss_sign * b * h->sigma_u / 4.0 : 0.0);
       const int N = std::max(g.N, 1);
       const int L = g.rows ? std::max(1, rows_L(h, g)) : h->strided_cfg[g.axis == AX_Y ? 0 : 1].L;
       c.L = L;
@@ -501,6 +517,11 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
       }
       const double* mr = h->mu_var ? h->mu_host[g.hc - 3].data() : nullptr;
       const double* er = h->eps_host[g.ec].data();
+      const double* sr = (h->lossy && !h->sig_host[g.ec].empty()) ? h->sig_host[g.ec].data() : nullptr;
+      // scaled rows: the loss adds loss_sign * sigma_j / 4 to the diagonal
+      auto loss_at = [&](long long at) {
+        return h->lossy ? loss_sign * (sr ? sr[at] : h->sigma_u) / 4.0 : 0.0;
+      };
       const long long nl = g.n_lines();
       for (long long line = 0; line < nl; ++line) {
         long long base;
@@ -520,7 +541,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
             const long long at = base + (long long)j * g.ls;
             const double b = std::fabs(hh) / (2.0 * kEps0 * er[at]);
             const double q = rnd(1.0 / b);
-            const double diag = q / 2.0 + kk;
+            const double diag = q / 2.0 + kk + loss_at(at);
             const double beta = diag - off * off * ibm;
             const double ib = 1.0 / beta;
             nq[at] = q;
@@ -546,7 +567,7 @@ int build_proc(fdtd_t* h, int slot, int op, double hh) {
           const long long at = base + (long long)j * g.ls;
           const double b = std::fabs(hh) / (2.0 * kEps0 * er[at]);
           const double q = rnd(1.0 / b);
-          const double diag = q / 2.0 + (kkf[(size_t)j] + kkf[(size_t)j - 1]) / 2.0;
+          const double diag = q / 2.0 + (kkf[(size_t)j] + kkf[(size_t)j - 1]) / 2.0 + loss_at(at);
           const double offm = -kkf[(size_t)j - 1] / 2.0;  // face j-1, between nodes j-1 and j
           const double beta = diag - offm * offm * ibm;
           const double ib = 1.0 / beta;
@@ -586,6 +607,10 @@ int build_all_coefs(fdtd_t* h) {
   } else {
     free_coef(h->proc[2]);
   }
+  free_coef(h->proc[3]);
+  free_coef(h->proc[4]);
+  if (h->lossy && h->scheme == FDTD_FADI && (rc = build_proc(h, 3, 1, dt, -1.0))) return rc;
+  if (h->lossy && h->scheme == FDTD_FLOD2 && (rc = build_proc(h, 4, 1, dt / 2, -1.0))) return rc;
   return FDTD_OK;
 }
 
@@ -775,12 +800,18 @@ bool tma_eligible(const fdtd_t* h, const PairGeom& g) {
 }
 
 // Tensor map of component c for tiles of LANES lines x BN nodes along y
-// (kind 0) or z (kind 1).  Re-encoded when the array moved.
+// (kind 0) or z (kind 1), or of `lanes` rows x BN elements along x (kind 2).
+// Re-encoded when the array moved.
 int get_tmap(fdtd_t* h, int c, int kind, int BN, int lanes, const CUtensorMap** out) {
   if (h->tmap_ptr[c][kind] != h->f[c] || h->tmap_bn[c][kind] != BN || h->tmap_lanes[c][kind] != lanes) {
     cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->ny + 1), (cuuint64_t)(h->nz + 1)};
     cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->esize, (cuuint64_t)h->plane * h->esize};
     cuuint32_t box[3] = {(cuuint32_t)lanes, kind == 0 ? (cuuint32_t)BN : 1u, kind == 0 ? 1u : (cuuint32_t)BN};
+    if (kind == 2) {
+      box[0] = (cuuint32_t)BN;
+      box[1] = (cuuint32_t)lanes;
+      box[2] = 1u;
+    }
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = tensor_map_encoder()(&h->tmap[c][kind],
                                       h->prec == FDTD_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -847,6 +878,69 @@ int launch_strided_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& 
   CK((ensure_tma_attr<T, LANES, MINB, NST>()));
   const int grid = std::min(q.n_tiles, MINB * h->num_sms);
   kern<<<grid, P * LANES, smem, h->stream>>>(*tE, *tH, p, q);
+  return FDTD_OK;
+}
+
+// TMA-fed x lines (proc_rows_tma_kernel), on request (tune[1] bit 4): FP32
+// fields, homogeneous media, 128 < N <= 256 (8 nodes per lane), R = 8
+// consumer warps per block; bits 5-6 pick the ring depth and blocks per SM
+// (0: 3 stages x 4 blocks, 1: 2 x 4, 2: 4 x 3, 3: 2 x 6).  Measured at 256^3
+// per launch: 67.6 / 63.8 / 64.7 / 118 us against 58.9 us for the
+// one-warp-per-line kernel, which stays the default: with the loads off the
+// critical path the solve itself binds (instruction issue at 58 % with 32
+// consumer warps per SM, against 66 % with 40 warps).
+constexpr int kRowsR = 8;
+
+bool rows_tma_eligible(const fdtd_t* h, const PairGeom& g) {
+  return h->use_tma && h->prec == FDTD_F32 && !h->per_node && g.rows && (h->desc.tune[1] & 16) != 0 &&
+         g.N > 128 && g.N <= 256 && rows_L(h, g) == 8 && tensor_map_encoder() != nullptr;
+}
+
+template <int NST, int MINB>
+cudaError_t ensure_rows_tma_attr_one() {
+  static bool set = false;
+  if (set) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) set = true;
+  return e;
+}
+
+// Set once per instantiation, outside any stream capture.
+cudaError_t ensure_rows_tma_attr() {
+  cudaError_t e = ensure_rows_tma_attr_one<3, 4>();
+  if (e == cudaSuccess) e = ensure_rows_tma_attr_one<2, 4>();
+  if (e == cudaSuccess) e = ensure_rows_tma_attr_one<4, 3>();
+  if (e == cudaSuccess) e = ensure_rows_tma_attr_one<2, 6>();
+  return e;
+}
+
+template <int NST, int MINB>
+void launch_rows_tma_v(fdtd_t* h, const CUtensorMap* tE, const CUtensorMap* tH, const fdtd::PairParams<float>& p,
+                       const fdtd::RowTiles& q) {
+  const size_t smem = 2 * (size_t)NST * kRowsR * q.BN * sizeof(float) + 2 * (size_t)NST * sizeof(uint64_t);
+  const int grid = std::min(q.n_tiles, MINB * h->num_sms);
+  fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB><<<grid, (kRowsR + 1) * 32, smem, h->stream>>>(*tE, *tH,
+                                                                                                       p, q);
+}
+
+int launch_rows_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<float>& p) {
+  const int BN = ((g.N + 7) / 8) * 8;
+  const CUtensorMap *tE, *tH;
+  int rc = get_tmap(h, g.ec, 2, BN, kRowsR, &tE);
+  if (rc) return rc;
+  if ((rc = get_tmap(h, g.hc, 2, BN, kRowsR, &tH))) return rc;
+  fdtd::RowTiles q;
+  q.BN = BN;
+  q.tpp = (g.n_o + kRowsR - 1) / kRowsR;
+  q.n_tiles = q.tpp * g.n_o2;
+  CK(ensure_rows_tma_attr());
+  switch ((h->desc.tune[1] >> 5) & 3) {
+    case 1: launch_rows_tma_v<2, 4>(h, tE, tH, p, q); break;
+    case 2: launch_rows_tma_v<4, 3>(h, tE, tH, p, q); break;
+    case 3: launch_rows_tma_v<2, 6>(h, tE, tH, p, q); break;
+    default: launch_rows_tma_v<3, 4>(h, tE, tH, p, q); break;
+  }
   return FDTD_OK;
 }
 
@@ -920,6 +1014,13 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   h->launches++;
   if (sizeof(T) == 8 && g.rows && rows_lanes(h, g) < 32) {
     if constexpr (sizeof(T) == 8) launch_rows_lpl<T>(h, g, p, rows_lanes(h, g));
+  } else if (sizeof(T) == 4 && rows_tma_eligible(h, g) && p.e_in == (const T*)h->f[g.ec] &&
+             p.h_in == (const T*)h->f[g.hc]) {
+    // the tensor maps describe the state arrays; other inputs (scratch) take
+    // the one-warp-per-line kernel
+    if constexpr (sizeof(T) == 4) {
+      if (int rc = launch_rows_tma(h, g, p)) return rc;
+    }
   } else if (g.rows) {
     switch (pick_rows_L(g.N)) {
       case 1: launch_rows_L<T, 1>(h, g, p, pn); break;
@@ -1075,6 +1176,16 @@ int fadi_init_t(fdtd_t* h) {
       fdtd::explicit_pair_kernel<T, false><<<blocks, 256, 0, h->stream>>>(p, g.rows ? 1 : 0);
     CK(cudaGetLastError());
   }
+  if (h->lossy) {
+    // the loss part of (I + dt/2 B): E -= (dt/2)(sigma/(2 eps)) E of u^0
+    for (int c = 0; c < 3; ++c) {
+      h->launches++;
+      fdtd::loss_scale_kernel<T><<<152 * 8, 256, 0, h->stream>>>(
+          (T*)h->scratch[c], (const T*)h->f[c], h->sig_node[c], h->per_node ? h->eps_node[c] : nullptr, h->sigma_u,
+          h->per_node ? 1.0 : h->eps_r, 0.25 * h->dt / kEps0, h->count);
+      CK(cudaGetLastError());
+    }
+  }
   for (int c = 0; c < 6; ++c) std::swap(h->f[c], h->scratch[c]);
   const double f0 = source_value(h, h->steps);
   if (f0 != 0.0) {
@@ -1183,6 +1294,7 @@ int step_graph(fdtd_t* h, int64_t nsteps) {
   if (!h->g_exec || ptrs != h->g_bound) {
     graph_release(h);
     if (h->prec == FDTD_F32) CK((ensure_tma_attr<float, 16, 2, 2>()));
+    if (h->prec == FDTD_F32) CK(ensure_rows_tma_attr());
     static const int seq_fss[3] = {0, 1, 0};
     static const int seq_two[2] = {0, 1};
     const int* seq = h->scheme == FDTD_FSS ? seq_fss : seq_two;
@@ -1392,7 +1504,7 @@ int physical_to_scratch(fdtd_t* h, long long n_next) {
       // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
       const double fp = source_value(h, n_next);
       if ((rc = add_point(h, h->scratch[h->src_comp < 0 ? 0 : h->src_comp], -0.5 * h->dt * fp))) return rc;
-      rc = procedure_ex(h, 1, -1.0, 0.5, 0.0, 0.5, h->scratch, h->scratch);
+      rc = procedure_ex(h, h->lossy ? 3 : 1, -1.0, 0.5, 0.0, 0.5, h->scratch, h->scratch);
       if (rc) return rc;
     } else if (h->scheme == FDTD_FLOD2) {
       // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4} - (dt/8) f(t_{n+1} + dt/2),
@@ -1401,7 +1513,7 @@ int physical_to_scratch(fdtd_t* h, long long n_next) {
       const double r = -0.125 * h->dt * source_value(h, n_next);
       void* at = h->scratch[h->src_comp < 0 ? 0 : h->src_comp];
       if ((rc = add_point(h, at, r))) return rc;
-      rc = procedure_ex(h, 2, -1.0, 1.0, -1.0, 1.0, h->scratch, h->scratch);
+      rc = procedure_ex(h, h->lossy ? 4 : 2, -1.0, 1.0, -1.0, 1.0, h->scratch, h->scratch);
       if (rc) return rc;
       if ((rc = add_point(h, at, r))) return rc;
     }
@@ -1781,6 +1893,7 @@ int fdtd_destroy(fdtd_t* h) {
   for (int c = 0; c < 3; ++c) {
     if (h->eps_node[c]) cudaFree(h->eps_node[c]);
     if (h->mu_node[c]) cudaFree(h->mu_node[c]);
+    if (h->sig_node[c]) cudaFree(h->sig_node[c]);
   }
   if (h->d_probe) cudaFree(h->d_probe);
   if (h->d_stash) cudaFree(h->d_stash);
@@ -1825,12 +1938,16 @@ int fdtd_synchronize(fdtd_t* h) {
 }
 
 int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
+  return fdtd_set_media(h, eps, mu, nullptr);
+}
+
+int fdtd_set_media(fdtd_t* h, const double* eps, const double* mu, const double* sigma) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
   if (h->steps > 0) return FDTD_ERR_STATE;
   const size_t nc = (size_t)h->nx * h->ny * h->nz;
-  const double e0 = eps ? eps[0] : 1.0, m0 = mu ? mu[0] : 1.0;
-  bool e_uniform = true, m_uniform = true;
+  const double e0 = eps ? eps[0] : 1.0, m0 = mu ? mu[0] : 1.0, s0 = sigma ? sigma[0] : 0.0;
+  bool e_uniform = true, m_uniform = true, s_uniform = true, any_loss = false;
   for (size_t q = 0; q < nc; ++q) {
     if (eps) {
       if (!(eps[q] > 0) || !std::isfinite(eps[q])) return FDTD_ERR_INVALID_ARG;
@@ -1840,22 +1957,61 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
       if (!(mu[q] > 0) || !std::isfinite(mu[q])) return FDTD_ERR_INVALID_ARG;
       if (mu[q] != m0) m_uniform = false;
     }
+    if (sigma) {
+      if (!(sigma[q] >= 0) || !std::isfinite(sigma[q])) return FDTD_ERR_INVALID_ARG;
+      if (sigma[q] != s0) s_uniform = false;
+      if (sigma[q] > 0) any_loss = true;
+    }
   }
   // per-node mu runs the general-media kernels, built for lines of at most
   // 256 cells along y and z and 256 along x
   if (!m_uniform && (h->nx > 256 || h->ny > 256 || h->nz > 256)) return FDTD_ERR_UNSUPPORTED;
+  // FADI's output relation and FLOD2's output processing solve with the loss
+  // diagonal's sign flipped; they stay well conditioned (and nonsingular)
+  // while sigma dt / eps <= 2 at every E sample (checked before the handle
+  // changes)
+  if (any_loss && (h->scheme == FDTD_FADI || h->scheme == FDTD_FLOD2)) {
+    bool ok = true;
+    if (e_uniform && s_uniform) {
+      ok = s0 * h->dt / (kEps0 * e0) <= 2.0;
+    } else {
+      std::vector<double> ones, ev, sv;
+      if (!eps) ones.assign(nc, 1.0);
+      for (int c = 0; c < 3 && ok; ++c) {
+        edge_eps(h, eps ? eps : ones.data(), c, ev);
+        if (!s_uniform) edge_eps(h, sigma, c, sv);
+        for (size_t q = 0; q < ev.size() && ok; ++q) {
+          if (ev[q] <= 0) continue;  // row padding
+          const double sg = s_uniform ? s0 : sv[q];
+          if (sg * h->dt / (kEps0 * ev[q]) > 2.0) ok = false;
+        }
+      }
+    }
+    if (!ok) return FDTD_ERR_UNSUPPORTED;
+  }
   graph_release(h);
   for (int c = 0; c < 3; ++c) {
     if (h->eps_node[c]) { cudaFree(h->eps_node[c]); h->eps_node[c] = nullptr; }
     if (h->mu_node[c]) { cudaFree(h->mu_node[c]); h->mu_node[c] = nullptr; }
+    if (h->sig_node[c]) { cudaFree(h->sig_node[c]); h->sig_node[c] = nullptr; }
   }
   h->mu_var = !m_uniform;
   h->mu_r = h->mu_var ? 1.0 : m0;
+  h->lossy = any_loss;
+  const bool sig_var = any_loss && !s_uniform;
+  h->sigma_u = any_loss && s_uniform ? s0 : 0.0;
   // tune[1] bit 1 keeps per-node coefficients even for a uniform eps
-  h->per_node = !e_uniform || h->mu_var || (h->desc.tune[1] & 2) != 0;
+  h->per_node = !e_uniform || h->mu_var || sig_var || (h->desc.tune[1] & 2) != 0;
   h->eps_r = h->per_node ? 1.0 : e0;
   h->shape_tuned = false;
   int rc = FDTD_OK;
+  auto release_host = [&]() {
+    for (int c = 0; c < 3; ++c) {
+      std::vector<double>().swap(h->eps_host[c]);
+      std::vector<double>().swap(h->mu_host[c]);
+      std::vector<double>().swap(h->sig_host[c]);
+    }
+  };
   if (h->per_node) {
     std::vector<double> ones;
     if (!eps) ones.assign(nc, 1.0);
@@ -1873,13 +2029,19 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
                            cudaMemcpyHostToDevice, h->stream));
       }
     }
+    if (sig_var) {
+      // sigma at an E sample: the mean of the cells sharing its edge, as eps
+      for (int c = 0; c < 3; ++c) {
+        edge_eps(h, sigma, c, h->sig_host[c]);
+        CK(dev_malloc((void**)&h->sig_node[c], sizeof(double) * h->sig_host[c].size()));
+        CK(cudaMemcpyAsync(h->sig_node[c], h->sig_host[c].data(), sizeof(double) * h->sig_host[c].size(),
+                           cudaMemcpyHostToDevice, h->stream));
+      }
+    }
     CK(cudaStreamSynchronize(h->stream));
   }
   rc = build_all_coefs(h);
-  for (int c = 0; c < 3; ++c) {
-    std::vector<double>().swap(h->eps_host[c]);
-    std::vector<double>().swap(h->mu_host[c]);
-  }
+  release_host();
   h->output_valid = false;
   h->inv_dirty = true;
   if (rc) return rc;
@@ -3230,7 +3392,7 @@ int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t c
   if (!h || !block || !out || nsteps < 1 || checkpoint_every < 1) return FDTD_ERR_INVALID_ARG;
   *out = nullptr;
   if (h->poisoned) return FDTD_ERR_STATE;
-  if (h->scheme != FDTD_FADI || !h->per_node || h->mu_var) return FDTD_ERR_UNSUPPORTED;
+  if (h->scheme != FDTD_FADI || !h->per_node || h->mu_var || h->lossy) return FDTD_ERR_UNSUPPORTED;
   if (!h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
   if (h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
   const int i0 = block[0], i1 = block[1], j0 = block[2], j1 = block[3], k0 = block[4], k1 = block[5];

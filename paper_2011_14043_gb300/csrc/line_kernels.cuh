@@ -1073,6 +1073,134 @@ __global__ void proc_rows_kernel(const PairParams<T> p) {
 }
 
 // ---------------------------------------------------------------------------
+// Lines along x, persistent, TMA-fed (homogeneous media, lines <= 256 cells)
+// ---------------------------------------------------------------------------
+// The one-warp-per-line kernel issues its loads only when a warp starts its
+// line, so a warp spends a memory latency waiting before each solve.  Here
+// a producer warp streams tiles of R consecutive rows (R x BN elements of E
+// and of H, one 3-D TMA box each) into an NST-stage shared-memory ring, and
+// R consumer warps each take one row of a tile: they copy their segments to
+// registers, release the stage at once (an mbarrier arrival per warp, so the
+// next tile's copy starts while they solve), then solve and store exactly as
+// proc_rows_kernel does (bit-identical results).
+struct RowTiles {
+  int BN;         // elements per row box (>= N, a multiple of 8, <= 256)
+  int tpp;        // tiles per plane: ceil(n_o / R)
+  int n_tiles;    // tpp * n_o2
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Dynamic shared memory: [NST][E, H][R][BN] + 2 NST mbarriers (full, empty).
+template <typename T, int L, int R, int NST, int MINB>
+__global__ void __launch_bounds__((R + 1) * 32, MINB)
+    proc_rows_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
+                         const PairParams<T> p, const RowTiles q) {
+  static_assert(NST >= 2 && NST <= 4, "ring depth");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int stage_elems = R * q.BN;
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(buf + 2 * NST * stage_elems);
+  uint64_t* empty = full + NST;
+  const uint32_t stage_bytes = 2u * (uint32_t)stage_elems * (uint32_t)sizeof(T);
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int st = 0; st < NST; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], R);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == R) {
+    // producer: one thread issues every copy of this block's tiles
+    if (lane != 0) return;
+    int k = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
+      const int stage = k % NST;
+      const uint32_t use = (uint32_t)(k / NST);
+      if (use > 0 && !mbar_wait_bounded(&empty[stage], (use - 1) & 1u, kWaitLimitNs)) {
+        atomicExch(p.err, 1);
+        ok = false;
+        break;
+      }
+      const int ko = p.o2_lo + tile / q.tpp;
+      const int j0 = p.o_lo + (tile % q.tpp) * R;
+      T* dE = buf + (2 * stage + 0) * stage_elems;
+      T* dH = buf + (2 * stage + 1) * stage_elems;
+      mbar_arrive_expect_tx(&full[stage], stage_bytes);
+      tma_load_3d(dE, &tmE, &full[stage], 0, j0, ko);
+      tma_load_3d(dH, &tmH, &full[stage], 0, j0, ko);
+    }
+    if (!ok) {
+      // drain: the copies already issued land before the block may exit
+      // (each wait bounded; a copy still outstanding after it is left in
+      // flight, the host reports FDTD_ERR_TIMEOUT)
+      for (int d = 1; d <= NST && k - d >= 0; ++d) {
+        const int kk = k - d;
+        mbar_wait_bounded(&full[kk % NST], (uint32_t)(kk / NST) & 1u, kWaitLimitNs);
+      }
+    }
+    return;
+  }
+
+  // consumers: warp `warp` takes row `warp` of every tile
+  int k = 0;
+  for (int tile = blockIdx.x; tile < q.n_tiles; tile += gridDim.x, ++k) {
+    const int stage = k % NST;
+    const uint32_t use = (uint32_t)(k / NST);
+    if (!mbar_wait_bounded(&full[stage], use & 1u, kWaitLimitNs)) {
+      // give up: flag it; a second bounded wait lets this stage's copy land
+      if (lane == 0) atomicExch(p.err, 1);
+      mbar_wait_bounded(&full[stage], use & 1u, kWaitLimitNs);
+      return;
+    }
+    const int kl = tile / q.tpp;
+    const int jl = (tile % q.tpp) * R + warp;       // row within the pair's range
+    const T* sE = buf + (2 * stage + 0) * stage_elems + warp * q.BN;
+    const T* sH = buf + (2 * stage + 1) * stage_elems + warp * q.BN;
+    const int j0 = lane * L;
+    T E[L], H[L], qn[L], ibn[L], ibl[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      qn[t] = T(0);
+      ibn[t] = T(0);
+      ibl[t] = T(0);
+    }
+    if (j0 + L <= q.BN) {
+      load_seg<T, L>(sE + j0, E);
+      load_seg<T, L>(sH + j0, H);
+    } else {
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        E[t] = T(0);
+        H[t] = T(0);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t >= p.N) {
+        E[t] = T(0);
+        H[t] = T(0);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[stage]);  // this warp is done with the stage
+    if (jl < p.n_o) {
+      const long long line = (long long)kl * p.n_o + jl;
+      row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Batched lines: many independent grids in one launch
 // ---------------------------------------------------------------------------
 // One launch covers the same pair of every grid of a batch.  y/z lines:

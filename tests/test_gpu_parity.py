@@ -199,6 +199,33 @@ def test_tma_path_bit_identical_to_direct_path(prec, dims):
         assert np.array_equal(c2[c], b[c]), c
 
 
+@pytest.mark.parametrize("scheme", ["fadi", "fss"])
+@pytest.mark.parametrize("dims", [(256, 40, 33), (200, 37, 29), (129, 20, 24), (256, 9, 300)])
+def test_tma_rows_bit_identical_to_direct_rows(dims, scheme):
+    """The persistent TMA-fed x-line kernel of FP32 fields in homogeneous
+    media (tune[1] bit 4; lines of 129..256 cells; every ring depth and
+    blocks-per-SM variant, bits 5-6) against the one-warp-per-line kernel:
+    the same arithmetic on the same values, bit for bit; and the oracle's
+    answer."""
+    nx, ny, nz = dims
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 6.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=nx + 2 * ny + 3 * nz)
+    steps = 4
+    ref_tma = None
+    for bits in (16, 48, 80, 112):
+        a, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, scheme, "f32", u0, steps, tune=(0, bits))
+        if ref_tma is None:
+            ref_tma = a
+        for c in G.COMPS:
+            assert np.array_equal(a[c], ref_tma[c]), (bits, c)
+    b, _, _, _ = gpu_run(nx, ny, nz, 1e-3, 1e-3, 1e-3, dt, scheme, "f32", u0, steps, tune=(0, 0))
+    for c in G.COMPS:
+        assert np.array_equal(ref_tma[c], b[c]), c
+    ref, _, _ = S.run_fundamental(S.Problem(g, dt), scheme, u0, steps)
+    check(ref_tma, ref, "f32")
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_fadi_probes_at_and_beside_the_source(prec):
     """FADI probe series (the output field w_B/2 of every step) at the source
