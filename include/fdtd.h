@@ -83,7 +83,10 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * instead of the one-warp-per-line kernel (the same results; measured
  * slower at 256^3); tune[1] bits 5-6: ring depth and blocks per SM of the
  * TMA-fed x-line kernel (0: 3 stages x 4 blocks, 1: 2 x 4, 2: 4 x 3,
- * 3: 2 x 6). */
+ * 3: 2 x 6); tune[1] bit 7 set: lines along x of FP32 fields in homogeneous
+ * media take the tabulated factors near the walls (lanes that diverge from
+ * the rest of their warp) instead of the converged factors on every lane
+ * with a rank-one (Sherman-Morrison) wall correction. */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of

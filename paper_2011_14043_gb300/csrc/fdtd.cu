@@ -56,11 +56,13 @@ struct PairGeom {
 // Coefficients of one pair for one procedure length h.
 struct PairCoef {
   double kb = 0, kd = 0;  // signed s*b/d_eta, s*d/d_eta
-  void* tab = nullptr;    // uniform media: [10][tlen] hi/lo rows (1/beta, m, c, PF, PB) in T
+  void* tab = nullptr;    // uniform media: [12][tlen] hi/lo rows (1/beta, m, c, PF, PB, kappa g) in T
   int tlen = 0;
   int L = 16;             // segment length the carry-product rows are built for
   int jc = 1 << 30;       // uniform media: first converged segment start
   double cv[6] = {0, 0, 0, 0, 0, 0};  // converged (hi, lo) of 1/beta, m, c
+  bool wall_fix = false;  // uniform media: the rank-one wall correction rows are built
+  int kg_len = 0;         // the correction is zero from this node on (a multiple of L)
   double qf[2][32] = {{0}}, qb[2][32] = {{0}};
   void* nq = nullptr;     // per-node media (field layout, T): 1/|b_j|
   void* nib = nullptr;    //   1/beta_j (hi)
@@ -454,26 +456,59 @@ int build_proc(fdtd_t* h, int slot, int op, double hh, double loss_sign = 1.0) {
       const bool f32 = h->prec == FDTD_F32;
       auto hi = [&](double x) { return f32 ? (double)(float)x : x; };
       auto lo = [&](double x) { return f32 ? (double)(float)(x - (double)(float)x) : 0.0; };
-      std::vector<double> tab((size_t)10 * tl, 0.0);
-      const std::vector<double>* rows[5] = {&ib, &m, &cc, &pf, &pb};
-      for (int r = 0; r < 5; ++r)
+      // The converged factors: the same recurrence continued until it stops
+      // changing (a fixed point, or a 2-cycle in the last bit).  Long lines
+      // reach these values in their tables; x lines use them on every lane
+      // together with the rank-one wall correction below.
+      double beta_inf = diag;
+      for (int it = 0; it < 100000; ++it) {
+        const double nb = diag - off * off * (1.0 / beta_inf);
+        if (nb == beta_inf) break;
+        beta_inf = nb;
+      }
+      const double ib_inf = 1.0 / beta_inf, mc_inf = off * ib_inf;
+      // Rank-one wall correction kappa g_j: the constant factors are the LU
+      // of T' = T + delta e_1 e_1^T with delta = beta_inf - diag; g solves
+      // T' g = e_1 with them (nodes 1..N-1) and kappa = delta/(1 - delta g_1)
+      std::vector<double> kg(tl, 0.0);
+      if (N >= 2) {
+        std::vector<double> yg((size_t)N + 1, 0.0), gg((size_t)N + 2, 0.0);
+        for (int j = 1; j <= N - 1; ++j) yg[j] = (j == 1 ? 1.0 : 0.0) - (j > 1 ? mc_inf * yg[j - 1] : 0.0);
+        for (int j = N - 1; j >= 1; --j) gg[j] = yg[j] * ib_inf - mc_inf * gg[j + 1];
+        const double delta = beta_inf - diag;
+        const double kappa = delta / (1.0 - delta * gg[1]);
+        // terms below 2^-50 of w'_1 change no result: drop them, so that the
+        // segments past the last nonzero term skip the correction
+        int last = 0;
+        for (int j = 1; j <= N - 1; ++j) {
+          kg[j] = kappa * gg[j];
+          if (std::fabs(kg[j]) < 0x1p-50) kg[j] = 0.0;
+          else last = j;
+        }
+        c.kg_len = last > 0 ? ((last + 1 + L - 1) / L) * L : 0;
+      }
+      std::vector<double> tab((size_t)fdtd::TB_ROWS * tl, 0.0);
+      const std::vector<double>* rows[6] = {&ib, &m, &cc, &pf, &pb, &kg};
+      for (int r = 0; r < 6; ++r)
         for (int j = 0; j < tl; ++j) {
           tab[(size_t)(2 * r) * tl + j] = hi((*rows[r])[j]);
           tab[(size_t)(2 * r + 1) * tl + j] = lo((*rows[r])[j]);
         }
-      // converged constants: the entries of the last full segment inside the
-      // line; jc = first segment start from which every full segment's
-      // entries (hi and lo) equal them
+      // converged constants (hi, lo) and segment carry products; jc = first
+      // segment start from which every full segment's table entries equal
+      // them
       c.jc = 1 << 30;
+      {
+        const double cvv[3] = {ib_inf, mc_inf, mc_inf};
+        for (int k = 0; k < 3; ++k) { c.cv[2 * k] = hi(cvv[k]); c.cv[2 * k + 1] = lo(cvv[k]); }
+        double qf = 1.0;
+        for (int t = 0; t < L; ++t) { qf *= -mc_inf; c.qf[0][t] = hi(qf); c.qf[1][t] = lo(qf); }
+        double qb = 1.0;
+        for (int t = L - 1; t >= 0; --t) { qb *= -mc_inf; c.qb[0][t] = hi(qb); c.qb[1][t] = lo(qb); }
+      }
+      c.wall_fix = L >= 2;
       const int last_seg = ((N) / L - 1) * L;  // start of the last segment with j0 + L <= N
       if (N >= 2 && last_seg >= 0) {
-        const int jr = last_seg + L - 1;
-        const double cvv[3] = {ib[jr], m[jr], cc[jr]};
-        for (int k = 0; k < 3; ++k) { c.cv[2 * k] = hi(cvv[k]); c.cv[2 * k + 1] = lo(cvv[k]); }
-        for (int t = 0; t < L; ++t) {
-          c.qf[0][t] = hi(pf[last_seg + t]); c.qf[1][t] = lo(pf[last_seg + t]);
-          c.qb[0][t] = hi(pb[last_seg + t]); c.qb[1][t] = lo(pb[last_seg + t]);
-        }
         auto seg_ok = [&](int j0) {
           for (int t = 0; t < L; ++t) {
             const int j = j0 + t;
@@ -666,6 +701,10 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.kd_scale = (T)(sgn * kd_mul);
   p.n_elem = h->count;
   p.tables_only = fp64_throughput_pair(h, g) ? 1 : 0;
+  // FP32 fields in homogeneous media: converged factors on every lane plus
+  // the rank-one wall correction (tune[1] bit 7: the table lanes instead)
+  p.wall_fix = (c.wall_fix && sizeof(T) == 4 && (h->desc.tune[1] & 128) == 0) ? 1 : 0;
+  p.kg_len = c.kg_len;
   return p;
 }
 
@@ -688,6 +727,8 @@ void launch_rows_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>
   const unsigned blocks = (unsigned)((nl + wpb - 1) / wpb);
   if (per_node)
     fdtd::proc_rows_kernel<T, L, true><<<blocks, wpb * 32, 0, h->stream>>>(p);
+  else if (sizeof(T) == 4 && L >= 2 && p.wall_fix)
+    fdtd::proc_rows_kernel<T, L, false, (sizeof(T) == 4 && L >= 2)><<<blocks, wpb * 32, 0, h->stream>>>(p);
   else
     fdtd::proc_rows_kernel<T, L, false><<<blocks, wpb * 32, 0, h->stream>>>(p);
 }
@@ -900,8 +941,11 @@ template <int NST, int MINB>
 cudaError_t ensure_rows_tma_attr_one() {
   static bool set = false;
   if (set) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB>,
+  cudaError_t e = cudaFuncSetAttribute(fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess) set = true;
   return e;
 }
@@ -920,8 +964,12 @@ void launch_rows_tma_v(fdtd_t* h, const CUtensorMap* tE, const CUtensorMap* tH, 
                        const fdtd::RowTiles& q) {
   const size_t smem = 2 * (size_t)NST * kRowsR * q.BN * sizeof(float) + 2 * (size_t)NST * sizeof(uint64_t);
   const int grid = std::min(q.n_tiles, MINB * h->num_sms);
-  fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB><<<grid, (kRowsR + 1) * 32, smem, h->stream>>>(*tE, *tH,
-                                                                                                       p, q);
+  if (p.wall_fix)
+    fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB, true><<<grid, (kRowsR + 1) * 32, smem, h->stream>>>(
+        *tE, *tH, p, q);
+  else
+    fdtd::proc_rows_tma_kernel<float, 8, kRowsR, NST, MINB, false><<<grid, (kRowsR + 1) * 32, smem, h->stream>>>(
+        *tE, *tH, p, q);
 }
 
 int launch_rows_tma(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<float>& p) {

@@ -110,6 +110,11 @@ struct PairParams {
   long long n_elem;      // elements of every field-layout array (bounds-checked builds)
   int tables_only;       // uniform media: every lane reads the tables (no converged-
                          // constant branch); set for FP64 fields on large pairs
+  int wall_fix;          // uniform media: solve with the converged factors on every
+                         // lane plus the rank-one wall correction (table rows
+                         // TB_KGH/TB_KGL) instead of table lanes near the walls
+  int kg_len;            // the wall correction is zero from this node on (a multiple of
+                         // the segment length)
 };
 
 // Bounds of one line for the checked build: a strided line touches its
@@ -153,7 +158,9 @@ __device__ __forceinline__ T fma2(HiLo<T> a, T x, T b) {
 }
 
 // Table rows of a homogeneous medium, each [tlen] long.
-enum { TB_IBH = 0, TB_IBL, TB_MH, TB_ML, TB_CH, TB_CL, TB_PFH, TB_PFL, TB_PBH, TB_PBL, TB_ROWS };
+// TB_KGH/TB_KGL: the rank-one wall correction kappa g_j of the constant-factor
+// x-line solve (row_solve_store_wall), zero at node 0 and from node N on.
+enum { TB_IBH = 0, TB_IBL, TB_MH, TB_ML, TB_CH, TB_CL, TB_PFH, TB_PFL, TB_PBH, TB_PBL, TB_KGH, TB_KGL, TB_ROWS };
 
 template <typename T, int MODE>
 __device__ __forceinline__ HiLo<T> tab2(const PairParams<T>& p, int row, int j, int t, const T* cv_hi,
@@ -406,6 +413,83 @@ __device__ __forceinline__ void strided_solve(const PairParams<T>& p, int j0, in
   }
 }
 
+// The segment solve of a block of LANES lines of a homogeneous medium with
+// the converged factors on every segment and the rank-one wall correction
+// (the strided counterpart of row_solve_store_wall): no segment reads the
+// factor tables, so every warp runs the same arithmetic between the chain
+// barriers.  Node 1's value w'_1 of every line reaches the segments that need
+// it without another barrier: segment 0 publishes its local backward value
+// there in a slot of the forward chain buffers that is free by then, and
+// every thread adds segment 0's incoming backward carry after the chain.  win
+// comes back corrected too (the next segment's first node).
+template <typename T, int LANES, int L>
+__device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j0, int s, int P, int lane, T* sh,
+                                                   const T (&E)[L], const T (&H)[L], T hm1, T (&y)[L], T& win,
+                                                   int tid = -1, int nthr = -1) {
+  if (tid < 0) {
+    tid = (int)threadIdx.x;
+    nthr = (int)blockDim.x;
+  }
+  const int N = p.N;
+  const HiLo<T> m = {p.cv[2], p.cv[3]};
+  const HiLo<T> ib = {p.cv[0], p.cv[1]};
+  const HiLo<T> c = {p.cv[4], p.cv[5]};
+  T hprev = hm1;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const int j = j0 + t;
+    T r = fma(p.kb, H[t] - hprev, E[t]);
+    hprev = H[t];
+    r = (j == 0 || j >= N) ? T(0) : r;
+    y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
+  }
+  const int PW = pow2_at_least(P);
+  const T yin = block_chain_forward<T, LANES>(sh, P, PW, s, lane, y[L - 1], HiLo<T>{p.qf[0][L - 1], p.qf[1][L - 1]},
+                                              tid, nthr);
+#pragma unroll
+  for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{p.qf[0][t], p.qf[1][t]}, yin, y[t]);
+  const bool full = j0 + L <= N;
+  T wn = T(0);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    const bool in = j0 + t < N;
+    const T ch = in ? c.hi : T(0), cl = in ? c.lo : T(0);
+    const T ih = in ? ib.hi : T(0), il = in ? ib.lo : T(0);
+    T u;
+    if constexpr (use_hilo<T>()) u = fma(-ch, wn, fma(-cl, wn, y[t] * il));
+    else u = -ch * wn;
+    y[t] = fma(y[t], ih, u);
+    wn = y[t];
+  }
+  // segment 0 publishes node 1's local value in the forward chain's slot of
+  // segment 0's hi products (read there only inside the forward scan)
+  const int PS = chain_stride(P);
+  T* ys1 = sh + PS * LANES;  // [lane * PS]
+  if (s == 0) ys1[lane * PS] = (L >= 2) ? y[1 % L] : T(0);
+  const HiLo<T> pb0 = full ? HiLo<T>{p.qb[0][0], p.qb[1][0]} : HiLo<T>{T(0), T(0)};
+  win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb0, tid, nthr);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const HiLo<T> pbt = full ? HiLo<T>{p.qb[0][t], p.qb[1][t]} : HiLo<T>{T(0), T(0)};
+    y[t] = fma2(pbt, win, y[t]);
+  }
+  if (j0 == 0) y[0] = T(0);  // node 0: the wall
+  if (j0 < p.kg_len) {
+    // w'_1 = segment 0's local value + its carry-product times its incoming
+    // backward carry (the chain result at segment 1)
+    const T* sab = sh + 3 * PS * LANES;
+    const T win0 = (P > 1) ? sab[lane * PS + 1] : T(0);
+    const bool full0 = L <= N;
+    const HiLo<T> pb1 = full0 ? HiLo<T>{p.qb[0][1 % L], p.qb[1][1 % L]} : HiLo<T>{T(0), T(0)};
+    const T w1 = fma2(pb1, win0, ys1[lane * PS]);
+    const T* kgh = p.tab + TB_KGH * p.tlen + j0;
+    const T* kgl = p.tab + TB_KGL * p.tlen + j0;
+#pragma unroll
+    for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{kgh[t], kgl[t]}, w1, y[t]);
+    win = fma2(HiLo<T>{kgh[L], kgl[L]}, w1, win);
+  }
+}
+
 // H update, subtraction and store of one strided segment.
 template <typename T, int L>
 __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long base, int j0, const T (&E)[L],
@@ -486,7 +570,12 @@ __global__ void proc_strided_kernel(const PairParams<T> p) {
     }
   }
   T win;
-  strided_solve<T, LANES, L, PER_NODE>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  if constexpr (!PER_NODE) {
+    if (p.wall_fix) strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win);
+    else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  } else {
+    strided_solve<T, LANES, L, true>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win);
+  }
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
   if constexpr (PER_NODE) {
     if (active && p.d_out) {
@@ -689,7 +778,10 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
       }
     }
     T win;
-    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
+    if (p.wall_fix)
+      strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win);
+    else
+      strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
                                       win);
     if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
   }
@@ -826,7 +918,10 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
       }
     }
     T win;
-    strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
+    if (p.wall_fix)
+      strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win);
+    else
+      strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
                                       win);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
@@ -1023,6 +1118,112 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
   }
 }
 
+// One x line of a homogeneous medium without divergent lanes.  The line
+// matrix T (nodes 1..N-1) has LU factors that vary only near node 1 and
+// converge to constants; the constant factors L' U' are the exact LU of
+// T' = T + delta e_1 e_1^T (delta = beta_inf - T_11, a change of the first
+// diagonal entry only).  So every lane solves T' w' = r with the converged
+// constants (kernel parameters, no table loads), and the Sherman-Morrison
+// formula restores T^{-1} r = w' + kappa g w'_1 with g = T'^{-1} e_1 and
+// kappa = delta / (1 - delta g_1): one broadcast of w'_1 and one hi + lo FMA
+// per node with kappa g_j from the table (it decays geometrically from the
+// wall; zero at node 0 and from node N on).  Node 0 and nodes >= N carry no
+// unknown: their right-hand side is zero, their factors 1/beta and c zero,
+// and node 0 is set to zero after the solve.  The result equals the
+// table-factor solve up to rounding (not bit for bit).
+template <typename T, int L>
+__device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, long long line, T (&E)[L],
+                                                     T (&H)[L]) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int jo = p.o_lo + (int)(line % p.n_o);
+  const int ko = p.o2_lo + (int)(line / p.n_o);
+  const long long base = (long long)ko * p.os2 + (long long)jo * p.os;
+  const bool ok = row_ok<T, L>(p, base);
+  const int j0 = lane * L;
+  const int N = p.N;
+  // the wall correction of this lane's nodes (vector loads; cache-resident)
+  T kgh[L], kgl[L];
+  load_seg<T, L>(p.tab + TB_KGH * p.tlen + j0, kgh);
+  load_seg<T, L>(p.tab + TB_KGL * p.tlen + j0, kgl);
+  T y[L];
+  T hm1 = __shfl_up_sync(FULL, H[L - 1], 1);
+  if (lane == 0) hm1 = T(0);
+  const HiLo<T> m = {p.cv[2], p.cv[3]};
+  const HiLo<T> ib = {p.cv[0], p.cv[1]};
+  const HiLo<T> c = {p.cv[4], p.cv[5]};
+  // forward sweep with the constant multiplier
+  T hprev = hm1;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const int j = j0 + t;
+    T r = fma(p.kb, H[t] - hprev, E[t]);
+    hprev = H[t];
+    r = (j == 0 || j >= N) ? T(0) : r;
+    y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
+  }
+  const T yin = warp_chain_forward<T>(y[L - 1], HiLo<T>{p.qf[0][L - 1], p.qf[1][L - 1]});
+#pragma unroll
+  for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{p.qf[0][t], p.qf[1][t]}, yin, y[t]);
+  // backward sweep; nodes >= N hold w = 0 and do not couple
+  const bool full = j0 + L <= N;
+  T wn = T(0);
+#pragma unroll
+  for (int t = L - 1; t >= 0; --t) {
+    const bool in = j0 + t < N;
+    const T ch = in ? c.hi : T(0), cl = in ? c.lo : T(0);
+    const T ih = in ? ib.hi : T(0), il = in ? ib.lo : T(0);
+    T u;
+    if constexpr (use_hilo<T>()) u = fma(-ch, wn, fma(-cl, wn, y[t] * il));
+    else u = -ch * wn;
+    y[t] = fma(y[t], ih, u);
+    wn = y[t];
+  }
+  const HiLo<T> pb0 = full ? HiLo<T>{p.qb[0][0], p.qb[1][0]} : HiLo<T>{T(0), T(0)};
+  const T win = warp_chain_backward<T>(y[0], pb0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const HiLo<T> pbt = full ? HiLo<T>{p.qb[0][t], p.qb[1][t]} : HiLo<T>{T(0), T(0)};
+    y[t] = fma2(pbt, win, y[t]);
+  }
+  if (lane == 0) y[0] = T(0);  // node 0: the wall
+  // rank-one correction w = w' + kappa g w'_1 (w'_1: node 1, from its lane)
+  const T w1 = (L >= 2) ? __shfl_sync(FULL, y[1 % L], 0) : __shfl_sync(FULL, y[0], 1);
+#pragma unroll
+  for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{kgh[t], kgl[t]}, w1, y[t]);
+  // H update needs w at the next lane's first node (after the correction)
+  T wnl = __shfl_down_sync(FULL, y[0], 1);
+  if (lane == 31) wnl = T(0);
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const T wnext = (t + 1 < L) ? y[t + 1] : wnl;
+    H[t] = fma(p.kd, wnext - y[t], H[t]);
+    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
+  if (!ok) return;
+  if (j0 + L <= N) {
+    store_seg<T, L>(p.e_out + base + j0, E);
+    store_seg<T, L>(p.h_out + base + j0, H);
+  } else if (j0 < N) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t < N) {
+        p.e_out[base + j0 + t] = E[t];
+        p.h_out[base + j0 + t] = H[t];
+      }
+    }
+  }
+}
+
+// Homogeneous media: the rank-one wall correction path when the host built
+// it (p.wall_fix), else the table lanes.
+template <typename T, int L>
+__device__ __forceinline__ void row_solve_store_uniform(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
+                                                        const T (&qn)[L], const T (&ibn)[L], const T (&ibl)[L]) {
+  if (p.wall_fix) row_solve_store_wall<T, L>(p, line, E, H);
+  else row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+}
+
 // Load this lane's segment of x line `line` (zeros past the line end).
 // Segments never run past the padded row (the row pitch is >= 32*L).
 template <typename T, int L, bool PER_NODE>
@@ -1062,14 +1263,18 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
   }
 }
 
-// One warp per x line.
-template <typename T, int L, bool PER_NODE>
+// One warp per x line.  WALL: homogeneous media with the rank-one wall
+// correction (p.wall_fix), a separate instantiation so that each path gets
+// its own register allocation.
+template <typename T, int L, bool PER_NODE, bool WALL = false>
 __global__ void proc_rows_kernel(const PairParams<T> p) {
   const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
   T E[L], H[L], qn[L], ibn[L], ibl[L];
   row_load<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
-  row_solve_store<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
+  if constexpr (PER_NODE) row_solve_store<T, L, true>(p, line, E, H, qn, ibn, ibl);
+  else if constexpr (WALL) row_solve_store_wall<T, L>(p, line, E, H);
+  else row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1094,7 +1299,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Dynamic shared memory: [NST][E, H][R][BN] + 2 NST mbarriers (full, empty).
-template <typename T, int L, int R, int NST, int MINB>
+template <typename T, int L, int R, int NST, int MINB, bool WALL>
 __global__ void __launch_bounds__((R + 1) * 32, MINB)
     proc_rows_tma_kernel(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmH,
                          const PairParams<T> p, const RowTiles q) {
@@ -1195,7 +1400,8 @@ __global__ void __launch_bounds__((R + 1) * 32, MINB)
     if (lane == 0) mbar_arrive(&empty[stage]);  // this warp is done with the stage
     if (jl < p.n_o) {
       const long long line = (long long)kl * p.n_o + jl;
-      row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+      if constexpr (WALL) row_solve_store_wall<T, L>(p, line, E, H);
+      else row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
     }
   }
 }
@@ -1291,6 +1497,7 @@ __global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ para
   }
   T win;
   if (pn) strided_solve<T, LANES, L, true>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
+  else if (p.wall_fix) strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win, tid, tpt);
   else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
 }
@@ -1317,7 +1524,7 @@ __global__ void proc_rows_batch_kernel(const PairParams<T>* __restrict__ params,
     row_solve_store<T, L, true>(p, line, E, H, qn, ibn, ibl);
   } else {
     row_load<T, L, false>(p, line, E, H, qn, ibn, ibl);
-    row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
+    row_solve_store_uniform<T, L>(p, line, E, H, qn, ibn, ibl);
   }
 }
 
