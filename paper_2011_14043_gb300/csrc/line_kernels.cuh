@@ -437,10 +437,9 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
   T hprev = hm1;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const int j = j0 + t;
     T r = fma(p.kb, H[t] - hprev, E[t]);
     hprev = H[t];
-    r = (j == 0 || j >= N) ? T(0) : r;
+    if (t == 0) r = (j0 == 0) ? T(0) : r;  // node 0 (past the end: cut off below)
     y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
   }
   const int PW = pow2_at_least(P);
@@ -450,16 +449,27 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
   for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{p.qf[0][t], p.qf[1][t]}, yin, y[t]);
   const bool full = j0 + L <= N;
   T wn = T(0);
+  if (full) {
 #pragma unroll
-  for (int t = L - 1; t >= 0; --t) {
-    const bool in = j0 + t < N;
-    const T ch = in ? c.hi : T(0), cl = in ? c.lo : T(0);
-    const T ih = in ? ib.hi : T(0), il = in ? ib.lo : T(0);
-    T u;
-    if constexpr (use_hilo<T>()) u = fma(-ch, wn, fma(-cl, wn, y[t] * il));
-    else u = -ch * wn;
-    y[t] = fma(y[t], ih, u);
-    wn = y[t];
+    for (int t = L - 1; t >= 0; --t) {
+      T u;
+      if constexpr (use_hilo<T>()) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
+      else u = -c.hi * wn;
+      y[t] = fma(y[t], ib.hi, u);
+      wn = y[t];
+    }
+  } else {
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      const bool in = j0 + t < N;
+      const T ch = in ? c.hi : T(0), cl = in ? c.lo : T(0);
+      const T ih = in ? ib.hi : T(0), il = in ? ib.lo : T(0);
+      T u;
+      if constexpr (use_hilo<T>()) u = fma(-ch, wn, fma(-cl, wn, y[t] * il));
+      else u = -ch * wn;
+      y[t] = fma(y[t], ih, u);
+      wn = y[t];
+    }
   }
   // segment 0 publishes node 1's local value in the forward chain's slot of
   // segment 0's hi products (read there only inside the forward scan)
@@ -468,10 +478,9 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
   if (s == 0) ys1[lane * PS] = (L >= 2) ? y[1 % L] : T(0);
   const HiLo<T> pb0 = full ? HiLo<T>{p.qb[0][0], p.qb[1][0]} : HiLo<T>{T(0), T(0)};
   win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb0, tid, nthr);
+  if (full) {
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const HiLo<T> pbt = full ? HiLo<T>{p.qb[0][t], p.qb[1][t]} : HiLo<T>{T(0), T(0)};
-    y[t] = fma2(pbt, win, y[t]);
+    for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{p.qb[0][t], p.qb[1][t]}, win, y[t]);
   }
   if (j0 == 0) y[0] = T(0);  // node 0: the wall
   if (j0 < p.kg_len) {
@@ -1165,7 +1174,9 @@ __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, lon
   const T yin = warp_chain_forward<T>(y[L - 1], HiLo<T>{p.qf[0][L - 1], p.qf[1][L - 1]});
 #pragma unroll
   for (int t = 0; t < L; ++t) y[t] = fma2(HiLo<T>{p.qf[0][t], p.qf[1][t]}, yin, y[t]);
-  // backward sweep; nodes >= N hold w = 0 and do not couple
+  // backward sweep; nodes >= N hold w = 0 and do not couple (masks by
+  // selects: one code path keeps the kernel at 48 registers, where two
+  // paths needed 64 and ran slower)
   const bool full = j0 + L <= N;
   T wn = T(0);
 #pragma unroll
