@@ -98,6 +98,81 @@ def assemble(grid: Grid, mat: dict):
     return A, B
 
 
+# Fourth-order assembly (Grid.order == 4): the terms of Eqs. 33-34 written
+# out again, (E row, H column, line axis, sign, operator), each first
+# difference being the fourth-order staggered one with PEC images.
+_TERMS4 = (
+    ("ex", "hz", "y", +1, "A"), ("ey", "hx", "z", +1, "A"), ("ez", "hy", "x", +1, "A"),
+    ("ex", "hy", "z", -1, "B"), ("ey", "hz", "x", -1, "B"), ("ez", "hx", "y", -1, "B"),
+)
+
+
+def assemble4(grid: Grid, mat: dict):
+    """Dense A and B with fourth-order staggered differences, entry by entry.
+    E row at node j of its line: (9/8)(H_j - H_{j-1}) - (1/24)(H_{j+1} - H_{j-2});
+    a face past a wall is its mirror image (H even).  H row at face f:
+    (9/8)(E_{f+1} - E_f) - (1/24)(E_{f+2} - E_{f-1}); a node past a wall is
+    minus its mirror image (tangential E odd)."""
+    off, n = layout(grid)
+    A = np.zeros((n, n))
+    B = np.zeros((n, n))
+    c1, c2 = 9.0 / 8.0, -1.0 / 24.0
+    dims = {"x": grid.nx, "y": grid.ny, "z": grid.nz}
+    sp = {"x": grid.dx, "y": grid.dy, "z": grid.dz}
+    pos = {"x": 2, "y": 1, "z": 0}
+
+    def idx(c, kji):
+        sk, sj, si = grid.shape(c)
+        k, j, i = kji
+        return off[c] + (k * sj + j) * si + i
+
+    def samples(c):
+        sk, sj, si = grid.shape(c)
+        for k in range(sk):
+            for j in range(sj):
+                for i in range(si):
+                    yield [k, j, i]
+
+    for ec, hc, ax, sg, op in _TERMS4:
+        O = A if op == "A" else B
+        N = dims[ax]
+        a = pos[ax]
+        d = sp[ax]
+        emask = grid.e_interior_mask(ec)
+        for kji in samples(ec):
+            if emask[tuple(kji)] == 0:
+                continue
+            j = kji[a]
+            r = idx(ec, kji)
+            e = mat[ec][tuple(kji)]
+            for fo, wgt in ((0, c1), (-1, -c1), (1, c2), (-2, -c2)):
+                f = j + fo
+                if f < 0:
+                    f = -1 - f
+                if f > N - 1:
+                    f = 2 * N - 1 - f
+                col = list(kji)
+                col[a] = f
+                O[r, idx(hc, col)] += sg * wgt / (e * d)
+        for kji in samples(hc):
+            f = kji[a]
+            r = idx(hc, kji)
+            m = mat[hc][tuple(kji)]
+            for no, wgt in ((1, c1), (0, -c1), (2, c2), (-1, -c2)):
+                node = f + no
+                s_img = 1.0
+                if node < 0:
+                    node, s_img = -node, -1.0
+                if node > N:
+                    node, s_img = 2 * N - node, -1.0
+                col = list(kji)
+                col[a] = node
+                if emask[tuple(col)] == 0:
+                    continue         # a wall sample: fixed at zero
+                O[r, idx(ec, col)] += sg * s_img * wgt / (m * d)
+    return A, B
+
+
 def cn(Oi, Oe, tau, x, f=None):
     """(I - tau Oi) x' = (I + tau Oe) x (+ tau f), dense."""
     I = np.eye(Oi.shape[0])

@@ -13,6 +13,18 @@ component, which has one line pair in A and one in B, loses half in each
 procedure.  In a procedure of length h the implicit diagonal becomes
 1/2 + b sigma / 4 (b = h / (2 eps)).
 
+Higher-order differences (the paper names "higher order, parameter
+optimized, compact" difference operators as possible variants without
+formulae, end of Sec. III-A): with order = 4 every first difference of A and
+B is the fourth-order staggered central difference
+    (9/8 (u_{+1/2} - u_{-1/2}) - 1/24 (u_{+3/2} - u_{-3/2})) / d,
+and the points past a PEC wall are images: tangential E is odd about the
+wall (E_{-j} = -E_j), the H samples half a cell off it are even
+(H_{-1/2-f} = H_{1/2+f}).  The two differences stay exact negative
+transposes of each other, so A and B stay skew in the energy product and
+every scheme keeps its invariant; eliminating H gives line systems of
+bandwidth 3, which the oracle solves densely line by line.
+
 Readings of what the paper leaves open (each is a documented choice):
 * differences are the standard Yee second-order central differences between
   staggered samples (sample layout in ``workloads``);
@@ -67,6 +79,7 @@ class Grid:
     dx: float
     dy: float
     dz: float
+    order: int = 2          # 2: Yee differences; 4: fourth-order staggered differences
 
     @property
     def spacing(self):
@@ -189,6 +202,107 @@ def diff_e_to_h(e: np.ndarray, axis: int, spacing: float) -> np.ndarray:
     return (e[tuple(hi)] - e[tuple(lo)]) / spacing
 
 
+C4 = (9.0 / 8.0, -1.0 / 24.0)   # fourth-order staggered difference weights
+
+
+def _pad_images(x: np.ndarray, axis: int, odd: bool) -> np.ndarray:
+    """x with one image sample added before and after along ``axis``: for E
+    (odd about the walls, which are its first and last samples) x[-1] = -x[1]
+    and x[n+1] = -x[n-1]; for H (even, half a cell off the walls) x[-1] = x[0]
+    and x[n] = x[n-1]."""
+    n = x.shape[axis]
+    idx_lo = 1 if odd else 0
+    idx_hi = n - 2 if odd else n - 1
+    lo = np.take(x, [idx_lo], axis=axis)
+    hi = np.take(x, [idx_hi], axis=axis)
+    if odd:
+        lo, hi = -lo, -hi
+    return np.concatenate([lo, x, hi], axis=axis)
+
+
+def diff_e_to_h4(e: np.ndarray, axis: int, spacing: float) -> np.ndarray:
+    """Fourth-order d/d(eta) of an E component at the H samples (faces
+    f = 0..n-1 between nodes f and f+1), PEC images past the walls."""
+    ep = _pad_images(e, axis, odd=True)        # ep[j + 1] = E_j
+    n = e.shape[axis] - 1
+
+    def sl(a, b):
+        s = [slice(None)] * e.ndim
+        s[axis] = slice(a, b)
+        return tuple(s)
+    c1, c2 = C4
+    return (c1 * (ep[sl(2, n + 2)] - ep[sl(1, n + 1)]) + c2 * (ep[sl(3, n + 3)] - ep[sl(0, n)])) / spacing
+
+
+def diff_h_to_e4(h: np.ndarray, axis: int, spacing: float, e_shape) -> np.ndarray:
+    """Fourth-order d/d(eta) of an H component at the E nodes j = 1..n-1
+    (zero at the two wall nodes), PEC images past the walls."""
+    hp = _pad_images(h, axis, odd=False)       # hp[f + 1] = H_f
+    n = e_shape[axis] - 1
+    out = np.zeros(e_shape)
+    if n < 2:
+        return out
+
+    def sl(a, b):
+        s = [slice(None)] * h.ndim
+        s[axis] = slice(a, b)
+        return tuple(s)
+    c1, c2 = C4
+    tgt = [slice(None)] * len(e_shape)
+    tgt[axis] = slice(1, n)
+    # node j (1..n-1): faces j, j-1, j+1, j-2 at hp[j+1], hp[j], hp[j+2], hp[j-1]
+    out[tuple(tgt)] = (c1 * (hp[sl(2, n + 1)] - hp[sl(1, n)]) + c2 * (hp[sl(3, n + 2)] - hp[sl(0, n - 1)])) / spacing
+    return out
+
+
+def d_e_to_h(grid: Grid, e, axis, spacing):
+    return diff_e_to_h4(e, axis, spacing) if grid.order == 4 else diff_e_to_h(e, axis, spacing)
+
+
+def d_h_to_e(grid: Grid, h, axis, spacing, e_shape):
+    return diff_h_to_e4(h, axis, spacing, e_shape) if grid.order == 4 else diff_h_to_e(h, axis, spacing, e_shape)
+
+
+def line_matrices4(n: int, spacing: float):
+    """The fourth-order differences of one line as matrices over its
+    interior E nodes 1..n-1: DEH (faces x interior nodes) and DHE (interior
+    nodes x faces), built by applying the difference functions to unit
+    vectors (images included)."""
+    m = max(n - 1, 0)
+    DEH = np.zeros((n, m))
+    DHE = np.zeros((m, n))
+    for k in range(m):
+        e = np.zeros(n + 1)
+        e[k + 1] = 1.0
+        DEH[:, k] = diff_e_to_h4(e, 0, spacing)
+    for f in range(n):
+        h = np.zeros(n)
+        h[f] = 1.0
+        DHE[:, f] = diff_h_to_e4(h, 0, spacing, (n + 1,))[1:n]
+    return DEH, DHE
+
+
+def solve_lines4(diag, gE: np.ndarray, gH: np.ndarray, rhs_e: np.ndarray, axis: int, spacing: float) -> np.ndarray:
+    """Solve diag*w - gE * DHE (gH * DEH w) = rhs along ``axis`` (fourth-order
+    differences) for the interior nodes, one dense system per line; w = 0 on
+    the two wall nodes.  diag is a number or an array of the E shape."""
+    r = np.moveaxis(rhs_e, axis, -1)
+    n = r.shape[-1] - 1
+    w = np.zeros_like(r)
+    if n < 2:
+        return np.moveaxis(w, -1, axis)
+    DEH, DHE = line_matrices4(n, spacing)
+    ge = np.moveaxis(gE, axis, -1)[..., 1:-1]
+    gh = np.moveaxis(gH, axis, -1)
+    dg = np.moveaxis(diag, axis, -1)[..., 1:-1] if np.ndim(diag) else np.full(ge.shape, float(diag))
+    K = np.einsum("jf,...f,fk->...jk", DHE, gh, DEH)
+    M = -ge[..., :, None] * K
+    idx = np.arange(n - 1)
+    M[..., idx, idx] += dg
+    w[..., 1:-1] = np.linalg.solve(M, r[..., 1:-1, None])[..., 0]
+    return np.moveaxis(w, -1, axis)
+
+
 def apply_op(grid: Grid, mat: dict, op: str, u: dict) -> dict:
     """O u for O = A (Eq. 33) or B (Eq. 34), PEC walls applied; in a lossy
     medium each operator also carries -(1/2)(sigma/eps) E on its E rows."""
@@ -196,8 +310,8 @@ def apply_op(grid: Grid, mat: dict, op: str, u: dict) -> dict:
     for ec, hc, ax, sgn in PAIRS[op]:
         a = AXIS[ax]
         sp = grid.spacing[ax]
-        out[ec] += sgn * diff_h_to_e(u[hc], a, sp, grid.shape(ec)) / mat[ec]
-        out[hc] += sgn * diff_e_to_h(u[ec], a, sp) / mat[hc]
+        out[ec] += sgn * d_h_to_e(grid, u[hc], a, sp, grid.shape(ec)) / mat[ec]
+        out[hc] += sgn * d_e_to_h(grid, u[ec], a, sp) / mat[hc]
         if "sigma" in mat:
             out[ec] -= 0.5 * mat["sigma"][ec] / mat[ec] * u[ec]
     for ec in E_COMPS:
@@ -261,10 +375,13 @@ def solve_implicit(grid: Grid, mat: dict, op: str, tau: float, rhs: dict) -> dic
         mask = grid.e_interior_mask(ec)
         gE = tau / mat[ec]
         gH = tau / mat[hc]
-        rE = (rhs[ec] + sgn * gE * diff_h_to_e(rhs[hc], a, sp, grid.shape(ec))) * mask
-        lo, ce, up = line_operator_coeffs(gE, gH, a, sp)
+        rE = (rhs[ec] + sgn * gE * d_h_to_e(grid, rhs[hc], a, sp, grid.shape(ec))) * mask
         alpha = 1.0 + 0.5 * tau * mat["sigma"][ec] / mat[ec] if "sigma" in mat else 1.0
-        w = solve_lines(alpha, lo, ce, up, rE, a) * mask
+        if grid.order == 4:
+            w = solve_lines4(alpha, gE, gH, rE, a, sp) * mask
+        else:
+            lo, ce, up = line_operator_coeffs(gE, gH, a, sp)
+            w = solve_lines(alpha, lo, ce, up, rE, a) * mask
         out[ec] = w
-        out[hc] = rhs[hc] + sgn * gH * diff_e_to_h(w, a, sp)
+        out[hc] = rhs[hc] + sgn * gH * d_e_to_h(grid, w, a, sp)
     return out

@@ -32,11 +32,18 @@ def energy(grid: Grid, mat: dict, u: dict) -> float:
 
 
 def adi_omega(dt: float, kx: float, ky: float, kz: float, dx: float, dy: float, dz: float,
-              c: float = C0) -> float:
-    """Angular frequency of the ADI/LOD1 amplification for wave vector k."""
-    P = (c * dt / dx) ** 2 * math.sin(kx * dx / 2) ** 2
-    Q = (c * dt / dy) ** 2 * math.sin(ky * dy / 2) ** 2
-    R = (c * dt / dz) ** 2 * math.sin(kz * dz / 2) ** 2
+              c: float = C0, order: int = 2) -> float:
+    """Angular frequency of the ADI/LOD1 amplification for wave vector k.
+    P = (c dt kappa_x / 2)^2 with kappa the symbol of the staggered first
+    difference: (2/d) sin(k d/2) (Yee), or (2/d)(9/8 sin(k d/2) - 1/24 sin(3 k d/2))
+    for the fourth-order difference."""
+    def kap(k, d):
+        if order == 4:
+            return (2.0 / d) * (9.0 / 8.0 * math.sin(k * d / 2) - 1.0 / 24.0 * math.sin(1.5 * k * d))
+        return (2.0 / d) * math.sin(k * d / 2)
+    P = (c * dt * kap(kx, dx) / 2) ** 2
+    Q = (c * dt * kap(ky, dy) / 2) ** 2
+    R = (c * dt * kap(kz, dz) / 2) ** 2
     s2 = (P + Q + R + P * Q + Q * R + R * P) / ((1 + P) * (1 + Q) * (1 + R))
     return 2.0 * math.asin(math.sqrt(s2)) / dt
 

@@ -34,14 +34,24 @@ OFFSET = {"ex": (0.5, 0, 0), "ey": (0, 0.5, 0), "ez": (0, 0, 0.5),
           "hx": (0, 0.5, 0.5), "hy": (0.5, 0, 0.5), "hz": (0.5, 0.5, 0)}
 
 
+def kappa(order: int, theta: float, d: float) -> float:
+    """Symbol of the staggered first difference on sin/cos samples, theta =
+    k d: (2/d) sin(theta/2) for the Yee difference; (2/d)(9/8 sin(theta/2) -
+    1/24 sin(3 theta/2)) for the fourth-order one (with PEC images the cavity
+    modes stay exact eigenfunctions)."""
+    if order == 4:
+        return (2.0 / d) * (9.0 / 8.0 * math.sin(theta / 2.0) - 1.0 / 24.0 * math.sin(1.5 * theta))
+    return (2.0 / d) * math.sin(theta / 2.0)
+
+
 def mode_operators(grid: Grid, m: int, n: int, p: int, eps: float = EPS0, mu: float = MU0,
                    sigma: float = 0.0):
     """A and B (Eqs. 33-34) restricted to the mode's 6-dimensional space; a
     homogeneous conductivity sigma puts -sigma/(2 eps) on the E diagonal of
     each (the split loss of oracle.grid)."""
-    kx = (2.0 / grid.dx) * math.sin(m * math.pi / grid.nx / 2.0)
-    ky = (2.0 / grid.dy) * math.sin(n * math.pi / grid.ny / 2.0)
-    kz = (2.0 / grid.dz) * math.sin(p * math.pi / grid.nz / 2.0)
+    kx = kappa(grid.order, m * math.pi / grid.nx, grid.dx)
+    ky = kappa(grid.order, n * math.pi / grid.ny, grid.dy)
+    kz = kappa(grid.order, p * math.pi / grid.nz, grid.dz)
     EX, EY, EZ, HX, HY, HZ = range(6)
     A = np.zeros((6, 6))
     B = np.zeros((6, 6))

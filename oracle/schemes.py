@@ -34,9 +34,9 @@ from typing import Callable
 
 import numpy as np
 
-from .grid import (AXIS, COMPS, E_COMPS, PAIRS, Grid, add, apply_op, diff_e_to_h,
-                   diff_h_to_e, line_operator_coeffs, material_at_samples, scale,
-                   solve_implicit, solve_lines)
+from .grid import (AXIS, COMPS, E_COMPS, PAIRS, Grid, add, apply_op, d_e_to_h, d_h_to_e,
+                   line_operator_coeffs, material_at_samples, scale, solve_implicit, solve_lines,
+                   solve_lines4)
 
 
 @dataclass
@@ -192,16 +192,20 @@ def procedure(P: Problem, state: dict, op: str, h: float, rhs_src: dict | None =
         mask = g.e_interior_mask(ec)
         b = h / (2.0 * P.mat[ec])
         d = h / (2.0 * P.mat[hc])
-        r = state[ec] + sgn * b * diff_h_to_e(state[hc], a, sp, g.shape(ec))
+        r = state[ec] + sgn * b * d_h_to_e(g, state[hc], a, sp, g.shape(ec))
         if rhs_src is not None:
             r = r + rhs_src[ec]
         r = r * mask
-        lo, ce, up = line_operator_coeffs(b, d, a, sp)
         diag = 0.5 + 0.25 * b * P.mat["sigma"][ec] if "sigma" in P.mat else 0.5
-        # 1/2 w - (b/2) d(d dw): the line operator scaled by 1/2
-        w = solve_lines(diag, 0.5 * lo, 0.5 * ce, 0.5 * up, r, a) * mask
+        if g.order == 4:
+            # 1/2 w - (b/2) D(d D w) with the fourth-order differences
+            w = solve_lines4(diag, 0.5 * b, d, r, a, sp) * mask
+        else:
+            lo, ce, up = line_operator_coeffs(b, d, a, sp)
+            # 1/2 w - (b/2) d(d dw): the line operator scaled by 1/2
+            w = solve_lines(diag, 0.5 * lo, 0.5 * ce, 0.5 * up, r, a) * mask
         w_all[ec] = w
-        new[hc] = state[hc] + sgn * d * diff_e_to_h(w, a, sp)
+        new[hc] = state[hc] + sgn * d * d_e_to_h(g, w, a, sp)
         e_new = w - state[ec]
         if post_src is not None:
             e_new = e_new + post_src[ec]
