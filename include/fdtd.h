@@ -143,6 +143,20 @@ int fdtd_set_material(fdtd_t* h, const double* eps_r_cell, const double* mu_r_ce
  * fdtd_step. */
 int fdtd_set_media(fdtd_t* h, const double* eps_r_cell, const double* mu_r_cell, const double* sigma_cell);
 
+/* Order of the spatial differences: 2 (the Yee differences of Sec. III,
+ * the default) or 4.  The paper names higher-order difference operators as
+ * a variant its fundamental schemes leave room for (end of Sec. III-A)
+ * without formulae; with order 4 every first difference of A and B is the
+ * fourth-order staggered central difference (9/8 (u_{+1/2} - u_{-1/2}) -
+ * 1/24 (u_{+3/2} - u_{-3/2})) / d, with PEC images past the walls
+ * (tangential E odd, H even).  A and B stay skew in the energy product (the
+ * schemes keep their invariants); each line system has bandwidth 3 and is
+ * solved by a banded LU formed in FP64, one thread per line (three
+ * field-sized device scratch arrays are allocated here).  Uniform lossless media and
+ * single grids only: FDTD_ERR_UNSUPPORTED for per-cell media, conductivity,
+ * batches and the reverse pass.  Only valid before the first fdtd_step. */
+int fdtd_set_order(fdtd_t* h, int order);
+
 /* Set one physical field component at the current time (compact Yee shape,
  * handle precision).  For FADI the auxiliary state (Eq. 10) is formed from
  * the physical fields on the next fdtd_step. */

@@ -166,6 +166,11 @@ class Simulation:
             sa, sp = ptr(sigma_cell)
             check(lib().fdtd_set_media(self._h, ep, mp, sp), "fdtd_set_media")
 
+    def set_order(self, order: int):
+        """Spatial difference order: 2 (Yee) or 4 (fourth-order staggered,
+        PEC images); before the first step, uniform lossless media."""
+        check(lib().fdtd_set_order(self._h, int(order)), "fdtd_set_order")
+
     def _put(self, fn, comp, data, what):
         c = COMPS[comp]
         if hasattr(data, "is_cuda") and data.is_cuda:

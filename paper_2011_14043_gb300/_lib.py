@@ -28,7 +28,7 @@ COMPS = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = (
-    "fdtd_create", "fdtd_destroy", "fdtd_get_dt", "fdtd_set_material", "fdtd_set_media", "fdtd_set_field",
+    "fdtd_create", "fdtd_destroy", "fdtd_get_dt", "fdtd_set_material", "fdtd_set_media", "fdtd_set_order", "fdtd_set_field",
     "fdtd_get_field", "fdtd_get_state", "fdtd_set_state", "fdtd_set_source", "fdtd_add_probe",
     "fdtd_step", "fdtd_get_probe", "fdtd_energy", "fdtd_steps_done", "fdtd_synchronize",
     "fdtd_strerror", "fdtd_set_timing", "fdtd_get_stats", "fdtd_reset_stats",
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         "fdtd_get_dt": (i32, [vp, dp]),
         "fdtd_set_material": (i32, [vp, vp, vp]),
         "fdtd_set_media": (i32, [vp, vp, vp, vp]),
+        "fdtd_set_order": (i32, [vp, i32]),
         "fdtd_set_field": (i32, [vp, i32, vp, i32]),
         "fdtd_get_field": (i32, [vp, i32, vp, i32]),
         "fdtd_get_state": (i32, [vp, i32, vp, i32]),

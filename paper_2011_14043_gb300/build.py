@@ -22,6 +22,7 @@ DEPENDS = SOURCES + [
     os.path.join(HERE, "csrc", "line_kernels.cuh"),
     os.path.join(HERE, "csrc", "aux_kernels.cuh"),
     os.path.join(HERE, "csrc", "adjoint_kernels.cuh"),
+    os.path.join(HERE, "csrc", "line4_kernels.cuh"),
     os.path.join(ROOT, "include", "fdtd.h"),
 ]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -32,6 +32,7 @@
 #include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "line_kernels.cuh"
+#include "line4_kernels.cuh"
 
 namespace {
 
@@ -126,6 +127,11 @@ struct fdtd_s {
   // b sigma / 4 to the implicit diagonal (a host-side change of the pivots)
   bool lossy = false;
   double sigma_u = 0.0;             // uniform sigma (when sig_node is null)
+  // order of the spatial differences: 2 (Yee) or 4 (fourth-order staggered,
+  // PEC images; uniform lossless media, single grids)
+  int order = 2;
+  void* tmp4 = nullptr;             // order 4: field-shaped scratch of the line solves, one
+                                    // per E component (pairs of a procedure run concurrently)
   double* sig_node[3] = {nullptr, nullptr, nullptr};  // per-node sigma at E samples (device)
   std::vector<double> sig_host[3];  // the same on the host, only while coefficients are built
   bool mu_var = false;              // per-node mu (general media kernels)
@@ -400,6 +406,89 @@ void edge_eps(const fdtd_t* h, const double* er, int c, std::vector<double>& out
       }
 }
 
+// Fourth-order differences: the banded LU (bandwidth 3, no pivoting: the
+// matrix is symmetric positive definite) of one pair's line system
+//   1/2 w - (kb kd / 2) D'(D' w) = r   on the interior nodes 1..N-1,
+// D' the stencil (c1 = 9/8, c2 = -1/24 as the kernel rounds it) with PEC
+// images, formed in FP64 from the couplings the kernel uses.  Rows (hi, lo)
+// of fdtd::T4_*: multipliers l1..l3 of L, 1/u0 and u1..u3 of U per node.
+int build_pair4(fdtd_t* h, const PairGeom& g, PairCoef& c, double hh) {
+  const bool f32 = h->prec == FDTD_F32;
+  auto rnd = [&](double x) { return f32 ? (double)(float)x : x; };
+  const double de = spacing(h, g.axis);
+  const double b = hh / (2.0 * kEps0 * h->eps_r);
+  c.kb = rnd(g.sign * b / de);
+  c.kd = rnd(c.kd);
+  const double bd = c.kb * c.kd;
+  const double c1 = 1.125, c2 = rnd(-1.0 / 24.0);
+  const int N = std::max(g.N, 1);
+  const int n = std::max(N - 1, 0);   // unknowns: nodes 1..N-1
+  // stencils with images: (D' E)_f over node offsets, (D' H)_j over faces
+  auto face_img = [&](int f) { return f < 0 ? -1 - f : (f > N - 1 ? 2 * N - 1 - f : f); };
+  // dense band of K = D'_HE D'_EH: row k (node k+1), columns k-3..k+3
+  std::vector<double> band((size_t)n * 7, 0.0);
+  auto addK = [&](int row, int col, double v) {
+    if (col < 0 || col >= n) return;  // a wall node: fixed at zero
+    const int o = col - row;
+    if (o < -3 || o > 3) return;
+    band[(size_t)row * 7 + (o + 3)] += v;
+  };
+  const int fo[4] = {0, -1, 1, -2};
+  const double fw[4] = {c1, -c1, c2, -c2};
+  const int no[4] = {1, 0, 2, -1};
+  const double nw[4] = {c1, -c1, c2, -c2};
+  for (int k = 0; k < n; ++k) {
+    const int j = k + 1;
+    for (int a = 0; a < 4; ++a) {
+      const int f = face_img(j + fo[a]);
+      for (int q = 0; q < 4; ++q) {
+        int m = f + no[q];
+        double sgn = 1.0;
+        if (m < 0) { m = -m; sgn = -1.0; }
+        if (m > N) { m = 2 * N - m; sgn = -1.0; }
+        addK(k, m - 1, fw[a] * sgn * nw[q]);
+      }
+    }
+  }
+  // M = 1/2 I - (bd/2) K, factored in place (band storage, offsets -3..3)
+  for (int k = 0; k < n; ++k) {
+    for (int o = 0; o < 7; ++o) band[(size_t)k * 7 + o] *= -0.5 * bd;
+    band[(size_t)k * 7 + 3] += 0.5;
+  }
+  auto at = [&](int r, int col) -> double& { return band[(size_t)r * 7 + (col - r + 3)]; };
+  for (int i = 0; i < n; ++i) {
+    const double piv = at(i, i);
+    if (!(std::fabs(piv) > 0)) return FDTD_ERR_INVALID_ARG;
+    for (int k = i + 1; k <= std::min(i + 3, n - 1); ++k) {
+      const double l = at(k, i) / piv;
+      at(k, i) = l;
+      for (int m = i + 1; m <= std::min(i + 3, n - 1); ++m) at(k, m) -= l * at(i, m);
+    }
+  }
+  c.tlen = ((N + 4 + 31) / 32) * 32;
+  const int tl = c.tlen;
+  auto hi = [&](double x) { return f32 ? (double)(float)x : x; };
+  auto lo = [&](double x) { return f32 ? (double)(float)(x - (double)(float)x) : 0.0; };
+  std::vector<double> tab((size_t)fdtd::T4_ROWS * tl, 0.0);
+  auto put = [&](int row, int j, double v) {
+    tab[(size_t)row * tl + j] = hi(v);
+    tab[(size_t)(row + 1) * tl + j] = lo(v);
+  };
+  for (int k = 0; k < n; ++k) {
+    const int j = k + 1;
+    if (k >= 1) put(fdtd::T4_L1H, j, at(k, k - 1));
+    if (k >= 2) put(fdtd::T4_L2H, j, at(k, k - 2));
+    if (k >= 3) put(fdtd::T4_L3H, j, at(k, k - 3));
+    put(fdtd::T4_IUH, j, 1.0 / at(k, k));
+    if (k + 1 < n) put(fdtd::T4_U1H, j, at(k, k + 1));
+    if (k + 2 < n) put(fdtd::T4_U2H, j, at(k, k + 2));
+    if (k + 3 < n) put(fdtd::T4_U3H, j, at(k, k + 3));
+  }
+  c.jc = 1 << 30;
+  c.wall_fix = false;
+  return upload_any(h, &c.tab, tab);
+}
+
 // FP64 factorisation of the line systems of one procedure (operator op,
 // length hh):  1/2 w_j - (b_j/2)(d/d^2)(w_{j+1} - 2 w_j + w_{j-1}) = r_j, plus
 // loss_sign * b_j sigma_j / 4 on the diagonal in lossy media (loss_sign = -1
@@ -415,6 +504,11 @@ int build_proc(fdtd_t* h, int slot, int op, double hh, double loss_sign = 1.0) {
     const double de = spacing(h, g.axis);
     const double d = hh / (2.0 * kMu0 * h->mu_r);
     c.kd = g.sign * d / de;
+    if (h->order == 4) {
+      int rc = build_pair4(h, g, c, hh);
+      if (rc) return rc;
+      continue;
+    }
     if (!h->per_node) {
       const double b = hh / (2.0 * kEps0 * h->eps_r);
       c.kb = g.sign * b / de;
@@ -705,6 +799,10 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   // the rank-one wall correction (tune[1] bit 7: the table lanes instead)
   p.wall_fix = (c.wall_fix && sizeof(T) == 4 && (h->desc.tune[1] & 128) == 0) ? 1 : 0;
   p.kg_len = c.kg_len;
+  // one scratch array per E component: the three pairs of a procedure run
+  // concurrently (graph branches) and each has its own E component
+  p.tmp4 = h->tmp4 ? (T*)h->tmp4 + (size_t)g.ec * h->count : nullptr;
+  p.c2_4 = (T)(-1.0 / 24.0);
   return p;
 }
 
@@ -1043,9 +1141,22 @@ int launch_pair_gm(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   return FDTD_OK;
 }
 
+// Fourth-order differences: one thread per line (128 per block).
+template <typename T>
+int launch_line4(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, int mode) {
+  if (!h->tmp4) return FDTD_ERR_STATE;
+  const long long nl = g.n_lines();
+  const unsigned blocks = (unsigned)std::min<long long>((nl + 127) / 128, 152LL * 64);
+  h->launches++;
+  fdtd::proc_line4_kernel<T><<<blocks, 128, 0, h->stream>>>(p, g.rows ? 1 : 0, mode);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
 template <typename T>
 int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   if (g.empty()) return FDTD_OK;
+  if (h->order == 4) return launch_line4<T>(h, g, p, 0);
   if (p.nkd) {
     h->launches++;
     return launch_pair_gm<T>(h, g, p);
@@ -1215,6 +1326,10 @@ int fadi_init_t(fdtd_t* h) {
     if (g.empty()) continue;
     // (I + tau B) with tau = dt/2: kb = s*b/d_eta with b = dt/(2 eps) = tau/eps
     fdtd::PairParams<T> p = make_params<T>(h, g, P.pc[q], 1.0, 1.0, 0.0, 1.0, h->f, h->scratch);
+    if (h->order == 4) {
+      if (int rc4 = launch_line4<T>(h, g, p, 1)) return rc4;
+      continue;
+    }
     const long long total = g.n_lines() * g.N;
     const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);
     h->launches++;
@@ -1947,6 +2062,7 @@ int fdtd_destroy(fdtd_t* h) {
   if (h->d_stash) cudaFree(h->d_stash);
   if (h->d_partial) cudaFree(h->d_partial);
   if (h->d_ref_partial) cudaFree(h->d_ref_partial);
+  if (h->tmp4) cudaFree(h->tmp4);
   if (h->d_err) cudaFree(h->d_err);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->g_run) cudaStreamSynchronize(h->g_run);
@@ -1989,6 +2105,23 @@ int fdtd_set_material(fdtd_t* h, const double* eps, const double* mu) {
   return fdtd_set_media(h, eps, mu, nullptr);
 }
 
+int fdtd_set_order(fdtd_t* h, int order) {
+  if (!h || (order != 2 && order != 4)) return FDTD_ERR_INVALID_ARG;
+  if (h->poisoned) return FDTD_ERR_STATE;
+  if (h->steps > 0) return FDTD_ERR_STATE;
+  if (order == h->order) return FDTD_OK;
+  if (order == 4 && (h->per_node || h->mu_var || h->lossy)) return FDTD_ERR_UNSUPPORTED;
+  graph_release(h);
+  if (order == 4 && !h->tmp4) {
+    CK(dev_malloc(&h->tmp4, 3 * (size_t)h->count * h->esize));
+    CK(cudaMemsetAsync(h->tmp4, 0, 3 * (size_t)h->count * h->esize, h->stream));
+  }
+  h->order = order;
+  h->output_valid = false;
+  h->inv_dirty = true;
+  return build_all_coefs(h);
+}
+
 int fdtd_set_media(fdtd_t* h, const double* eps, const double* mu, const double* sigma) {
   if (!h) return FDTD_ERR_INVALID_ARG;
   if (h->poisoned) return FDTD_ERR_STATE;
@@ -2014,6 +2147,9 @@ int fdtd_set_media(fdtd_t* h, const double* eps, const double* mu, const double*
   // per-node mu runs the general-media kernels, built for lines of at most
   // 256 cells along y and z and 256 along x
   if (!m_uniform && (h->nx > 256 || h->ny > 256 || h->nz > 256)) return FDTD_ERR_UNSUPPORTED;
+  // fourth-order differences: uniform lossless media
+  if (h->order == 4 && (!e_uniform || !m_uniform || any_loss || (h->desc.tune[1] & 2) != 0))
+    return FDTD_ERR_UNSUPPORTED;
   // FADI's output relation and FLOD2's output processing solve with the loss
   // diagonal's sign flipped; they stay well conditioned (and nonsingular)
   // while sigma dt / eps <= 2 at every E sample (checked before the handle
@@ -2901,7 +3037,7 @@ int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batc
     if (h->poisoned) return FDTD_ERR_STATE;
     if (h->scheme != handles[0]->scheme || h->prec != handles[0]->prec) return FDTD_ERR_INVALID_ARG;
     if (h->stream != (cudaStream_t)stream) return FDTD_ERR_INVALID_ARG;
-    if (h->src_comp >= 0 || h->nprobes > 0 || h->mu_var) return FDTD_ERR_UNSUPPORTED;
+    if (h->src_comp >= 0 || h->nprobes > 0 || h->mu_var || h->order != 2) return FDTD_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (handles[j] == h) return FDTD_ERR_INVALID_ARG;
   }
@@ -3440,7 +3576,8 @@ int fdtd_adj_create(fdtd_t* h, const int32_t block[6], int64_t nsteps, int32_t c
   if (!h || !block || !out || nsteps < 1 || checkpoint_every < 1) return FDTD_ERR_INVALID_ARG;
   *out = nullptr;
   if (h->poisoned) return FDTD_ERR_STATE;
-  if (h->scheme != FDTD_FADI || !h->per_node || h->mu_var || h->lossy) return FDTD_ERR_UNSUPPORTED;
+  if (h->scheme != FDTD_FADI || !h->per_node || h->mu_var || h->lossy || h->order != 2)
+    return FDTD_ERR_UNSUPPORTED;
   if (!h->pending_init || h->steps != 0) return FDTD_ERR_STATE;
   if (h->nprobes > 0) return FDTD_ERR_UNSUPPORTED;
   const int i0 = block[0], i1 = block[1], j0 = block[2], j1 = block[3], k0 = block[4], k1 = block[5];

@@ -115,6 +115,8 @@ struct PairParams {
                          // TB_KGH/TB_KGL) instead of table lanes near the walls
   int kg_len;            // the wall correction is zero from this node on (a multiple of
                          // the segment length)
+  T* tmp4;               // fourth-order differences: field-shaped scratch of the line solve
+  T c2_4;                // fourth-order difference weight -1/24 in the field precision
 };
 
 // Bounds of one line for the checked build: a strided line touches its
