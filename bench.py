@@ -548,10 +548,12 @@ def suite(args):
     import oracle.grid as G
     import oracle.schemes as S
 
-    def gpu(nx, ny, nz, d, scheme, prec, cfl, fields, eps=None, src=None, steps=50, warm=5):
+    def gpu(nx, ny, nz, d, scheme, prec, cfl, fields, eps=None, src=None, steps=50, warm=5, sigma=None, order=2):
         sim = Simulation(nx, ny, nz, d, scheme=scheme, precision=prec, cfl=cfl, tune=tuple(args.tune))
-        if eps is not None:
-            sim.set_material(eps)
+        if order != 2:
+            sim.set_order(order)
+        if eps is not None or sigma is not None:
+            sim.set_material(eps, None, sigma)
         if src is not None:
             sim.set_source(*src)
         sim.set_fields(fields)
@@ -593,6 +595,12 @@ def suite(args):
     out.append({"workload": "FADI 256^3 cavity, CFL 4, 8 modes (no per-launch timing)",
                 "f32": gpu(256, 256, 256, 1e-3, "fadi", "f32", 4.0, f256, steps=200),
                 "f64": gpu(256, 256, 256, 1e-3, "fadi", "f64", 4.0, f256, steps=20)})
+    out.append({"workload": "FADI 256^3 cavity, CFL 4, 8 modes, fourth-order differences",
+                "f32": gpu(256, 256, 256, 1e-3, "fadi", "f32", 4.0, f256, steps=40, order=4),
+                "f64": gpu(256, 256, 256, 1e-3, "fadi", "f64", 4.0, f256, steps=10, order=4)})
+    out.append({"workload": "FADI 256^3 cavity, CFL 4, 8 modes, eps_r 2.5, uniform sigma 0.05 S/m (lossy)",
+                "f32": gpu(256, 256, 256, 1e-3, "fadi", "f32", 4.0, f256, steps=200,
+                           eps=np.full((256, 256, 256), 2.5), sigma=np.full((256, 256, 256), 0.05))})
     del f256
     n = 256
     d = 0.5e-3
@@ -605,6 +613,11 @@ def suite(args):
                     "f32": gpu(n, n, n, d, scheme, "f32", 8.0, z, eps, ("ez", 128, 128, 128, cur), steps=100),
                     "f64": gpu(n, n, n, d, scheme, "f64", 8.0, z, eps, ("ez", 128, 128, 128, cur), steps=20),
                     "oracle_1core": cpu(n, n, n, d, scheme, 8.0, z, eps, steps=1)})
+    sig = np.where(eps > 5.0, 0.5, 0.0)
+    out.append({"workload": "FLOD 256^3, eps_r blocks U[1,10] with sigma 0.5 S/m where eps_r > 5 (lossy), CFL 8, "
+                            "z dipole",
+                "f32": gpu(n, n, n, d, "flod", "f32", 8.0, z, eps, ("ez", 128, 128, 128, cur), steps=100,
+                           sigma=sig)})
     for o in out:
         o["unit"] = "cell-steps/s"
         print(json.dumps(o), flush=True)
