@@ -169,18 +169,50 @@ __global__ void probe_kernel(const ProbeParams<T> pp, double* stash, double* out
   }
 }
 
-// Per-block partial sums of w * x^2 in FP64 (w = scalar weight, or a
-// per-element FP64 weight times the scalar when wv != nullptr).
+// The six components' weighted sums of squares in one launch: per block one
+// FP64 partial sum of w_c * (wv[g]) * x_c[g]^2 over the concatenated arrays
+// (each n elements, n a multiple of 4, 16-byte aligned), read as 16-byte
+// vectors.  FP32 fields with scalar weights sum the 4 squares of a vector in
+// FP32 (FMA) before the FP64 accumulation: one FP64 operation per 4
+// elements, so the reduction runs at memory speed instead of at the FP64
+// rate; the rounding of that 4-term sum is 2^-22 relative, far below the
+// FP32 values' own.  Everything else accumulates each element in FP64.
+struct Energy6 {
+  const void* x[6];
+  const double* wv[6];
+  double w[6];
+};
+
 template <typename T>
-__global__ void weighted_sumsq_kernel(const T* x, const double* wv, double w, long long n,
-                                      double* partial) {
+__global__ void weighted_sumsq6_kernel(const Energy6 a, long long n, double* partial) {
+  const long long n4 = n / 4;
   double acc = 0.0;
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n;
-       g += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)x[g];
-    acc += (wv ? wv[g] : 1.0) * v * v;
+  for (int c = 0; c < 6; ++c) {
+    const double w = a.w[c];
+    const double* wv = a.wv[c];
+    double ac = 0.0;
+    if constexpr (sizeof(T) == 4) {
+      const float4* x4 = reinterpret_cast<const float4*>(a.x[c]);
+      for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n4;
+           g += (long long)gridDim.x * blockDim.x) {
+        const float4 v = x4[g];
+        if (wv) {
+          ac += wv[4 * g] * ((double)v.x * v.x) + wv[4 * g + 1] * ((double)v.y * v.y) +
+                wv[4 * g + 2] * ((double)v.z * v.z) + wv[4 * g + 3] * ((double)v.w * v.w);
+        } else {
+          ac += (double)fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+        }
+      }
+    } else {
+      const double2* x2 = reinterpret_cast<const double2*>(a.x[c]);
+      for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n / 2;
+           g += (long long)gridDim.x * blockDim.x) {
+        const double2 v = x2[g];
+        ac += (wv ? wv[2 * g] : 1.0) * v.x * v.x + (wv ? wv[2 * g + 1] : 1.0) * v.y * v.y;
+      }
+    }
+    acc += w * ac;
   }
-  acc *= w;
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

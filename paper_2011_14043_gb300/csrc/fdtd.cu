@@ -1314,11 +1314,17 @@ double source_value(const fdtd_t* h, long long n) {
   return h->src_scale * h->src_current[(size_t)n];
 }
 
+int copy_uncovered_to_scratch(fdtd_t* h, int slot);
+
 // FADI input initialization (Eq. 10 with Eqs. 7, 8a): v^0 = (I + dt/2 B) u^0
 // plus the first sub-step's source (dt/2) f.
 template <typename T>
 int fadi_init_t(fdtd_t* h) {
-  int rc = copy_state_to_scratch(h);
+  // the B pairs write their lines of all six arrays into scratch; what no
+  // line covers keeps its value: the H samples on the walls (normal H, not
+  // updated) and the arrays of a pair without unknowns are copied, while E
+  // outside the lines is the walls and the row padding, zero in every array
+  int rc = copy_uncovered_to_scratch(h, 1);
   if (rc) return rc;
   const ProcCoef& P = h->proc[1];
   for (int q = 0; q < 3; ++q) {
@@ -1652,35 +1658,65 @@ int one_step(fdtd_t* h) {
   return FDTD_OK;
 }
 
+// Scratch receives the B procedure's (or explicit operator's) output line by
+// line; the samples no line of it covers keep the state's values: the three
+// H components are copied whole (their samples on the walls, normal H, are
+// in no line), and both arrays of a pair without unknowns (lines of one
+// cell).  E outside the lines is the walls and the row padding, zero in the
+// state and in scratch alike (no kernel writes a nonzero value there).
+int copy_uncovered_to_scratch(fdtd_t* h, int slot) {
+  int rc = ensure_scratch(h);
+  if (rc) return rc;
+  const ProcCoef& P = h->proc[slot];
+  bool copied[6] = {false, false, false, false, false, false};
+  for (int c = 3; c < 6; ++c) copied[c] = true;
+  for (int q = 0; q < 3; ++q)
+    if (h->geom[P.op][q].empty()) copied[h->geom[P.op][q].ec] = true;
+  for (int c = 0; c < 6; ++c)
+    if (copied[c])
+      CK(cudaMemcpyAsync(h->scratch[c], h->f[c], (size_t)h->count * h->esize, cudaMemcpyDeviceToDevice,
+                         h->stream));
+  return FDTD_OK;
+}
+
 // Physical field into scratch (FADI: (I + dt/2 B)^{-1}(v - pending source),
 // from Eqs. 2a, 8a, 9; FLOD2: output processing Eq. 23).  n_next: index of
 // the step that would come next (-1: the steps taken so far).
 int physical_to_scratch(fdtd_t* h, long long n_next) {
   if (n_next < 0) n_next = h->steps;
   if (h->output_valid) return FDTD_OK;
-  int rc = copy_state_to_scratch(h);
-  if (rc) return rc;
-  if (!h->pending_init) {
-    if (h->scheme == FDTD_FADI) {
-      // u = (I + dt/2 B)^{-1} (v - (dt/2) f_pending), from Eqs. 2a, 8a and 9:
-      // the B pairs' line systems with the couplings of a procedure of length
-      // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
-      const double fp = source_value(h, n_next);
-      if ((rc = add_point(h, h->scratch[h->src_comp < 0 ? 0 : h->src_comp], -0.5 * h->dt * fp))) return rc;
-      rc = procedure_ex(h, h->lossy ? 3 : 1, -1.0, 0.5, 0.0, 0.5, h->scratch, h->scratch);
-      if (rc) return rc;
-    } else if (h->scheme == FDTD_FLOD2) {
-      // Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4} - (dt/8) f(t_{n+1} + dt/2),
-      // u^{n+1} = v - u^{n+5/4}; the source term is added before the solve
-      // and once more to the new E (which subtracts the E the solve saw)
-      const double r = -0.125 * h->dt * source_value(h, n_next);
-      void* at = h->scratch[h->src_comp < 0 ? 0 : h->src_comp];
-      if ((rc = add_point(h, at, r))) return rc;
-      rc = procedure_ex(h, h->lossy ? 4 : 2, -1.0, 1.0, -1.0, 1.0, h->scratch, h->scratch);
-      if (rc) return rc;
-      if ((rc = add_point(h, at, r))) return rc;
-    }
+  int rc;
+  if (h->pending_init || (h->scheme != FDTD_FADI && h->scheme != FDTD_FLOD2)) {
+    if ((rc = copy_state_to_scratch(h))) return rc;
+    h->output_valid = true;
+    return FDTD_OK;
   }
+  // The B pairs read the state and write scratch (out of place); what no
+  // line covers is copied (copy_uncovered_to_scratch).  The source sample's
+  // E component is copied to scratch first and adjusted there.
+  const bool fadi = h->scheme == FDTD_FADI;
+  const int slot = fadi ? (h->lossy ? 3 : 1) : (h->lossy ? 4 : 2);
+  if ((rc = copy_uncovered_to_scratch(h, slot))) return rc;
+  void* in[6];
+  for (int c = 0; c < 6; ++c) in[c] = h->f[c];
+  // FADI: u = (I + dt/2 B)^{-1} (v - (dt/2) f_pending), from Eqs. 2a, 8a and
+  // 9: the B pairs' line systems with the couplings of a procedure of length
+  // -dt; E_out = w/2 and H_out = H + (1/2) kd' dw.
+  // FLOD2, Eq. 23: (1/2 I + dt/8 B) v = u^{n+5/4} - (dt/8) f(t_{n+1} + dt/2),
+  // u^{n+1} = v - u^{n+5/4}; the source term is added before the solve and
+  // once more to the new E (which subtracts the E the solve saw).
+  const double adj = fadi ? -0.5 * h->dt * source_value(h, n_next) : -0.125 * h->dt * source_value(h, n_next);
+  const bool src = h->src_comp >= 0 && adj != 0.0;
+  if (src) {
+    CK(cudaMemcpyAsync(h->scratch[h->src_comp], h->f[h->src_comp], (size_t)h->count * h->esize,
+                       cudaMemcpyDeviceToDevice, h->stream));
+    if ((rc = add_point(h, h->scratch[h->src_comp], adj))) return rc;
+    in[h->src_comp] = h->scratch[h->src_comp];
+  }
+  if (fadi) rc = procedure_ex(h, slot, -1.0, 0.5, 0.0, 0.5, in, h->scratch);
+  else rc = procedure_ex(h, slot, -1.0, 1.0, -1.0, 1.0, in, h->scratch);
+  if (rc) return rc;
+  if (!fadi && src && (rc = add_point(h, h->scratch[h->src_comp], adj))) return rc;
   h->output_valid = true;
   return FDTD_OK;
 }
@@ -1820,26 +1856,27 @@ int zero_walls(fdtd_t* h, int comp, void* arr) {
   return FDTD_OK;
 }
 
-constexpr int kEnergyBlocks = 152 * 4;
+constexpr int kEnergyBlocks = 152 * 8;
 
-// Per-block partial sums of the energy of six arrays into partial[6][blocks]
-// (asynchronous on the handle's stream).
+// Per-block partial sums of the energy of the six arrays into
+// partial[blocks], one launch (asynchronous on the handle's stream).
 template <typename T>
 int energy_launch(fdtd_t* h, void* const* arr, double* partial) {
+  fdtd::Energy6 a;
   for (int c = 0; c < 6; ++c) {
-    const double w = c < 3 ? kEps0 * (h->per_node ? 1.0 : h->eps_r) : kMu0 * h->mu_r;
-    const double* wv = c < 3 ? (h->per_node ? h->eps_node[c] : nullptr) : (h->mu_var ? h->mu_node[c - 3] : nullptr);
-    h->launches++;
-    fdtd::weighted_sumsq_kernel<T><<<kEnergyBlocks, 256, 0, h->stream>>>((const T*)arr[c], wv, w, h->count,
-                                                                         partial + (size_t)c * kEnergyBlocks);
-    CK(cudaGetLastError());
+    a.x[c] = arr[c];
+    a.w[c] = c < 3 ? kEps0 * (h->per_node ? 1.0 : h->eps_r) : kMu0 * h->mu_r;
+    a.wv[c] = c < 3 ? (h->per_node ? h->eps_node[c] : nullptr) : (h->mu_var ? h->mu_node[c - 3] : nullptr);
   }
+  h->launches++;
+  fdtd::weighted_sumsq6_kernel<T><<<kEnergyBlocks, 256, 0, h->stream>>>(a, h->count, partial);
+  CK(cudaGetLastError());
   return FDTD_OK;
 }
 
 // Read back and add up the partials (synchronises the stream).
 int energy_sum(fdtd_t* h, const double* partial, double* out) {
-  std::vector<double> part((size_t)6 * kEnergyBlocks);
+  std::vector<double> part((size_t)kEnergyBlocks);
   CK(cudaMemcpyAsync(part.data(), partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   double s = 0;
@@ -1850,7 +1887,7 @@ int energy_sum(fdtd_t* h, const double* partial, double* out) {
 
 int energy(fdtd_t* h, void* const* arr, double* out) {
   if (!h->d_partial) {
-    CK(dev_malloc((void**)&h->d_partial, sizeof(double) * 6 * kEnergyBlocks));
+    CK(dev_malloc((void**)&h->d_partial, sizeof(double) * kEnergyBlocks));
     h->partial_n = kEnergyBlocks;
   }
   int rc = h->prec == FDTD_F64 ? energy_launch<double>(h, arr, h->d_partial)
@@ -1870,7 +1907,7 @@ int take_invariant_ref(fdtd_t* h) {
   h->inv_have = false;
   h->inv_ref = -1.0;
   if (h->src_comp >= 0) return FDTD_OK;
-  if (!h->d_ref_partial) CK(dev_malloc((void**)&h->d_ref_partial, sizeof(double) * 6 * kEnergyBlocks));
+  if (!h->d_ref_partial) CK(dev_malloc((void**)&h->d_ref_partial, sizeof(double) * kEnergyBlocks));
   int rc = h->prec == FDTD_F64 ? energy_launch<double>(h, h->f, h->d_ref_partial)
                                : energy_launch<float>(h, h->f, h->d_ref_partial);
   if (rc) return rc;
