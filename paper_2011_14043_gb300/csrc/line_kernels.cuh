@@ -234,9 +234,23 @@ __device__ __forceinline__ HiLo<T> phase_forward(const PairParams<T>& p, int j0,
     if constexpr (MODE == 2) r = fma(qn[t], E[t], p.ks * (H[t] - hprev));
     else r = fma(p.kb, H[t] - hprev, E[t]);
     hprev = H[t];
-    const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev);
-    y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
-    if constexpr (MODE == 2) pf *= -m.hi;
+    if constexpr (MODE == 2 && use_hilo<T>()) {
+      // FP32: m_t = off / beta_{t-1}: y_t = r_t - off (y_{t-1} / beta_{t-1}),
+      // the pivot and the off-diagonal each applied as hi + lo (no
+      // double-float product of the two).  FP64 keeps m_t = off * (1/beta)
+      // as one product: fewer operations on the FP64 pipe that binds it.
+      if (t == 0) {
+        y[t] = r;
+      } else {
+        const T v = fma(ibn[t - 1], y[t - 1], ibl[t - 1] * y[t - 1]);
+        y[t] = fma(-p.offh, v, fma(-p.offl, v, r));
+      }
+      pf *= -p.offh * (t == 0 ? ib_prev.hi : ibn[t - 1]);
+    } else {
+      const HiLo<T> m = coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev);
+      y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
+      if constexpr (MODE == 2) pf *= -m.hi;
+    }
   }
   if constexpr (MODE == 2) return {pf, T(0)};
   else return coef_pf<T, MODE>(p, j0, L - 1);
@@ -251,7 +265,8 @@ __device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0
     T q = T(1);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
-      q *= -coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev).hi;
+      if constexpr (use_hilo<T>()) q *= -p.offh * (t == 0 ? ib_prev.hi : ibn[t - 1]);
+      else q *= -coef_m<T, L, MODE>(p, j0, t, ibl, ibn, ib_prev).hi;
       y[t] = fma(q, yin, y[t]);
     }
   } else {
@@ -261,14 +276,21 @@ __device__ __forceinline__ HiLo<T> phase_backward(const PairParams<T>& p, int j0
   T pb = T(1), wn = T(0);
 #pragma unroll
   for (int t = L - 1; t >= 0; --t) {
-    const HiLo<T> c = coef_c<T, L, MODE>(p, j0, t, ibl, ibn);
-    const HiLo<T> ib = coef_ib<T, L, MODE>(p, j0, t, ibl, ibn);
-    T u;
-    if constexpr (use_hilo<T>()) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
-    else u = -c.hi * wn;
-    y[t] = fma(y[t], ib.hi, u);
+    if constexpr (MODE == 2 && use_hilo<T>()) {
+      // FP32: c_t = off / beta_t: w_t = (y_t - off w_{t+1}) / beta_t
+      const T u = fma(-p.offh, wn, fma(-p.offl, wn, y[t]));
+      y[t] = fma(ibn[t], u, ibl[t] * u);
+      pb *= -p.offh * ibn[t];
+    } else {
+      const HiLo<T> c = coef_c<T, L, MODE>(p, j0, t, ibl, ibn);
+      const HiLo<T> ib = coef_ib<T, L, MODE>(p, j0, t, ibl, ibn);
+      T u;
+      if constexpr (use_hilo<T>()) u = fma(-c.hi, wn, fma(-c.lo, wn, y[t] * ib.lo));
+      else u = -c.hi * wn;
+      y[t] = fma(y[t], ib.hi, u);
+      if constexpr (MODE == 2) pb *= -c.hi;
+    }
     wn = y[t];
-    if constexpr (MODE == 2) pb *= -c.hi;
   }
   if constexpr (MODE == 2) return {pb, T(0)};
   else return coef_pb<T, MODE>(p, j0, 0);
@@ -282,7 +304,8 @@ __device__ __forceinline__ void phase_fix(const PairParams<T>& p, int j0, T win,
     T q = T(1);
 #pragma unroll
     for (int t = L - 1; t >= 0; --t) {
-      q *= -coef_c<T, L, MODE>(p, j0, t, ibl, ibn).hi;
+      if constexpr (use_hilo<T>()) q *= -p.offh * ibn[t];
+      else q *= -coef_c<T, L, MODE>(p, j0, t, ibl, ibn).hi;
       y[t] = fma(q, win, y[t]);
     }
   } else {

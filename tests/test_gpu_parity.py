@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs.  Bars: relative error <= 1e-12 in FP64 mode and <= 1e-4
-in FP32 mode (energy norm over all six components and per component)."""
+in FP32 mode, in the energy norm over all six components and per component
+(every component carrying at least 1e-4 of the energy), for probe series
+(relative to the series' maximum) and for energies."""
 import math
 
 import numpy as np
@@ -20,10 +22,12 @@ TOL = {"f64": 1e-12, "f32": 1e-4}
 
 
 def check(a, b, prec):
+    """The whole field in the energy norm and every component carrying at
+    least 1e-4 of the energy, each within the stated tolerance."""
     e = energy_norm_rel(a, b)
     assert e <= TOL[prec], e
-    for c, v in per_comp_rel(a, b).items():
-        assert v <= TOL[prec] * 10, (c, v)
+    for c, v in per_comp_rel(a, b, floor=1e-4).items():
+        assert v <= TOL[prec], (c, v)
     return e
 
 
@@ -79,7 +83,7 @@ def test_inhomogeneous_with_dipole_vs_oracle(scheme, prec):
     ref, _, _ = S.run_fundamental(P, scheme, u0, steps)
     out, _, en, _ = gpu_run(nx, ny, nz, d, d, d, dt, scheme, prec, u0, steps, eps=eps, source=src)
     check(out, ref, prec)
-    assert en[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec] * 10)
+    assert en[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec])
 
 
 @pytest.mark.parametrize("dims", [(2, 2, 1), (2, 2, 2), (3, 2, 2), (2, 3, 4), (5, 4, 1), (3, 3, 3)])
@@ -244,7 +248,7 @@ def test_fadi_probes_at_and_beside_the_source(prec):
     _, series, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "fadi", prec, W.zero_fields(nx, ny, nz), steps,
                               eps=eps, source=src, probes=probes)
     for a, b in zip(series, ref):
-        assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b)), (np.max(np.abs(a - b)), np.max(np.abs(b)))
+        assert np.max(np.abs(a - b)) <= TOL[prec] * np.max(np.abs(b)), (np.max(np.abs(a - b)), np.max(np.abs(b)))
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -278,7 +282,7 @@ def test_flod2_probes_vs_oracle(prec):
     out, series, _, _ = gpu_run(nx, ny, nz, d, d, d, dt, "flod2", prec, u0, steps, probes=probes)
     check(out, ref_u, prec)
     for a, b in zip(series, ref):
-        assert np.max(np.abs(a - b)) <= TOL[prec] * 10 * np.max(np.abs(b))
+        assert np.max(np.abs(a - b)) <= TOL[prec] * np.max(np.abs(b))
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -342,8 +346,8 @@ def test_general_media_eps_and_mu_vs_oracle(scheme, prec):
     check(out, ref, prec)
     for pid, s_ref in zip(pids, series):
         got = sim.get_probe(pid, steps)
-        assert np.max(np.abs(got - s_ref)) <= TOL[prec] * 10 * np.max(np.abs(s_ref))
-    assert sim.energy()[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec] * 10)
+        assert np.max(np.abs(got - s_ref)) <= TOL[prec] * np.max(np.abs(s_ref))
+    assert sim.energy()[0] == pytest.approx(I.energy(g, P.mat, ref), rel=TOL[prec])
     sim.close()
 
 
