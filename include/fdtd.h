@@ -86,7 +86,9 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * 3: 2 x 6); tune[1] bit 7 set: lines along x of FP32 fields in homogeneous
  * media take the tabulated factors near the walls (lanes that diverge from
  * the rest of their warp) instead of the converged factors on every lane
- * with a rank-one (Sherman-Morrison) wall correction. */
+ * with a rank-one (Sherman-Morrison) wall correction; tune[1] bit 8 set:
+ * fields set from page-locked host memory go through a staging copy
+ * instead of being read in place by the unpacking kernel. */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of

@@ -203,6 +203,44 @@ def test_tma_path_bit_identical_to_direct_path(prec, dims):
         assert np.array_equal(c2[c], b[c]), c
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_pinned_host_buffers_match_pageable(prec):
+    """Fields set from page-locked host memory are read in place by the
+    unpacking kernel (no staging copy); pageable memory (and tune[1] bit 8)
+    takes the staged copy.  Both give identical arrays, read back into
+    pinned or pageable memory alike."""
+    import torch
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 37, 29, 23
+    dtype = np.float64 if prec == "f64" else np.float32
+    tdt = torch.float64 if prec == "f64" else torch.float32
+    u0 = random_fields(nx, ny, nz, seed=91)
+    outs = []
+    for pinned, tune in ((True, (0, 0)), (False, (0, 0)), (True, (0, 256))):
+        sim = Simulation(nx, ny, nz, 1e-3, scheme="fadi", precision=prec, cfl=4.0, tune=tune)
+        for c in G.COMPS:
+            if pinned:
+                t = torch.empty(u0[c].shape, dtype=tdt, pin_memory=True)
+                t.numpy()[...] = u0[c].astype(dtype)
+                sim.set_field(c, t.numpy())
+            else:
+                sim.set_field(c, u0[c].astype(dtype))
+        sim.step(5)
+        got = {}
+        for c in G.COMPS:
+            if pinned:
+                t = torch.empty(sim.shape(c), dtype=tdt, pin_memory=True)
+                sim.get_field(c, out=t.numpy())
+                got[c] = t.numpy().copy()
+            else:
+                got[c] = sim.get_field(c)
+        outs.append(got)
+        sim.close()
+    for c in G.COMPS:
+        assert np.array_equal(outs[0][c], outs[1][c]), c
+        assert np.array_equal(outs[2][c], outs[1][c]), c
+
+
 @pytest.mark.parametrize("scheme", ["fadi", "fss"])
 @pytest.mark.parametrize("dims", [(256, 40, 33), (200, 37, 29), (129, 20, 24), (256, 9, 300)])
 def test_tma_rows_bit_identical_to_direct_rows(dims, scheme):
