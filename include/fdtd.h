@@ -88,7 +88,10 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * the rest of their warp) instead of the converged factors on every lane
  * with a rank-one (Sherman-Morrison) wall correction; tune[1] bit 8 set:
  * fields set from page-locked host memory go through a staging copy
- * instead of being read in place by the unpacking kernel. */
+ * instead of being read in place by the unpacking kernel; tune[1] bit 9
+ * set: with fourth-order differences every line takes the one-thread-per-
+ * line kernel instead of the block-tiled kernel (FP32 fields, lines of at
+ * most 512 cells; the same arithmetic, the same results). */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of

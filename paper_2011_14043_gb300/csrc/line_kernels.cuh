@@ -117,6 +117,9 @@ struct PairParams {
                          // the segment length)
   T* tmp4;               // fourth-order differences: field-shaped scratch of the line solve
   T c2_4;                // fourth-order difference weight -1/24 in the field precision
+  int jc4, je4;          // fourth-order differences: the factor rows of nodes jc4..je4 all
+                         // equal cv4 (empty when jc4 > je4)
+  T cv4[14];             // those rows' (hi, lo) l1, l2, l3, 1/u0, u1, u2, u3
 };
 
 // Bounds of one line for the checked build: a strided line touches its
