@@ -383,6 +383,7 @@ def run_batch(wls, prec, steps, warmup, want_fields):
     ms = e0.elapsed_time(e1)
     per_step = b.launches_per_step()
     cfg = b.config()
+    cfg.update(b.mode())
     fields = [s.get_fields() for s in sims] if want_fields else None
     b.close()
     for s in sims:

@@ -288,7 +288,8 @@ typedef struct fdtd_batch_s fdtd_batch_t;
 int fdtd_batch_create(fdtd_t* const* handles, int count, void* stream, fdtd_batch_t** out);
 int fdtd_batch_step(fdtd_batch_t* b, int64_t nsteps);
 int fdtd_batch_destroy(fdtd_batch_t* b);
-/* Kernel launches per batch step (for accounting); valid after a step. */
+/* Kernel launches per batch step (for accounting; persistent mode: one per
+ * procedure, memsets not counted); valid after a step. */
 int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
 /* Launch shape of the batch: cfg = {y lanes, y L, z lanes, z L, x warps per
  * block, x packing} (lanes: lines per tile of the y/z kernels; L: nodes per
@@ -307,6 +308,24 @@ int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step);
  * to tuning. */
 int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[6], double tune_ms[3]);
 int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg);
+/* How a batch step runs.  mode 0: the graph of shape-uniform launches above
+ * (one per launch group, on parallel branches).  mode 1: one persistent
+ * launch per procedure: its blocks take work items (a block's worth of the
+ * y/z tiles or x lines of any group of any grid) from a counter that a
+ * memset zeroes before the launch, until the list is exhausted; both steps
+ * are captured in the step graph.  mode -1 (default): the first step times
+ * both on the batch's own data (one-step graph replays writing scratch) and
+ * keeps the faster; cached like the shapes.  Persistent launches need y and
+ * z lines of one shape with a built kernel ((lanes, L) = (16, 8), and for
+ * FP32 fields (16, 16)) and x lines of per-node grids packed by 8, 16 or 32
+ * lanes: mode
+ * 1 otherwise fails with FDTD_ERR_UNSUPPORTED at the next step, and mode -1
+ * keeps the launches.  Both modes run the same arithmetic per line: the
+ * fields agree to the last bit.  fdtd_batch_get_mode (valid after a step)
+ * gives the mode in use (1 persistent) and the tuned time of one step in
+ * each mode (ms; 0 when not timed). */
+int fdtd_batch_set_mode(fdtd_batch_t* b, int mode);
+int fdtd_batch_get_mode(const fdtd_batch_t* b, int32_t* persistent, double step_ms[2]);
 
 /* Reverse mode: gradient of a probe-energy objective of FADI with respect to
  * the per-cell permittivity.

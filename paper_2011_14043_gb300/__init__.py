@@ -268,8 +268,9 @@ class Simulation:
 
 
 class Batch:
-    """Many independent grids stepped together (one launch per line direction
-    and procedure for the whole batch, one CUDA graph per batch step).  The
+    """Many independent grids stepped together (launch groups per line
+    direction and procedure, or one persistent launch per procedure, for the
+    whole batch; one CUDA graph per batch step).  The
     Simulation objects stay usable for set/get/energy and must share scheme,
     precision and stream; they must outlive the batch."""
 
@@ -308,6 +309,24 @@ class Batch:
         v = ctypes.c_int64()
         check(lib().fdtd_batch_launches(self._h, ctypes.byref(v)), "fdtd_batch_launches")
         return v.value
+
+    _MODES = {"auto": -1, "launches": 0, "persistent": 1}
+
+    def set_mode(self, mode: str = "auto"):
+        """How a step runs: "launches" (a graph of shape-uniform launches),
+        "persistent" (one persistent launch per procedure over a work list
+        of every grid's lines), or "auto" (the faster, timed at the first
+        step)."""
+        check(lib().fdtd_batch_set_mode(self._h, self._MODES[mode]), "fdtd_batch_set_mode")
+
+    def mode(self) -> dict:
+        """The mode in use (after a step) and the tuned time of one step in
+        each mode (ms; 0 when not timed)."""
+        v = ctypes.c_int32()
+        ms = (ctypes.c_double * 2)()
+        check(lib().fdtd_batch_get_mode(self._h, ctypes.byref(v), ms), "fdtd_batch_get_mode")
+        return {"mode": "persistent" if v.value else "launches",
+                "tuned_step_ms": {"launches": ms[0], "persistent": ms[1]}}
 
     def synchronize(self):
         self.sims[0].synchronize()

@@ -33,7 +33,8 @@ EXPORTS = (
     "fdtd_step", "fdtd_get_probe", "fdtd_energy", "fdtd_steps_done", "fdtd_synchronize",
     "fdtd_strerror", "fdtd_set_timing", "fdtd_get_stats", "fdtd_reset_stats",
     "fdtd_energy_noalloc", "fdtd_batch_create", "fdtd_batch_step", "fdtd_batch_destroy",
-    "fdtd_batch_launches", "fdtd_batch_get_config", "fdtd_batch_set_config", "fdtd_adj_create", "fdtd_adj_forward", "fdtd_adj_backward", "fdtd_adj_memory",
+    "fdtd_batch_launches", "fdtd_batch_get_config", "fdtd_batch_set_config", "fdtd_batch_set_mode",
+    "fdtd_batch_get_mode", "fdtd_adj_create", "fdtd_adj_forward", "fdtd_adj_backward", "fdtd_adj_memory",
     "fdtd_adj_destroy", "fdtd_selftest_bounded_wait", "fdtd_debug_fail_alloc", "fdtd_probe_fp64_fma",
 )
 
@@ -110,6 +111,8 @@ def lib() -> ctypes.CDLL:
         "fdtd_batch_launches": (i32, [vp, ctypes.POINTER(i64)]),
         "fdtd_batch_get_config": (i32, [vp, ctypes.POINTER(ctypes.c_int32), dp]),
         "fdtd_batch_set_config": (i32, [vp, ctypes.POINTER(ctypes.c_int32)]),
+        "fdtd_batch_set_mode": (i32, [vp, i32]),
+        "fdtd_batch_get_mode": (i32, [vp, ctypes.POINTER(ctypes.c_int32), dp]),
         "fdtd_adj_create": (i32, [vp, ctypes.POINTER(ctypes.c_int32), i64, ctypes.c_int32, ctypes.POINTER(vp)]),
         "fdtd_adj_forward": (i32, [vp, dp]),
         "fdtd_adj_backward": (i32, [vp, ctypes.c_double, vp, i32]),

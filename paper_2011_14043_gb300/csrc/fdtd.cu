@@ -2636,6 +2636,20 @@ struct fdtd_batch_s {
   bool tuned = false;       // cfg chosen (by the tuner, the cache or the caller)
   bool autotune = true;
   double tune_ms[3] = {0, 0, 0};  // per direction: time of the chosen shape (both procedures)
+  // How a step runs: a graph of shape-uniform launches on parallel branches
+  // (0), or one persistent launch per procedure taking every group's work
+  // from a list (1).  mode -1: the tuner times both and keeps the faster.
+  int mode = -1;
+  int tuned_persistent = -1;   // the tuner's choice for the current shapes (-1: not made)
+  bool persistent = false;
+  double mode_ms[2] = {0, 0};  // tuned time of one step in each mode (0: not timed)
+  struct Persistent {
+    void* d_groups = nullptr;  // BatchGroupRef<T>[groups of the slot]
+    void* d_work = nullptr;    // BatchWork[nwork]
+    int nwork = 0, threads = 0, blocks = 0, lanes = 0, L = 0;
+    size_t smem = 0;
+  } pl[2];
+  int* d_counter = nullptr;    // one work counter per procedure of a step
 };
 
 namespace {
@@ -2648,9 +2662,18 @@ void free_group_list(std::vector<BatchGroup>& gs) {
   gs.clear();
 }
 
+void free_persistent(fdtd_batch_t::Persistent (&pl)[2]) {
+  for (auto& q : pl) {
+    if (q.d_groups) cudaFree(q.d_groups);
+    if (q.d_work) cudaFree(q.d_work);
+    q = fdtd_batch_t::Persistent();
+  }
+}
+
 void free_groups(fdtd_batch_t* b) {
   free_group_list(b->groups[0]);
   free_group_list(b->groups[1]);
+  free_persistent(b->pl);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
@@ -2867,17 +2890,149 @@ int launch_batch_group(const BatchGroup& g, cudaStream_t s) {
   return FDTD_OK;
 }
 
+// The persistent launches' shapes: (lanes, L) of the y/z lines (one for
+// both directions) with an instantiated kernel.
+// (FP64 fields: (16, 8) only; at L = 16 their solve needs more than the
+// 128 registers a 512-thread block leaves.)
+template <typename T>
+const void* persistent_fn(int lanes, int L) {
+  if (lanes == 16 && L == 8) return (const void*)fdtd::proc_batch_persistent_kernel<T, 16, 8>;
+  if constexpr (sizeof(T) == 4)
+    if (lanes == 16 && L == 16) return (const void*)fdtd::proc_batch_persistent_kernel<T, 16, 16>;
+  return nullptr;
+}
+
+// Work lists of the persistent launches, one per procedure slot, from the
+// groups built for the same shapes.  FDTD_ERR_UNSUPPORTED when the groups
+// do not fit one persistent kernel: y and z lines of different (lanes, L),
+// a shape without an instantiated kernel, or x lines of uniform media.
+template <typename T>
+int build_persistent_t(const std::vector<BatchGroup> (&gs)[2], fdtd_batch_t::Persistent (&out)[2]) {
+  int lanes = 0, L = 0, maxtpt = 32;
+  for (int slot = 0; slot < 2; ++slot)
+    for (const auto& g : gs[slot]) {
+      if (g.kind == 2) {
+        if (g.lpl != 8 && g.lpl != 16 && g.lpl != 32) return FDTD_ERR_UNSUPPORTED;
+        continue;
+      }
+      if (lanes == 0) {
+        lanes = g.lanes;
+        L = g.L;
+      }
+      if (g.lanes != lanes || g.L != L) return FDTD_ERR_UNSUPPORTED;
+      maxtpt = std::max(maxtpt, g.P * g.lanes);
+    }
+  if (lanes == 0) {  // no y/z lines at all: any instantiated shape serves the x lines
+    lanes = 16;
+    L = 8;
+  }
+  const void* fn = persistent_fn<T>(lanes, L);
+  if (!fn) return FDTD_ERR_UNSUPPORTED;
+  const int threads = std::max(256, ((maxtpt + 31) / 32) * 32);
+  cudaFuncAttributes fa;
+  BCK(cudaFuncGetAttributes(&fa, fn));
+  if (threads > fa.maxThreadsPerBlock) return FDTD_ERR_UNSUPPORTED;
+  int dev = 0, nsm = 1;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  for (int slot = 0; slot < 2; ++slot) {
+    fdtd_batch_t::Persistent& q = out[slot];
+    std::vector<fdtd::BatchGroupRef<T>> refs;
+    std::vector<fdtd::BatchWork> work_yz, work_x;
+    size_t smem = 0;
+    for (size_t gi = 0; gi < gs[slot].size(); ++gi) {
+      const BatchGroup& g = gs[slot][gi];
+      fdtd::BatchGroupRef<T> r{};
+      r.params = (const fdtd::PairParams<T>*)g.d_params;
+      r.index = g.d_index;
+      r.nitems = g.nitems;
+      r.ngrids = g.ngrids;
+      if (g.kind == 2) {
+        r.kind = 1;
+        r.lpl = g.lpl;
+        const int wpi = threads / 32;
+        const long long warps = (g.nitems + (32 / g.lpl) - 1) / (32 / g.lpl);
+        for (long long w0 = 0; w0 < warps; w0 += wpi) work_x.push_back({(int)gi, 0, w0});
+      } else {
+        const int tpt = g.P * g.lanes;
+        const int nslots = (threads + tpt - 1) / tpt;
+        r.kind = 0;
+        r.P = g.P;
+        r.G = std::max(1, threads / tpt);
+        smem = std::max(smem, fdtd::batch_params_bytes<T>(nslots) +
+                                  (size_t)nslots * 6 * (g.P | 1) * g.lanes * sizeof(T));
+        for (long long t0 = 0; t0 < g.nitems; t0 += r.G) work_yz.push_back({(int)gi, 0, t0});
+      }
+      refs.push_back(r);
+    }
+    // the y/z items (their blocks run the longest) first
+    std::vector<fdtd::BatchWork> work = work_yz;
+    work.insert(work.end(), work_x.begin(), work_x.end());
+    if (smem > 227 * 1024) return FDTD_ERR_UNSUPPORTED;
+    if (smem > 48 * 1024) BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    if (per_sm < 1) return FDTD_ERR_UNSUPPORTED;
+    q.threads = threads;
+    q.smem = smem;
+    q.lanes = lanes;
+    q.L = L;
+    q.nwork = (int)work.size();
+    q.blocks = (int)std::min<long long>(std::max(1, q.nwork), (long long)nsm * per_sm);
+    if (!refs.empty()) {
+      BCK(dev_malloc(&q.d_groups, sizeof(fdtd::BatchGroupRef<T>) * refs.size()));
+      BCK(cudaMemcpy(q.d_groups, refs.data(), sizeof(fdtd::BatchGroupRef<T>) * refs.size(), cudaMemcpyHostToDevice));
+    }
+    if (!work.empty()) {
+      BCK(dev_malloc(&q.d_work, sizeof(fdtd::BatchWork) * work.size()));
+      BCK(cudaMemcpy(q.d_work, work.data(), sizeof(fdtd::BatchWork) * work.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  return FDTD_OK;
+}
+
+template <typename T>
+int launch_persistent(const fdtd_batch_t::Persistent& q, int* counter, cudaStream_t s) {
+  if (q.nwork == 0) return FDTD_OK;
+  BCK(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  const auto* groups = (const fdtd::BatchGroupRef<T>*)q.d_groups;
+  const auto* work = (const fdtd::BatchWork*)q.d_work;
+  if (q.lanes == 16 && q.L == 8) {
+    fdtd::proc_batch_persistent_kernel<T, 16, 8><<<q.blocks, q.threads, q.smem, s>>>(groups, work, q.nwork, counter);
+  } else if constexpr (sizeof(T) == 4) {
+    if (q.lanes == 16 && q.L == 16)
+      fdtd::proc_batch_persistent_kernel<T, 16, 16><<<q.blocks, q.threads, q.smem, s>>>(groups, work, q.nwork,
+                                                                                         counter);
+    else
+      return FDTD_ERR_UNSUPPORTED;
+  } else {
+    return FDTD_ERR_UNSUPPORTED;
+  }
+  BCK(cudaGetLastError());
+  return FDTD_OK;
+}
+
 // One time step of every grid: the scheme's procedure sequence.  The groups
 // of one procedure write disjoint arrays, so they fork onto parallel
-// branches; the next procedure starts when all of them have joined.
+// branches; the next procedure starts when all of them have joined.  In
+// persistent mode each procedure is one launch (after the reset of its work
+// counter).
 template <typename T>
-int batch_one_step(fdtd_batch_t* b) {
+int batch_one_step_with(fdtd_batch_t* b, const std::vector<BatchGroup> (&groups)[2],
+                        const fdtd_batch_t::Persistent (&pl)[2], bool persistent) {
   static const int seq_fss[3] = {0, 1, 0};
   static const int seq_two[2] = {0, 1};
   const int* seq = b->scheme == FDTD_FSS ? seq_fss : seq_two;
   const int n = b->scheme == FDTD_FSS ? 3 : 2;
+  if (persistent) {
+    for (int k = 0; k < n; ++k) {
+      int rc = launch_persistent<T>(pl[seq[k]], b->d_counter + k, b->run);
+      if (rc) return rc;
+    }
+    return FDTD_OK;
+  }
   for (int k = 0; k < n; ++k) {
-    const auto& gs = b->groups[seq[k]];
+    const auto& gs = groups[seq[k]];
     const int nb = std::min<int>(kBatchBranches, (int)gs.size());
     BCK(cudaEventRecord(b->ev_fork, b->run));
     for (int i = 0; i < nb; ++i) BCK(cudaStreamWaitEvent(b->branch[i], b->ev_fork, 0));
@@ -2891,6 +3046,11 @@ int batch_one_step(fdtd_batch_t* b) {
     }
   }
   return FDTD_OK;
+}
+
+template <typename T>
+int batch_one_step(fdtd_batch_t* b) {
+  return batch_one_step_with<T>(b, b->groups, b->pl, b->persistent);
 }
 
 // ---------------------------------------------------------------------------
@@ -2992,6 +3152,120 @@ double time_direction(fdtd_batch_t* b, const BatchCfg& cfg, int kind, int reps) 
   return ok ? best : -1.0;
 }
 
+// Time of one step (ms, best of `reps` replays of a captured one-step graph,
+// writing scratch) in each mode under cfg; a negative value when the mode
+// does not apply.
+template <typename T>
+int time_step_modes(fdtd_batch_t* b, const BatchCfg& cfg, int reps, double out[2], bool launches = true) {
+  out[0] = out[1] = -1.0;
+  std::vector<BatchGroup> gs[2];
+  fdtd_batch_t::Persistent pl[2];
+  int rc = build_groups_t<T>(b, cfg, gs, -1, true);
+  const bool have_pl = rc == FDTD_OK && build_persistent_t<T>(gs, pl) == FDTD_OK;
+  cudaGetLastError();
+  for (int mode = launches ? 0 : 1; mode < 2 && rc == FDTD_OK; ++mode) {
+    if (mode == 1 && !have_pl) break;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaStreamBeginCapture(b->run, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+    const int rs = batch_one_step_with<T>(b, gs, pl, mode == 1);
+    const cudaError_t e = cudaStreamEndCapture(b->run, &g);
+    if (rs != FDTD_OK || e != cudaSuccess || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      continue;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    bool ok = true;
+    for (int r = 0; r < reps + 1 && ok; ++r) {  // the first replay warms up
+      cudaEventRecord(e0, b->run);
+      if (cudaGraphLaunch(ex, b->run) != cudaSuccess) ok = false;
+      cudaEventRecord(e1, b->run);
+      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    if (ok) out[mode] = best;
+  }
+  free_group_list(gs[0]);
+  free_group_list(gs[1]);
+  free_persistent(pl);
+  BCK(cudaGetLastError());
+  return rc;
+}
+
+std::string batch_mode_key(const fdtd_batch_t* b) {
+  const BatchCfg& c = b->cfg;
+  return batch_key(b) + "|mode|" + std::to_string(c.lanes[0]) + "," + std::to_string(c.L[0]) + "," +
+         std::to_string(c.lanes[1]) + "," + std::to_string(c.L[1]) + "," + std::to_string(c.wpb) + "," +
+         std::to_string(c.xpack);
+}
+
+// The tuner's choice between the two modes (cached like the shapes): the
+// graph of launches with the current shapes against the persistent launches
+// with the current shapes, when they fit one persistent kernel, and with
+// each built persistent shape on both y and z; a persistent win brings its
+// shapes along.
+template <typename T>
+int batch_tune_mode_t(fdtd_batch_t* b) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const std::string key = batch_mode_key(b);
+  TuneVal v;
+  auto take = [&](int pers, int Ly, int Lz) {
+    b->tuned_persistent = pers;
+    if (pers) {
+      b->cfg.lanes[0] = b->cfg.lanes[1] = 16;
+      b->cfg.L[0] = Ly;
+      b->cfg.L[1] = Lz;
+      b->cfg.xpack = 1;
+    }
+  };
+  if (tune_cache_get(key, &v)) {
+    b->mode_ms[0] = v[1] * 1e-3;
+    b->mode_ms[1] = v[2] * 1e-3;
+    take(v[0], v[3], v[4]);
+    return FDTD_OK;
+  }
+  BCK(cudaEventRecord(b->ev_in, b->stream));
+  BCK(cudaStreamWaitEvent(b->run, b->ev_in, 0));
+  double ms[2];
+  int rc = time_step_modes<T>(b, b->cfg, 5, ms);
+  if (rc) return rc;
+  double best = ms[1];
+  BatchCfg pick = b->cfg;
+  for (int L : {8, 16}) {
+    BatchCfg c = b->cfg;
+    c.lanes[0] = c.lanes[1] = 16;
+    c.L[0] = c.L[1] = L;
+    c.xpack = 1;
+    if (!persistent_fn<T>(16, L)) continue;
+    if (c.lanes[0] == b->cfg.lanes[0] && c.lanes[1] == b->cfg.lanes[1] && c.L[0] == b->cfg.L[0] &&
+        c.L[1] == b->cfg.L[1] && c.xpack == b->cfg.xpack)
+      continue;  // timed above
+    double m2[2];
+    if ((rc = time_step_modes<T>(b, c, 5, m2, false))) return rc;
+    if (m2[1] > 0 && (best < 0 || m2[1] < best)) {
+      best = m2[1];
+      pick = c;
+    }
+  }
+  b->mode_ms[0] = ms[0] > 0 ? ms[0] : 0;
+  b->mode_ms[1] = best > 0 ? best : 0;
+  const int pers = (best > 0 && (ms[0] < 0 || best < ms[0])) ? 1 : 0;
+  take(pers, pick.L[0], pick.L[1]);
+  tune_cache_put(key, {pers, (int)std::lround(b->mode_ms[0] * 1e3), (int)std::lround(b->mode_ms[1] * 1e3),
+                       pick.L[0], pick.L[1], 0});
+  return FDTD_OK;
+}
+
 template <typename T>
 int batch_tune_t(fdtd_batch_t* b) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -3070,15 +3344,28 @@ int batch_prepare(fdtd_batch_t* b) {
       if (rc) return rc;
     }
     b->tuned = true;
+    b->tuned_persistent = -1;
     b->bound.clear();
   }
+  if (!b->d_counter) BCK(dev_malloc((void**)&b->d_counter, 3 * sizeof(int)));
+  if (b->mode == -1 && b->tuned_persistent < 0) {
+    int rc = b->prec == FDTD_F64 ? batch_tune_mode_t<double>(b) : batch_tune_mode_t<float>(b);
+    if (rc) return rc;
+  }
+  const bool want = b->mode == 1 || (b->mode == -1 && b->tuned_persistent == 1);
   std::vector<const void*> ptrs;
   for (fdtd_t* h : b->h)
     for (int c = 0; c < 6; ++c) ptrs.push_back(h->f[c]);
-  if (ptrs == b->bound && !b->groups[0].empty()) return FDTD_OK;
+  if (ptrs == b->bound && !b->groups[0].empty() && want == b->persistent) return FDTD_OK;
   free_groups(b);
   int rc = b->prec == FDTD_F64 ? build_groups_t<double>(b, b->cfg, b->groups, -1, false)
                                : build_groups_t<float>(b, b->cfg, b->groups, -1, false);
+  b->persistent = false;
+  if (!rc && want) {
+    rc = b->prec == FDTD_F64 ? build_persistent_t<double>(b->groups, b->pl)
+                             : build_persistent_t<float>(b->groups, b->pl);
+    b->persistent = rc == FDTD_OK;
+  }
   if (rc) {
     free_groups(b);
     return rc;
@@ -3238,6 +3525,7 @@ int fdtd_batch_destroy(fdtd_batch_t* b) {
   if (b->run) cudaStreamSynchronize(b->run);
   cudaStreamSynchronize(b->stream);
   free_groups(b);
+  if (b->d_counter) cudaFree(b->d_counter);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -3292,8 +3580,28 @@ int fdtd_batch_launches(const fdtd_batch_t* b, int64_t* per_step) {
   const int n = b->scheme == FDTD_FSS ? 3 : 2;
   const int seq[3] = {0, 1, 0};
   long long c = 0;
-  for (int k = 0; k < n; ++k) c += (long long)b->groups[seq[k]].size();
+  for (int k = 0; k < n; ++k)
+    c += b->persistent ? (b->pl[seq[k]].nwork > 0 ? 1 : 0) : (long long)b->groups[seq[k]].size();
   *per_step = c;
+  return FDTD_OK;
+}
+
+int fdtd_batch_set_mode(fdtd_batch_t* b, int mode) {
+  if (!b || mode < -1 || mode > 1) return FDTD_ERR_INVALID_ARG;
+  if (mode == b->mode) return FDTD_OK;
+  b->mode = mode;
+  free_groups(b);
+  b->bound.clear();
+  return FDTD_OK;
+}
+
+int fdtd_batch_get_mode(const fdtd_batch_t* b, int32_t* persistent, double step_ms[2]) {
+  if (!b || !persistent) return FDTD_ERR_INVALID_ARG;
+  *persistent = b->persistent ? 1 : 0;
+  if (step_ms) {
+    step_ms[0] = b->mode_ms[0];
+    step_ms[1] = b->mode_ms[1];
+  }
   return FDTD_OK;
 }
 
@@ -3334,6 +3642,7 @@ int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg) {
   b->cfg.xpack = cfg[5];
   b->autotune = false;
   b->tuned = true;
+  b->tuned_persistent = -1;
   free_groups(b);
   b->bound.clear();
   return FDTD_OK;

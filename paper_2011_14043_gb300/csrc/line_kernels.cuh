@@ -1466,28 +1466,37 @@ __host__ __device__ constexpr size_t batch_params_bytes(int G) {
   return ((sizeof(PairParams<T>) * (size_t)G + 15) / 16) * 16;
 }
 
+// The tiles of one block: slots of tpt = P * LANES threads (whole warps) from
+// thread 0 on, the first G of them holding tiles first .. first + G - 1;
+// slots past those (or past the last tile), including a last slot with
+// fewer than tpt threads, are spares that take part in the barriers with no
+// active lane.  Shared memory: nslots parameter copies, then nslots carry
+// buffers.
 template <typename T, int LANES, int L>
-__global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ params,
-                                          const BatchTile* __restrict__ tiles, int ntiles, int G) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tpt = blockDim.x / G;  // threads of one tile
+__device__ __forceinline__ void strided_batch_block(const PairParams<T>* __restrict__ params,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, int G, int tpt,
+                                                    int nslots, long long first, unsigned char* smem_raw) {
   const int sub = threadIdx.x / tpt;
   const int tid = threadIdx.x % tpt;
   const int P = tpt / LANES;
-  const int tix = blockIdx.x * G + sub;
-  const bool have = tix < ntiles;
-  const BatchTile tile = tiles[have ? tix : blockIdx.x * G];
+  const long long tix = first + sub;
+  const bool have = sub < G && tix < ntiles;
   PairParams<T>* ps = reinterpret_cast<PairParams<T>*>(smem_raw);
   {
-    // cooperative word copy of this tile's grid parameters
+    // word copy of every slot's grid parameters (spare slots: the first tile's)
     static_assert(sizeof(PairParams<T>) % 4 == 0, "word copy");
-    const int* src = reinterpret_cast<const int*>(params + tile.grid);
-    int* dst = reinterpret_cast<int*>(ps + sub);
-    for (int k = tid; k < (int)(sizeof(PairParams<T>) / 4); k += tpt) dst[k] = src[k];
+    constexpr int W = (int)(sizeof(PairParams<T>) / 4);
+    for (int k = threadIdx.x; k < nslots * W; k += blockDim.x) {
+      const int sl = k / W;
+      const long long tx = first + sl;
+      const int grid = tiles[(sl < G && tx < ntiles) ? tx : first].grid;
+      reinterpret_cast<int*>(ps + sl)[k % W] = reinterpret_cast<const int*>(params + grid)[k % W];
+    }
   }
   __syncthreads();
+  const BatchTile tile = tiles[have ? tix : first];
   const PairParams<T>& p = ps[sub];
-  T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(G)) + (size_t)sub * 6 * chain_stride(P) * LANES;
+  T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(nslots)) + (size_t)sub * 6 * chain_stride(P) * LANES;
   const int lane = tid % LANES;
   const int s = tid / LANES;
   const int i = tile.x0 + lane;
@@ -1539,6 +1548,14 @@ __global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ para
   else if (p.wall_fix) strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win, tid, tpt);
   else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
+}
+
+template <typename T, int LANES, int L>
+__global__ void proc_strided_batch_kernel(const PairParams<T>* __restrict__ params,
+                                          const BatchTile* __restrict__ tiles, int ntiles, int G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  strided_batch_block<T, LANES, L>(params, tiles, ntiles, G, (int)blockDim.x / G, G, (long long)blockIdx.x * G,
+                                   smem_raw);
 }
 
 // x lines of every grid of a group: one warp per line; line_start[g] is the
@@ -1686,12 +1703,12 @@ __global__ void proc_rows_lpl_kernel(const PairParams<T> p) {
 // access leaves the line.  Lines past the last one take part in the
 // shuffles without touching memory.
 template <typename T, int L, int LPL>
-__global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ params,
-                                          const long long* __restrict__ line_start, int ngrids) {
+__device__ __forceinline__ void rows_batch_pn_warp(const PairParams<T>* __restrict__ params,
+                                                   const long long* __restrict__ line_start, int ngrids,
+                                                   long long gwarp) {
   constexpr int LPW = 32 / LPL;  // lines per warp
   const int lane = threadIdx.x & 31;
   const int sl = lane % LPL;
-  const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const long long total = line_start[ngrids];
   if (gwarp * LPW >= total) return;  // whole warp leaves together
   const long long gline = gwarp * LPW + lane / LPL;
@@ -1774,6 +1791,68 @@ __global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ para
         p.h_out[base + j0 + t] = H[t];
       }
     }
+  }
+}
+
+template <typename T, int L, int LPL>
+__global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ params,
+                                          const long long* __restrict__ line_start, int ngrids) {
+  rows_batch_pn_warp<T, L, LPL>(params, line_start, ngrids,
+                                (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+}
+
+// ---------------------------------------------------------------------------
+// A whole procedure of a batch in one persistent launch
+// ---------------------------------------------------------------------------
+// The work of one procedure (its three pairs on every grid) is a list of
+// items, each a block's worth of one launch group: G tiles of a y/z group
+// (slots of P * LANES threads, as strided_batch_block), or blockDim / 32
+// warps of an x group of per-node grids (LPL lanes per line).  Every block
+// takes the next item from a counter (zeroed before the launch) until the
+// list is exhausted; all its threads see the same item and pass the same
+// barriers, and the loop ends after at most one pass over the list.
+struct BatchWork {
+  int group;        // index into the launch's group table
+  int pad;
+  long long first;  // y/z: first tile of the item; x: first warp
+};
+
+template <typename T>
+struct BatchGroupRef {
+  const PairParams<T>* params;  // [ngrids]
+  const void* index;            // y/z: BatchTile[nitems]; x: line_start[ngrids + 1]
+  long long nitems;             // y/z: tiles; x: lines
+  int ngrids;
+  int kind;                     // 0 y/z tiles, 1 x lines of per-node grids
+  int P, G, lpl, pad;           // y/z: segments and tiles per item; x: lanes per line
+};
+
+template <typename T, int LANES, int L>
+__global__ void __launch_bounds__(512) proc_batch_persistent_kernel(const BatchGroupRef<T>* __restrict__ groups,
+                                                                     const BatchWork* __restrict__ work, int nwork,
+                                                                     int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = s_next;
+    if (w >= nwork) break;  // the same value in every thread of the block
+    const BatchWork item = work[w];
+    const BatchGroupRef<T> g = groups[item.group];
+    if (g.kind == 0) {
+      const int tpt = g.P * LANES;
+      const int nslots = ((int)blockDim.x + tpt - 1) / tpt;
+      strided_batch_block<T, LANES, L>(g.params, static_cast<const BatchTile*>(g.index), (int)g.nitems, g.G, tpt,
+                                       nslots, item.first, smem_raw);
+    } else {
+      const long long gwarp = item.first + (threadIdx.x >> 5);
+      const long long* ls = static_cast<const long long*>(g.index);
+      if (g.lpl == 8) rows_batch_pn_warp<T, 8, 8>(g.params, ls, g.ngrids, gwarp);
+      else if (g.lpl == 16) rows_batch_pn_warp<T, 8, 16>(g.params, ls, g.ngrids, gwarp);
+      else rows_batch_pn_warp<T, 8, 32>(g.params, ls, g.ngrids, gwarp);
+    }
+    __syncthreads();  // the next item reuses the shared memory and s_next
   }
 }
 

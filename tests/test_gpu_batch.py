@@ -2,7 +2,8 @@
 reduced sizes): every grid against the FP64 oracle, and, with the batch's
 segment length pinned to the handles' own, against the same grid stepped on
 its own (the same arithmetic: bit-identical).  Tuned and fixed launch
-shapes against the oracle; the tuner's cache file."""
+shapes against the oracle; the tuner's cache file; one persistent launch
+per procedure against the graph of launch groups (bit-identical)."""
 import numpy as np
 import pytest
 
@@ -121,15 +122,108 @@ def test_tuner_cache_file(tmp_path, monkeypatch):
     b1 = Batch(sims)
     b1.step(1)
     cfg1 = b1.config()
+    mode1 = b1.mode()
     b1.close()
+    # one line for the shapes, one for the mode chosen with them
     lines = path.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].split()[1:] == [str(v) for v in (*cfg1["y"], *cfg1["z"],
+    assert len(lines) == 2 and lines[0].split()[1:] == [str(v) for v in (*cfg1["y"], *cfg1["z"],
                                                                        cfg1["x_warps_per_block"], cfg1["x_pack"])]
+    assert "|mode|" in lines[1] and lines[1].split()[1] == ("1" if mode1["mode"] == "persistent" else "0")
     sims2 = [make_sim(sp, "fadi", "f32") for sp in specs]
     b2 = Batch(sims2)
     b2.step(1)
     assert b2.config()["y"] == cfg1["y"] and b2.config()["z"] == cfg1["z"]
-    assert len(path.read_text().splitlines()) == 1     # served from the cache
+    assert b2.mode()["mode"] == mode1["mode"]
+    assert len(path.read_text().splitlines()) == 2     # served from the cache
     with pytest.raises(FdtdError):
         b2.set_config(y=(24, 16), z=(16, 16))
     b2.close()
+
+
+def per_node_specs(seed):
+    """Grids with eps_r blocks (per-node media) of uneven sizes: y lines up to
+    165 cells (22 segments of 8: 352-thread tiles), z lines up to 129, x lines
+    packed by 8, 16 and 32 lanes."""
+    rng = np.random.default_rng(seed)
+    d = 1e-3
+    out = []
+    for nx, ny, nz in [(40, 165, 6), (9, 7, 33), (70, 12, 20), (17, 33, 129), (6, 6, 5), (33, 40, 17),
+                       (130, 10, 9)]:
+        cfl = float(rng.uniform(2.0, 10.0))
+        eps = W.eps_blocks(rng, nx, ny, nz, 1.0, 4.0)
+        modes = W.random_modes(rng, nx, ny, nz, d, d, d, count=3, mmax=4)
+        out.append((nx, ny, nz, cfl, eps, W.mode_sum_fields(modes, nx, ny, nz)))
+    return out
+
+
+def run_mode(specs, scheme, prec, mode, shape, steps):
+    from paper_2011_14043_gb300 import Batch
+    sims = [make_sim(sp, scheme, prec) for sp in specs]
+    b = Batch(sims)
+    b.set_config(y=shape, z=shape, x_pack=1)
+    b.set_mode(mode)
+    b.step(2)
+    b.step(steps - 2)  # a second call replays the same graph
+    info = b.mode()
+    per_step = b.launches_per_step()
+    out = [sm.get_fields() for sm in sims]
+    b.close()
+    for sm in sims:
+        sm.close()
+    return out, info, per_step
+
+
+@pytest.mark.parametrize("prec,shape", [("f64", (16, 8)), ("f32", (16, 8)), ("f32", (16, 16))])
+@pytest.mark.parametrize("scheme", ["fadi", "fss"])
+def test_persistent_batch_matches_launch_groups(scheme, prec, shape):
+    """One persistent launch per procedure (work items of every group of
+    every grid) against the graph of shape-uniform launches: the same
+    arithmetic per line, so the fields agree to the last bit; one launch per
+    procedure; the smallest grid against the FP64 oracle."""
+    specs = per_node_specs(70)
+    steps = 5
+    a, ia, na = run_mode(specs, scheme, prec, "launches", shape, steps)
+    p, ip, n_p = run_mode(specs, scheme, prec, "persistent", shape, steps)
+    assert ia["mode"] == "launches" and ip["mode"] == "persistent"
+    assert n_p == (3 if scheme == "fss" else 2) and na > n_p
+    for q, (x, y) in enumerate(zip(a, p)):
+        for c in G.COMPS:
+            assert np.array_equal(x[c], y[c]), (q, c)
+    nx, ny, nz, cfl, eps, u0 = specs[4]
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    from paper_2011_14043_gb300 import Simulation
+    dt = Simulation(nx, ny, nz, 1e-3, scheme=scheme, precision=prec, cfl=cfl).dt
+    ref, _, _ = S.run_fundamental(S.Problem(g, dt, eps_r_cell=eps), scheme, u0, steps)
+    assert energy_norm_rel(p[4], ref) <= TOL[prec]
+
+
+def test_batch_mode_tuned_and_persistent_limits():
+    """mode "auto" times both modes on the batch's own data and keeps the
+    faster; "persistent" on a batch whose x lines are not packed (uniform
+    media) is refused at the step."""
+    from paper_2011_14043_gb300 import Batch, FdtdError
+    specs = per_node_specs(71)
+    sims = [make_sim(sp, "fadi", "f32") for sp in specs]
+    b = Batch(sims)
+    b.set_config(y=(16, 8), z=(16, 8), x_pack=1)  # shapes fixed; the mode still tuned
+    b.step(2)
+    info = b.mode()
+    ms = info["tuned_step_ms"]
+    assert ms["launches"] > 0 and ms["persistent"] > 0
+    assert info["mode"] == ("persistent" if ms["persistent"] < ms["launches"] else "launches")
+    b.close()
+    for sm in sims:
+        sm.close()
+    specs = small_batch(72, 4)
+    sims = [make_sim(sp, "fadi", "f32") for sp in specs]
+    b = Batch(sims)
+    b.set_config(y=(16, 16), z=(16, 16), x_pack=0)
+    b.set_mode("persistent")
+    with pytest.raises(FdtdError) as err:
+        b.step(1)
+    assert err.value.code == -6
+    b.set_mode("launches")
+    b.step(1)
+    b.close()
+    for sm in sims:
+        sm.close()
