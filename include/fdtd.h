@@ -310,17 +310,20 @@ int fdtd_batch_get_config(const fdtd_batch_t* b, int32_t cfg[6], double tune_ms[
 int fdtd_batch_set_config(fdtd_batch_t* b, const int32_t* cfg);
 /* How a batch step runs.  mode 0: the graph of shape-uniform launches above
  * (one per launch group, on parallel branches).  mode 1: one persistent
- * launch per procedure: its blocks take work items (a block's worth of the
- * y/z tiles or x lines of any group of any grid) from a counter that a
- * memset zeroes before the launch, until the list is exhausted; both steps
- * are captured in the step graph.  mode -1 (default): the first step times
+ * launch per procedure: its blocks take work items (y/z tiles of any grid
+ * packed side by side into the block's threads, or a block's worth of x
+ * lines) from a counter that a memset zeroes before the launch, until the
+ * list is exhausted; both are captured in the step graph.  mode -1 (default): the first step times
  * both on the batch's own data (one-step graph replays writing scratch) and
- * keeps the faster; cached like the shapes.  Persistent launches need y and
- * z lines of one shape with a built kernel ((lanes, L) = (16, 8), and for
- * FP32 fields (16, 16)) and x lines of per-node grids packed by 8, 16 or 32
- * lanes: mode
- * 1 otherwise fails with FDTD_ERR_UNSUPPORTED at the next step, and mode -1
- * keeps the launches.  Both modes run the same arithmetic per line: the
+ * keeps the faster (the persistent launches also with both y and z lines
+ * at (16, 8) and (16, 16), a persistent win bringing its shape along);
+ * cached like the shapes.  Persistent launches run blocks of 256 threads
+ * and need per-node media on every grid, y and z lines of one shape with a
+ * built kernel ((lanes, L) = (16, 8), and for FP32 fields (16, 16)) whose
+ * tiles take at most 256 threads (lines of at most 128 cells at L = 8, 256
+ * at L = 16), and x lines packed by 8, 16 or 32 lanes: mode 1 otherwise
+ * fails with FDTD_ERR_UNSUPPORTED at the next step, and mode -1 keeps the
+ * launches.  Both modes run the same arithmetic per line: the
  * fields agree to the last bit.  fdtd_batch_get_mode (valid after a step)
  * gives the mode in use (1 persistent) and the tuned time of one step in
  * each mode (ms; 0 when not timed). */

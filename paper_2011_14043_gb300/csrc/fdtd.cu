@@ -2612,6 +2612,7 @@ struct BatchGroup {
   int L = 16, P = 1, lanes = 16, wpb = 8;
   int G = 1;                // y/z tiles per block
   int lpl = 0;              // x lines of per-node grids: lanes per line (0: one warp per line)
+  int pn = 0;               // per-node media
   int ngrids = 0;
   long long nitems = 0;     // tiles (strided) or lines (x)
   void* d_params = nullptr; // PairParams<T>[ngrids]
@@ -2646,6 +2647,7 @@ struct fdtd_batch_s {
   struct Persistent {
     void* d_groups = nullptr;  // BatchGroupRef<T>[groups of the slot]
     void* d_work = nullptr;    // BatchWork[nwork]
+    void* d_slots = nullptr;   // BatchSlot[] of the y/z items
     int nwork = 0, threads = 0, blocks = 0, lanes = 0, L = 0;
     size_t smem = 0;
   } pl[2];
@@ -2666,6 +2668,7 @@ void free_persistent(fdtd_batch_t::Persistent (&pl)[2]) {
   for (auto& q : pl) {
     if (q.d_groups) cudaFree(q.d_groups);
     if (q.d_work) cudaFree(q.d_work);
+    if (q.d_slots) cudaFree(q.d_slots);
     q = fdtd_batch_t::Persistent();
   }
 }
@@ -2771,6 +2774,7 @@ int build_groups_t(fdtd_batch_t* b, const BatchCfg& cfg, std::vector<BatchGroup>
     for (auto& k : keys) {
       BatchGroup bg;
       bg.kind = k.kind;
+      bg.pn = k.pn;
       bg.L = k.L;
       bg.lanes = k.lanes;
       bg.P = k.P;
@@ -2893,7 +2897,10 @@ int launch_batch_group(const BatchGroup& g, cudaStream_t s) {
 // The persistent launches' shapes: (lanes, L) of the y/z lines (one for
 // both directions) with an instantiated kernel.
 // (FP64 fields: (16, 8) only; at L = 16 their solve needs more than the
-// 128 registers a 512-thread block leaves.)
+// 128 registers of two 256-thread blocks per SM.)  Blocks of 256 threads:
+// y/z tiles of at most 256 threads (P * lanes), i.e. lines of at most 128
+// cells at L = 8 and 256 at L = 16.
+constexpr int kPersistentThreads = 256;
 template <typename T>
 const void* persistent_fn(int lanes, int L) {
   if (lanes == 16 && L == 8) return (const void*)fdtd::proc_batch_persistent_kernel<T, 16, 8>;
@@ -2903,14 +2910,19 @@ const void* persistent_fn(int lanes, int L) {
 }
 
 // Work lists of the persistent launches, one per procedure slot, from the
-// groups built for the same shapes.  FDTD_ERR_UNSUPPORTED when the groups
-// do not fit one persistent kernel: y and z lines of different (lanes, L),
-// a shape without an instantiated kernel, or x lines of uniform media.
+// groups built for the same shapes.  The y/z tiles of every group are packed
+// into items of kPersistentThreads threads, best fit by free warps, largest
+// tiles first; the threads an item leaves over form its spare slot.
+// FDTD_ERR_UNSUPPORTED when the groups do not fit one persistent kernel:
+// y and z lines of different (lanes, L), a shape without an instantiated
+// kernel, uniform media (their y/z tiles may read coefficient tables, which
+// a spare slot of another segment count must not), or x lines not packed.
 template <typename T>
 int build_persistent_t(const std::vector<BatchGroup> (&gs)[2], fdtd_batch_t::Persistent (&out)[2]) {
   int lanes = 0, L = 0, maxtpt = 32;
   for (int slot = 0; slot < 2; ++slot)
     for (const auto& g : gs[slot]) {
+      if (!g.pn) return FDTD_ERR_UNSUPPORTED;
       if (g.kind == 2) {
         if (g.lpl != 8 && g.lpl != 16 && g.lpl != 32) return FDTD_ERR_UNSUPPORTED;
         continue;
@@ -2928,18 +2940,23 @@ int build_persistent_t(const std::vector<BatchGroup> (&gs)[2], fdtd_batch_t::Per
   }
   const void* fn = persistent_fn<T>(lanes, L);
   if (!fn) return FDTD_ERR_UNSUPPORTED;
-  const int threads = std::max(256, ((maxtpt + 31) / 32) * 32);
+  const int threads = kPersistentThreads;
+  if (maxtpt > threads) return FDTD_ERR_UNSUPPORTED;
+  const int warps = threads / 32;
   cudaFuncAttributes fa;
   BCK(cudaFuncGetAttributes(&fa, fn));
   if (threads > fa.maxThreadsPerBlock) return FDTD_ERR_UNSUPPORTED;
   int dev = 0, nsm = 1;
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  size_t smem = 0;
   for (int slot = 0; slot < 2; ++slot) {
     fdtd_batch_t::Persistent& q = out[slot];
     std::vector<fdtd::BatchGroupRef<T>> refs;
-    std::vector<fdtd::BatchWork> work_yz, work_x;
-    size_t smem = 0;
+    std::vector<fdtd::BatchWork> work, work_x;
+    std::vector<fdtd::BatchSlot> slots;
+    // y/z groups by tile size, largest first
+    std::vector<int> order;
     for (size_t gi = 0; gi < gs[slot].size(); ++gi) {
       const BatchGroup& g = gs[slot][gi];
       fdtd::BatchGroupRef<T> r{};
@@ -2950,35 +2967,59 @@ int build_persistent_t(const std::vector<BatchGroup> (&gs)[2], fdtd_batch_t::Per
       if (g.kind == 2) {
         r.kind = 1;
         r.lpl = g.lpl;
-        const int wpi = threads / 32;
-        const long long warps = (g.nitems + (32 / g.lpl) - 1) / (32 / g.lpl);
-        for (long long w0 = 0; w0 < warps; w0 += wpi) work_x.push_back({(int)gi, 0, w0});
+        const long long nw = (g.nitems + (32 / g.lpl) - 1) / (32 / g.lpl);
+        for (long long w0 = 0; w0 < nw; w0 += warps) work_x.push_back({(int)gi, 0, w0});
       } else {
-        const int tpt = g.P * g.lanes;
-        const int nslots = (threads + tpt - 1) / tpt;
         r.kind = 0;
         r.P = g.P;
-        r.G = std::max(1, threads / tpt);
-        smem = std::max(smem, fdtd::batch_params_bytes<T>(nslots) +
-                                  (size_t)nslots * 6 * (g.P | 1) * g.lanes * sizeof(T));
-        for (long long t0 = 0; t0 < g.nitems; t0 += r.G) work_yz.push_back({(int)gi, 0, t0});
+        order.push_back((int)gi);
       }
       refs.push_back(r);
     }
-    // the y/z items (their blocks run the longest) first
-    std::vector<fdtd::BatchWork> work = work_yz;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return gs[slot][a].P > gs[slot][b].P; });
+    struct Item {
+      std::vector<fdtd::BatchSlot> s;
+      int free;
+    };
+    std::vector<Item> items;
+    std::vector<std::vector<int>> open(warps + 1);  // items by free warps
+    for (int gi : order) {
+      const BatchGroup& g = gs[slot][gi];
+      const int need = g.P * g.lanes / 32;
+      for (long long t = 0; t < g.nitems; ++t) {
+        int it = -1;
+        for (int f = need; f < warps && it < 0; ++f)
+          if (!open[f].empty()) {
+            it = open[f].back();
+            open[f].pop_back();
+          }
+        if (it < 0) {
+          it = (int)items.size();
+          items.push_back({{}, warps});
+        }
+        Item& m = items[it];
+        m.s.push_back({gi, (int)t, (warps - m.free) * 32, need * 32, 0, 0});
+        m.free -= need;
+        if (m.free > 0) open[m.free].push_back(it);
+      }
+    }
+    for (Item& m : items) {
+      if (m.free > 0) m.s.push_back({m.s[0].group, -1, (warps - m.free) * 32, m.free * 32, 0, 0});
+      int coff = 0;
+      for (auto& b : m.s) {
+        b.coff = coff;
+        coff += 6 * ((b.tpt / lanes) | 1) * lanes;
+      }
+      smem = std::max(smem, fdtd::batch_params_bytes<T>((int)m.s.size()) + (size_t)coff * sizeof(T));
+      work.push_back({-1, (int)m.s.size(), (long long)slots.size()});
+      slots.insert(slots.end(), m.s.begin(), m.s.end());
+    }
     work.insert(work.end(), work_x.begin(), work_x.end());
-    if (smem > 227 * 1024) return FDTD_ERR_UNSUPPORTED;
-    if (smem > 48 * 1024) BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
-    if (per_sm < 1) return FDTD_ERR_UNSUPPORTED;
     q.threads = threads;
-    q.smem = smem;
     q.lanes = lanes;
     q.L = L;
     q.nwork = (int)work.size();
-    q.blocks = (int)std::min<long long>(std::max(1, q.nwork), (long long)nsm * per_sm);
     if (!refs.empty()) {
       BCK(dev_malloc(&q.d_groups, sizeof(fdtd::BatchGroupRef<T>) * refs.size()));
       BCK(cudaMemcpy(q.d_groups, refs.data(), sizeof(fdtd::BatchGroupRef<T>) * refs.size(), cudaMemcpyHostToDevice));
@@ -2987,6 +3028,19 @@ int build_persistent_t(const std::vector<BatchGroup> (&gs)[2], fdtd_batch_t::Per
       BCK(dev_malloc(&q.d_work, sizeof(fdtd::BatchWork) * work.size()));
       BCK(cudaMemcpy(q.d_work, work.data(), sizeof(fdtd::BatchWork) * work.size(), cudaMemcpyHostToDevice));
     }
+    if (!slots.empty()) {
+      BCK(dev_malloc(&q.d_slots, sizeof(fdtd::BatchSlot) * slots.size()));
+      BCK(cudaMemcpy(q.d_slots, slots.data(), sizeof(fdtd::BatchSlot) * slots.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  if (smem > 227 * 1024) return FDTD_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024) BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+  if (per_sm < 1) return FDTD_ERR_UNSUPPORTED;
+  for (auto& q : out) {
+    q.smem = smem;
+    q.blocks = (int)std::min<long long>(std::max(1, q.nwork), (long long)nsm * per_sm);
   }
   return FDTD_OK;
 }
@@ -2997,12 +3051,14 @@ int launch_persistent(const fdtd_batch_t::Persistent& q, int* counter, cudaStrea
   BCK(cudaMemsetAsync(counter, 0, sizeof(int), s));
   const auto* groups = (const fdtd::BatchGroupRef<T>*)q.d_groups;
   const auto* work = (const fdtd::BatchWork*)q.d_work;
+  const auto* slots = (const fdtd::BatchSlot*)q.d_slots;
   if (q.lanes == 16 && q.L == 8) {
-    fdtd::proc_batch_persistent_kernel<T, 16, 8><<<q.blocks, q.threads, q.smem, s>>>(groups, work, q.nwork, counter);
+    fdtd::proc_batch_persistent_kernel<T, 16, 8><<<q.blocks, q.threads, q.smem, s>>>(groups, work, slots, q.nwork,
+                                                                                      counter);
   } else if constexpr (sizeof(T) == 4) {
     if (q.lanes == 16 && q.L == 16)
-      fdtd::proc_batch_persistent_kernel<T, 16, 16><<<q.blocks, q.threads, q.smem, s>>>(groups, work, q.nwork,
-                                                                                         counter);
+      fdtd::proc_batch_persistent_kernel<T, 16, 16><<<q.blocks, q.threads, q.smem, s>>>(groups, work, slots,
+                                                                                         q.nwork, counter);
     else
       return FDTD_ERR_UNSUPPORTED;
   } else {

@@ -1466,37 +1466,14 @@ __host__ __device__ constexpr size_t batch_params_bytes(int G) {
   return ((sizeof(PairParams<T>) * (size_t)G + 15) / 16) * 16;
 }
 
-// The tiles of one block: slots of tpt = P * LANES threads (whole warps) from
-// thread 0 on, the first G of them holding tiles first .. first + G - 1;
-// slots past those (or past the last tile), including a last slot with
-// fewer than tpt threads, are spares that take part in the barriers with no
-// active lane.  Shared memory: nslots parameter copies, then nslots carry
-// buffers.
+// One tile of LANES lines on the tpt = P * LANES threads of one slot (whole
+// warps): tid is the thread's index in the slot, sh the slot's carry buffer,
+// p its grid's parameters (shared memory).  have = false: a spare slot that
+// passes the barriers of the solve with no active lane (no global access).
 template <typename T, int LANES, int L>
-__device__ __forceinline__ void strided_batch_block(const PairParams<T>* __restrict__ params,
-                                                    const BatchTile* __restrict__ tiles, int ntiles, int G, int tpt,
-                                                    int nslots, long long first, unsigned char* smem_raw) {
-  const int sub = threadIdx.x / tpt;
-  const int tid = threadIdx.x % tpt;
+__device__ __forceinline__ void strided_slot(const PairParams<T>& p, const BatchTile& tile, bool have, int tid,
+                                             int tpt, T* sh) {
   const int P = tpt / LANES;
-  const long long tix = first + sub;
-  const bool have = sub < G && tix < ntiles;
-  PairParams<T>* ps = reinterpret_cast<PairParams<T>*>(smem_raw);
-  {
-    // word copy of every slot's grid parameters (spare slots: the first tile's)
-    static_assert(sizeof(PairParams<T>) % 4 == 0, "word copy");
-    constexpr int W = (int)(sizeof(PairParams<T>) / 4);
-    for (int k = threadIdx.x; k < nslots * W; k += blockDim.x) {
-      const int sl = k / W;
-      const long long tx = first + sl;
-      const int grid = tiles[(sl < G && tx < ntiles) ? tx : first].grid;
-      reinterpret_cast<int*>(ps + sl)[k % W] = reinterpret_cast<const int*>(params + grid)[k % W];
-    }
-  }
-  __syncthreads();
-  const BatchTile tile = tiles[have ? tix : first];
-  const PairParams<T>& p = ps[sub];
-  T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(nslots)) + (size_t)sub * 6 * chain_stride(P) * LANES;
   const int lane = tid % LANES;
   const int s = tid / LANES;
   const int i = tile.x0 + lane;
@@ -1548,6 +1525,39 @@ __device__ __forceinline__ void strided_batch_block(const PairParams<T>* __restr
   else if (p.wall_fix) strided_solve_wall<T, LANES, L>(p, j0, s, P, lane, sh, E, H, hm1, y, win, tid, tpt);
   else strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, ib_prev, y, win, tid, tpt);
   if (active) strided_store<T, L>(p, base, j0, E, H, y, win);
+}
+
+// The tiles of one block: slots of tpt = P * LANES threads (whole warps) from
+// thread 0 on, the first G of them holding tiles first .. first + G - 1;
+// slots past those (or past the last tile), including a last slot with
+// fewer than tpt threads, are spares that take part in the barriers with no
+// active lane.  Shared memory: nslots parameter copies, then nslots carry
+// buffers.
+template <typename T, int LANES, int L>
+__device__ __forceinline__ void strided_batch_block(const PairParams<T>* __restrict__ params,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, int G, int tpt,
+                                                    int nslots, long long first, unsigned char* smem_raw) {
+  const int sub = threadIdx.x / tpt;
+  const int tid = threadIdx.x % tpt;
+  const int P = tpt / LANES;
+  const long long tix = first + sub;
+  const bool have = sub < G && tix < ntiles;
+  PairParams<T>* ps = reinterpret_cast<PairParams<T>*>(smem_raw);
+  {
+    // word copy of every slot's grid parameters (spare slots: the first tile's)
+    static_assert(sizeof(PairParams<T>) % 4 == 0, "word copy");
+    constexpr int W = (int)(sizeof(PairParams<T>) / 4);
+    for (int k = threadIdx.x; k < nslots * W; k += blockDim.x) {
+      const int sl = k / W;
+      const long long tx = first + sl;
+      const int grid = tiles[(sl < G && tx < ntiles) ? tx : first].grid;
+      reinterpret_cast<int*>(ps + sl)[k % W] = reinterpret_cast<const int*>(params + grid)[k % W];
+    }
+  }
+  __syncthreads();
+  const BatchTile tile = tiles[have ? tix : first];
+  T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(nslots)) + (size_t)sub * 6 * chain_stride(P) * LANES;
+  strided_slot<T, LANES, L>(ps[sub], tile, have, tid, tpt, sh);
 }
 
 template <typename T, int LANES, int L>
@@ -1805,16 +1815,27 @@ __global__ void proc_rows_batch_pn_kernel(const PairParams<T>* __restrict__ para
 // A whole procedure of a batch in one persistent launch
 // ---------------------------------------------------------------------------
 // The work of one procedure (its three pairs on every grid) is a list of
-// items, each a block's worth of one launch group: G tiles of a y/z group
-// (slots of P * LANES threads, as strided_batch_block), or blockDim / 32
+// items, each a block's worth of work: y/z tiles of per-node grids packed
+// into slots of P * LANES threads (tiles of different segment counts P side
+// by side; a last spare slot takes the threads left over), or blockDim / 32
 // warps of an x group of per-node grids (LPL lanes per line).  Every block
 // takes the next item from a counter (zeroed before the launch) until the
-// list is exhausted; all its threads see the same item and pass the same
-// barriers, and the loop ends after at most one pass over the list.
+// list is exhausted; every thread of the block belongs to exactly one slot
+// of a y/z item and runs the same solve code, so all pass the same barriers,
+// and the loop ends after at most one pass over the list.
 struct BatchWork {
-  int group;        // index into the launch's group table
+  int group;        // x items: the x group; y/z items: -1
+  int nslots;       // y/z items: slots of the item
+  long long first;  // x: first warp; y/z: first slot in the slot list
+};
+
+struct BatchSlot {
+  int group;  // y/z group of the tile (spare slot: that of slot 0)
+  int tile;   // tile index in the group; -1: the spare slot
+  int toff;   // first thread of the slot (slots ascend)
+  int tpt;    // threads of the slot: P * LANES
+  int coff;   // offset of its carry buffer (elements of T) after the parameter copies
   int pad;
-  long long first;  // y/z: first tile of the item; x: first warp
 };
 
 template <typename T>
@@ -1828,8 +1849,9 @@ struct BatchGroupRef {
 };
 
 template <typename T, int LANES, int L>
-__global__ void __launch_bounds__(512) proc_batch_persistent_kernel(const BatchGroupRef<T>* __restrict__ groups,
-                                                                     const BatchWork* __restrict__ work, int nwork,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && L == 8) ? 3 : 2) proc_batch_persistent_kernel(const BatchGroupRef<T>* __restrict__ groups,
+                                                                     const BatchWork* __restrict__ work,
+                                                                     const BatchSlot* __restrict__ slots, int nwork,
                                                                      int* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
@@ -1839,13 +1861,33 @@ __global__ void __launch_bounds__(512) proc_batch_persistent_kernel(const BatchG
     const int w = s_next;
     if (w >= nwork) break;  // the same value in every thread of the block
     const BatchWork item = work[w];
-    const BatchGroupRef<T> g = groups[item.group];
-    if (g.kind == 0) {
-      const int tpt = g.P * LANES;
-      const int nslots = ((int)blockDim.x + tpt - 1) / tpt;
-      strided_batch_block<T, LANES, L>(g.params, static_cast<const BatchTile*>(g.index), (int)g.nitems, g.G, tpt,
-                                       nslots, item.first, smem_raw);
+    if (item.group < 0) {
+      const BatchSlot* sl = slots + item.first;
+      const int ns = item.nslots;
+      int my = 0;
+      for (int k = 1; k < ns; ++k)
+        if ((int)threadIdx.x >= sl[k].toff) my = k;
+      PairParams<T>* ps = reinterpret_cast<PairParams<T>*>(smem_raw);
+      {
+        // word copy of every slot's grid parameters (the spare: slot 0's)
+        constexpr int W = (int)(sizeof(PairParams<T>) / 4);
+        for (int k = threadIdx.x; k < ns * W; k += blockDim.x) {
+          const int q = k / W;
+          const BatchSlot& b = sl[q].tile >= 0 ? sl[q] : sl[0];
+          const BatchGroupRef<T>& gq = groups[b.group];
+          const int grid = static_cast<const BatchTile*>(gq.index)[b.tile].grid;
+          reinterpret_cast<int*>(ps + q)[k % W] = reinterpret_cast<const int*>(gq.params + grid)[k % W];
+        }
+      }
+      __syncthreads();
+      const BatchSlot me = sl[my];
+      const bool have = me.tile >= 0;
+      const BatchSlot& src = have ? me : sl[0];
+      const BatchTile tile = static_cast<const BatchTile*>(groups[src.group].index)[src.tile];
+      T* sh = reinterpret_cast<T*>(smem_raw + batch_params_bytes<T>(ns)) + me.coff;
+      strided_slot<T, LANES, L>(ps[my], tile, have, (int)threadIdx.x - me.toff, me.tpt, sh);
     } else {
+      const BatchGroupRef<T> g = groups[item.group];
       const long long gwarp = item.first + (threadIdx.x >> 5);
       const long long* ls = static_cast<const long long*>(g.index);
       if (g.lpl == 8) rows_batch_pn_warp<T, 8, 8>(g.params, ls, g.ngrids, gwarp);

@@ -142,12 +142,13 @@ def test_tuner_cache_file(tmp_path, monkeypatch):
 
 def per_node_specs(seed):
     """Grids with eps_r blocks (per-node media) of uneven sizes: y lines up to
-    165 cells (22 segments of 8: 352-thread tiles), z lines up to 129, x lines
-    packed by 8, 16 and 32 lanes."""
+    121 cells and z lines up to 128 (16 segments of 8: 256-thread tiles, the
+    largest a persistent block takes), tiles of 2 to 16 segments packed side
+    by side, x lines packed by 8, 16 and 32 lanes."""
     rng = np.random.default_rng(seed)
     d = 1e-3
     out = []
-    for nx, ny, nz in [(40, 165, 6), (9, 7, 33), (70, 12, 20), (17, 33, 129), (6, 6, 5), (33, 40, 17),
+    for nx, ny, nz in [(40, 121, 6), (9, 7, 33), (70, 12, 20), (17, 33, 128), (6, 6, 5), (33, 40, 17),
                        (130, 10, 9)]:
         cfl = float(rng.uniform(2.0, 10.0))
         eps = W.eps_blocks(rng, nx, ny, nz, 1.0, 4.0)
@@ -200,7 +201,8 @@ def test_persistent_batch_matches_launch_groups(scheme, prec, shape):
 def test_batch_mode_tuned_and_persistent_limits():
     """mode "auto" times both modes on the batch's own data and keeps the
     faster; "persistent" on a batch whose x lines are not packed (uniform
-    media) is refused at the step."""
+    media), or whose lines need tiles of more than 256 threads, is refused
+    at the step."""
     from paper_2011_14043_gb300 import Batch, FdtdError
     specs = per_node_specs(71)
     sims = [make_sim(sp, "fadi", "f32") for sp in specs]
@@ -227,3 +229,16 @@ def test_batch_mode_tuned_and_persistent_limits():
     b.close()
     for sm in sims:
         sm.close()
+    spec = per_node_specs(73)[0]
+    nx, ny, nz, cfl, eps, u0 = spec
+    ny = 140  # 18 segments of 8 along y: a 288-thread tile
+    spec = (nx, ny, nz, cfl, np.ones((nz, ny, nx)) * 2.0 + (np.arange(nx) % 2), W.zero_fields(nx, ny, nz))
+    sims = [make_sim(spec, "fadi", "f32")]
+    b = Batch(sims)
+    b.set_config(y=(16, 8), z=(16, 8), x_pack=1)
+    b.set_mode("persistent")
+    with pytest.raises(FdtdError) as err:
+        b.step(1)
+    assert err.value.code == -6
+    b.close()
+    sims[0].close()
