@@ -255,9 +255,12 @@ def fp64_reference_fields(args, fields, steps):
     return out
 
 
-def run_e2e(args, prec, fields):
+def run_e2e(args, prec, fields, reps=3):
     """Same metric through the C ABI with pinned host buffers: H2D of the
-    initial fields, K steps, D2H of all six field components, all timed."""
+    initial fields, K steps, D2H of all six field components, all timed.
+    One untimed round first, then `reps` timed rounds (a fresh handle each);
+    the median is reported with every sample (the host-device link shows
+    sporadic stalls of several milliseconds)."""
     import numpy as np
     import torch
     from paper_2011_14043_gb300 import Simulation
@@ -271,19 +274,23 @@ def run_e2e(args, prec, fields):
         t.numpy()[...] = v.astype(np_dtype)
         host_in[c] = t
         host_out[c] = torch.empty(v.shape, dtype=t_dtype, pin_memory=True)
-    sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl, tune=tuple(args.tune))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for c in fields:
-        sim.set_field(c, host_in[c].numpy())
-    sim.step(args.steps)
-    for c in fields:
-        sim.get_field(c, out=host_out[c].numpy())
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    sim.close()
+    times = []
+    for r in range(reps + 1):
+        sim = Simulation(n, n, n, 1e-3, scheme="fadi", precision=prec, cfl=args.cfl, tune=tuple(args.tune))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in fields:
+            sim.set_field(c, host_in[c].numpy())
+        sim.step(args.steps)
+        for c in fields:
+            sim.get_field(c, out=host_out[c].numpy())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sim.close()
+        if r > 0:
+            times.append(t1 - t0)
     nbytes = sum(v.numel() * v.element_size() for v in host_in.values())
-    return {"s": t1 - t0, "h2d": nbytes, "d2h": nbytes}
+    return {"s": statistics.median(times), "samples_s": times, "h2d": nbytes, "d2h": nbytes}
 
 
 def replica_throughput(local_ms: float, units_per_rank: float, ws: int, device: str):
@@ -715,7 +722,10 @@ def main():
         e = run_e2e(args, "f32", fields)
         ev = ws * cells * args.steps / e["s"]
         line["e2e"] = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": e["h2d"] / args.steps,
-                       "d2h_bytes_per_step": e["d2h"] / args.steps}
+                       "d2h_bytes_per_step": e["d2h"] / args.steps,
+                       "timing": "median of 3 timed rounds after one untimed round, host clock around "
+                                 "set_field x6, step(K), get_field x6 with pinned buffers",
+                       "samples": [ws * cells * args.steps / t for t in e["samples_s"]]}
     if not args.no_batch:
         line["batch"] = batch_section(args)
     if not args.no_adjoint:
