@@ -102,11 +102,11 @@ FP64_FLOPS_PER_CELL_STEP = 42 + 30
 # What the kernels issue per cell-step, for context: per node of one pair,
 # RHS 1 sub + 1 FMA, forward sweep 1 FMA, forward carry fix 1 FMA, backward
 # sweep 1 mul + 1 FMA, backward carry fix 1 FMA, H update 1 sub + 1 FMA,
-# E update 1 mul + 1 FMA: 7 FMAs + 4 adds/muls = 18 flops (an FMA counts 2),
-# six pairs per step; the carry scans add about one flop per node.  The
+# E update 1 sub: 6 FMAs + 4 adds/muls = 16 flops (an FMA counts 2), six
+# pairs per step; the carry scans add about one flop per node.  The
 # reassociated (segmented) Thomas solve costs the carry-fix FMAs beyond the
 # method's count.
-KERNEL_FP64_FLOPS_PER_CELL_STEP = 6 * 18
+KERNEL_FP64_FLOPS_PER_CELL_STEP = 6 * 16
 
 
 def fp64_alu_roofline(cell_steps_per_s: float) -> dict:

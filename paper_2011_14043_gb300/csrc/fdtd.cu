@@ -796,6 +796,7 @@ fdtd::PairParams<T> make_params(const fdtd_t* h, const PairGeom& g, const PairCo
   p.kd = (T)(sgn * kd_mul * c.kd);
   p.alpha = (T)alpha;
   p.beta = (T)beta;
+  p.e_unit = (alpha == 1.0 && beta == -1.0) ? 1 : 0;
   p.tab = (const T*)c.tab;
   p.tlen = c.tlen;
   p.jc = c.jc;

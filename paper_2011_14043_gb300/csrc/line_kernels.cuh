@@ -82,6 +82,7 @@ struct PairParams {
   T kb;                  // uniform: RHS coupling s*b/d_eta
   T kd;                  // H update coupling s*d/d_eta
   T alpha, beta;         // E_out = alpha*w + beta*E_in
+  int e_unit;            // alpha = 1, beta = -1 (the procedure's E <- w - E)
   const T* tab;          // uniform: [TB_ROWS][tlen] hi/lo rows of 1/beta, m, c and the
                          // segment carry products PF, PB (zero beyond N and at walls)
   int tlen;
@@ -160,6 +161,35 @@ template <typename T>
 __device__ __forceinline__ T fma2(HiLo<T> a, T x, T b) {
   if constexpr (use_hilo<T>()) return fma(a.hi, x, fma(a.lo, x, b));
   else return fma(a.hi, x, b);
+}
+
+// E_out = alpha w + beta E of a segment.  FP64 fields: the procedure's own
+// E <- w - E (p.e_unit) is one subtraction; fma(1, w, -E) rounds w - E once,
+// exactly as the subtraction does, so both forms give the same bits, with
+// one FP64 instruction fewer per node where the FP64 pipe binds (the branch
+// is the same for every thread of a launch).  FP32 fields keep the fused form:
+// their kernels are bound by HBM, and the second path costs the x-line
+// kernel 8 registers and 6 % of its time.
+template <typename T, int L>
+__device__ __forceinline__ void e_next(const PairParams<T>& p, const T (&y)[L], const T (&E)[L], T (&En)[L]) {
+  if (sizeof(T) == 8 && p.e_unit) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) En[t] = y[t] - E[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) En[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void e_update(const PairParams<T>& p, const T (&y)[L], T (&E)[L]) {
+  if (sizeof(T) == 8 && p.e_unit) {
+#pragma unroll
+    for (int t = 0; t < L; ++t) E[t] = y[t] - E[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < L; ++t) E[t] = fma(p.alpha, y[t], p.beta * E[t]);
+  }
 }
 
 // Table rows of a homogeneous medium, each [tlen] long.
@@ -534,11 +564,13 @@ __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long 
   T* pe = p.e_out + base + (long long)j0 * p.ls;
   T* ph = p.h_out + base + (long long)j0 * p.ls;
   const long long ls = p.ls;
+  T En[L];
+  e_next<T, L>(p, y, E, En);
   if (j0 + L <= p.N) {
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
-      pe[t * ls] = fma(p.alpha, y[t], p.beta * E[t]);
+      pe[t * ls] = En[t];
       ph[t * ls] = fma(p.kd, wnext - y[t], H[t]);
     }
   } else {
@@ -546,7 +578,7 @@ __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long 
     for (int t = 0; t < L; ++t) {
       if (j0 + t < p.N) {
         const T wnext = (t + 1 < L) ? y[t + 1] : win;
-        pe[t * ls] = fma(p.alpha, y[t], p.beta * E[t]);
+        pe[t * ls] = En[t];
         ph[t * ls] = fma(p.kd, wnext - y[t], H[t]);
       }
     }
@@ -960,6 +992,8 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
     else
       strided_solve<T, LANES, L, false>(p, j0, s, P, lane, sh, E, H, hm1, qn, ibn, ibl, HiLo<T>{T(0), T(0)}, y,
                                       win);
+    T En[L];
+    e_next<T, L>(p, y, E, En);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const int j = j0 + t;
@@ -967,7 +1001,7 @@ __global__ void __launch_bounds__(LANES * ((256 + L - 1) / L), MINB)
         T eo = E[t], ho = H[t];
         if (active && j < N) {
           const T wnext = (t + 1 < L) ? y[t + 1] : win;
-          eo = fma(p.alpha, y[t], p.beta * E[t]);
+          eo = En[t];
           ho = fma(p.kd, wnext - y[t], H[t]);
         }
         oE[j * LANES + lane] = eo;
@@ -1099,14 +1133,14 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     const T win = warp_chain_backward<T>(y[0], pb);
     phase_fix<T, L, 2>(p, j0, win, ibn, ibl, y);
     // H update and subtraction below use y (= w) and win
-    T D[L];
+    T D[L], En[L];
+    e_next<T, L>(p, y, E, En);
 #pragma unroll
     for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
       H[t] = fma(p.kd, wnext - y[t], H[t]);
-      const T e_new = fma(p.alpha, y[t], p.beta * E[t]);
-      D[t] = E[t] - e_new;
-      E[t] = e_new;
+      D[t] = E[t] - En[t];
+      E[t] = En[t];
     }
     if (p.d_out && ok) {
       if (j0 + L <= N) {
@@ -1135,8 +1169,8 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
     for (int t = 0; t < L; ++t) {
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
       H[t] = fma(p.kd, wnext - y[t], H[t]);
-      E[t] = fma(p.alpha, y[t], p.beta * E[t]);
     }
+    e_update<T, L>(p, y, E);
   }
   // values beyond N are exactly zero, so whole segments inside the padded
   // row are stored as vectors; the segment holding the line end element-wise
@@ -1237,8 +1271,8 @@ __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, lon
   for (int t = 0; t < L; ++t) {
     const T wnext = (t + 1 < L) ? y[t + 1] : wnl;
     H[t] = fma(p.kd, wnext - y[t], H[t]);
-    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
   }
+  e_update<T, L>(p, y, E);
   if (!ok) return;
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
@@ -1688,8 +1722,8 @@ __global__ void proc_rows_lpl_kernel(const PairParams<T> p) {
   for (int t = 0; t < L; ++t) {
     const T wnext = (t + 1 < L) ? y[t + 1] : win;
     H[t] = fma(p.kd, wnext - y[t], H[t]);
-    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
   }
+  e_update<T, L>(p, y, E);
   if (!ok) return;
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
@@ -1787,8 +1821,8 @@ __device__ __forceinline__ void rows_batch_pn_warp(const PairParams<T>* __restri
   for (int t = 0; t < L; ++t) {
     const T wnext = (t + 1 < L) ? y[t + 1] : win;
     H[t] = fma(p.kd, wnext - y[t], H[t]);
-    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
   }
+  e_update<T, L>(p, y, E);
   if (!valid) return;
   if (full) {
     store_seg<T, L>(p.e_out + base + j0, E);
@@ -2028,13 +2062,15 @@ __global__ void proc_strided_gm_kernel(const PairParams<T> p) {
   const T win = block_chain_backward<T, LANES>(sh, P, PW, s, lane, y[0], pb, (int)threadIdx.x, (int)blockDim.x);
   gm_fix<T, L>(win, ibn, ibl, offh, offl, y);
   if (!active) return;
+  T En[L];
+  e_next<T, L>(p, y, E, En);
 #pragma unroll
   for (int t = 0; t < L; ++t) {
     const int j = j0 + t;
     if (j < N) {
       const long long at = base + (long long)j * ls;
       const T wnext = (t + 1 < L) ? y[t + 1] : win;
-      p.e_out[at] = fma(p.alpha, y[t], p.beta * E[t]);
+      p.e_out[at] = En[t];
       p.h_out[at] = fma(p.kd_scale * kd[t], wnext - y[t], H[t]);
     }
   }
@@ -2092,8 +2128,8 @@ __global__ void proc_rows_gm_kernel(const PairParams<T> p) {
   for (int t = 0; t < L; ++t) {
     const T wnext = (t + 1 < L) ? y[t + 1] : win;
     H[t] = fma(p.kd_scale * kd[t], wnext - y[t], H[t]);
-    E[t] = fma(p.alpha, y[t], p.beta * E[t]);
   }
+  e_update<T, L>(p, y, E);
   if (!ok) return;
   if (j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
