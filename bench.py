@@ -99,14 +99,13 @@ def recorded_traffic(kernel_class: str, n: int):
 # solves (5N per system of order N).  This is the basis of the FP64 form's
 # ALU roofline.
 FP64_FLOPS_PER_CELL_STEP = 42 + 30
-# What the kernels issue per cell-step, for context: per node of one pair,
-# RHS 1 sub + 1 FMA, forward sweep 1 FMA, forward carry fix 1 FMA, backward
-# sweep 1 mul + 1 FMA, backward carry fix 1 FMA, H update 1 sub + 1 FMA,
-# E update 1 sub: 6 FMAs + 4 adds/muls = 16 flops (an FMA counts 2), six
-# pairs per step; the carry scans add about one flop per node.  The
-# reassociated (segmented) Thomas solve costs the carry-fix FMAs beyond the
-# method's count.
-KERNEL_FP64_FLOPS_PER_CELL_STEP = 6 * 16
+# What the kernels issue per cell-step at 256^3, for context.  Per node of
+# an x-line pair (segmented solve): RHS 1 sub + 1 FMA, forward sweep 1 FMA,
+# forward carry fix 1 FMA, backward sweep 1 mul + 1 FMA, backward carry fix
+# 1 FMA, H update 1 sub + 1 FMA, E update 1 sub: 16 flops (an FMA counts 2);
+# per node of a y/z pair (one thread per line, no carry fixes or scans): 12.
+# Two x pairs and four y/z pairs per step.
+KERNEL_FP64_FLOPS_PER_CELL_STEP = 2 * 16 + 4 * 12
 
 
 def fp64_alu_roofline(cell_steps_per_s: float) -> dict:
@@ -122,7 +121,8 @@ def fp64_alu_roofline(cell_steps_per_s: float) -> dict:
             "flops_basis": "the method's count, Table I: 42 RHS/explicit + 30 tridiagonal per cell-step",
             "kernel_issued": {"flops_per_cell_step": KERNEL_FP64_FLOPS_PER_CELL_STEP, "achieved": issued,
                               "frac": issued / peak,
-                              "note": "FP64 flops the kernels issue (segmented Thomas with carry fixes)"}}
+                              "note": "FP64 flops the kernels issue at 256^3 (x lines: segmented Thomas with carry fixes; "
+                                      "y/z lines: one thread per line)"}}
 
 
 def measured_peaks():

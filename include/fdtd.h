@@ -91,7 +91,11 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * instead of being read in place by the unpacking kernel; tune[1] bit 9
  * set: with fourth-order differences every line takes the one-thread-per-
  * line kernel instead of the block-tiled kernel (FP32 fields, lines of at
- * most 512 cells; the same arithmetic, the same results). */
+ * most 512 cells; the same arithmetic, the same results); tune[1] bit 10
+ * set: lines along y and z of FP64 fields in homogeneous media (pairs of at
+ * least 4096 lines) take the segmented solve instead of one thread per line
+ * walking the Thomas recurrences (equal to rounding; the default needs a
+ * scratch of three field arrays, allocated at the first fdtd_step). */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of

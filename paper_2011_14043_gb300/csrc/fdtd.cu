@@ -134,6 +134,8 @@ struct fdtd_s {
   int order = 2;
   void* tmp4 = nullptr;             // order 4: field-shaped scratch of the line solves, one
                                     // per E component (pairs of a procedure run concurrently)
+  void* yseq = nullptr;             // FP64 y/z lines solved one thread per line: the forward
+                                    // values, one field-shaped array per E component
   double* sig_node[3] = {nullptr, nullptr, nullptr};  // per-node sigma at E samples (device)
   std::vector<double> sig_host[3];  // the same on the host, only while coefficients are built
   bool mu_var = false;              // per-node mu (general media kernels)
@@ -1257,6 +1259,30 @@ int launch_line4(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, int
   return FDTD_OK;
 }
 
+// FP64 y/z lines of homogeneous media (tables on every node), pairs of at
+// least kSeqMinLines lines, take one thread per line (proc_strided_seq_kernel)
+// once the scratch of its forward values exists (ensure_yseq, before the
+// first step); tune[1] bit 10 keeps the segmented kernel.  Measured: 256^3
+// (65,280 lines per pair) 8.5 G cell-steps/s against 7.4 G segmented; 128^3
+// (16,256 lines, under one block per SM) 6.5 G against 7.8 G.
+constexpr long long kSeqMinLines = 32768;
+bool seq_wanted(const fdtd_t* h) {
+  return h->prec == FDTD_F64 && !h->per_node && !h->mu_var && h->order == 2 && (h->desc.tune[1] & 1024) == 0;
+}
+
+template <typename T>
+bool seq_eligible(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
+  return seq_wanted(h) && h->yseq && !g.rows && p.nq == nullptr && p.nkd == nullptr && p.d_out == nullptr &&
+         p.tab != nullptr && g.N >= 2 && p.tables_only && g.n_lines() >= kSeqMinLines;
+}
+
+int ensure_yseq(fdtd_t* h) {
+  if (!seq_wanted(h) || h->yseq) return FDTD_OK;
+  CK(dev_malloc(&h->yseq, 3 * (size_t)h->count * h->esize));
+  CK(cudaMemsetAsync(h->yseq, 0, 3 * (size_t)h->count * h->esize, h->stream));
+  return FDTD_OK;
+}
+
 template <typename T>
 int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   if (g.empty()) return FDTD_OK;
@@ -1305,6 +1331,12 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
     // tiles with one block per SM equal)
     if constexpr (sizeof(T) == 4) {
       if (int rc = launch_strided_tma<T, 16, 2, 2>(h, g, p)) return rc;
+    }
+  } else if (sizeof(T) == 8 && seq_eligible(h, g, p)) {
+    if constexpr (sizeof(T) == 8) {
+      const long long nl = g.n_lines();
+      fdtd::proc_strided_seq_kernel<T><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(
+          p, (T*)h->yseq + (size_t)g.ec * h->count);
     }
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];
@@ -2231,6 +2263,7 @@ int fdtd_destroy(fdtd_t* h) {
   if (h->d_partial) cudaFree(h->d_partial);
   if (h->d_ref_partial) cudaFree(h->d_ref_partial);
   if (h->tmp4) cudaFree(h->tmp4);
+  if (h->yseq) cudaFree(h->yseq);
   if (h->d_err) cudaFree(h->d_err);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->g_run) cudaStreamSynchronize(h->g_run);
@@ -2499,7 +2532,9 @@ int fdtd_step(fdtd_t* h, int64_t nsteps) {
   NvtxScope range("fdtd_step");
   if (h->poisoned) return FDTD_ERR_STATE;
   if (nsteps == 0) return FDTD_OK;
-  int rc = scheme_init(h);
+  int rc = ensure_yseq(h);
+  if (rc) return rc;
+  rc = scheme_init(h);
   if (rc) return rc;
   if ((rc = take_invariant_ref(h))) return rc;
   if (h->per_node && !h->shape_tuned && h->desc.tune[0] == 0) {

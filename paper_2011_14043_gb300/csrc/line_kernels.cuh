@@ -557,6 +557,98 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
   }
 }
 
+// Lines along y or z of a homogeneous medium, FP64 fields: one thread per
+// line walks the strided axis (consecutive x on consecutive threads, every
+// access coalesced) through the plain Thomas recurrences with the tabulated
+// factors, the forward values in a field-shaped scratch array ys:
+//   y_j = r_j - m_j y_{j-1},   w_j = (1/beta_j) y_j - c_j w_{j+1},
+// then H_j += kd (w_{j+1} - w_j) and E_j <- alpha w_j + beta E_j as w_j
+// appears.  Per node 8 FP64 instructions against the segmented solve's 10
+// and its carry scans: the FP64 pipe binds these lines, and a launch of
+// 256 x 255 lines still keeps it busy.  Reads of E and H happen before any
+// write of the same line (in place is safe).  Chunks of SEQ_U = 8 nodes
+// (97 registers) measured faster than 16 (196 registers: 8.1 against 8.5 G
+// cell-steps/s at 256^3).
+template <typename T, int SEQ_U = 8>
+__global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<T> p, T* __restrict__ ys) {
+  const long long nl = p.lane_hi - p.lane_lo;
+  const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nl <= 0 || line >= nl * p.n_o) return;
+  const int i = p.lane_lo + (int)(line % nl);
+  const int o = p.o_lo + (int)(line / nl);
+  const long long base = (long long)o * p.os + i;
+  if (!strided_line_ok(p, base)) return;
+  const int N = p.N;
+  const long long ls = p.ls;
+  const T* tm = p.tab + TB_MH * p.tlen;
+  const T* tib = p.tab + TB_IBH * p.tlen;
+  const T* tc = p.tab + TB_CH * p.tlen;
+  // forward sweep over the unknowns 1 .. N-1 (nodes 0 and N are the walls),
+  // in chunks of U nodes whose loads are all issued before their arithmetic
+  // (the stores to ys may alias the field arrays as far as the compiler
+  // knows, so it would not move later loads above them)
+  constexpr int U = SEQ_U;
+  T hprev = p.h_in[base];
+  T yprev = T(0);
+  for (int j0 = 1; j0 < N; j0 += U) {
+    T hv[U], ev[U], mv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j < N) {
+        const long long at = base + (long long)j * ls;
+        hv[u] = p.h_in[at];
+        ev[u] = p.e_in[at];
+        mv[u] = __ldg(tm + j);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j < N) {
+        const T r = fma(p.kb, hv[u] - hprev, ev[u]);
+        hprev = hv[u];
+        const T y = fma(-mv[u], yprev, r);
+        ys[base + (long long)j * ls] = y;
+        yprev = y;
+      }
+    }
+  }
+  // backward sweep with the H and E updates of each node as its w appears
+  const bool unit = p.e_unit != 0;
+  T wnext = T(0);
+  for (int j1 = N - 1; j1 >= 1; j1 -= U) {
+    T yv[U], hv[U], ev[U], bv[U], cv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j1 - u;
+      if (j >= 1) {
+        const long long at = base + (long long)j * ls;
+        yv[u] = ys[at];
+        hv[u] = p.h_in[at];
+        ev[u] = p.e_in[at];
+        bv[u] = __ldg(tib + j);
+        cv[u] = __ldg(tc + j);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j1 - u;
+      if (j >= 1) {
+        const long long at = base + (long long)j * ls;
+        const T w = fma(yv[u], bv[u], -cv[u] * wnext);
+        p.h_out[at] = fma(p.kd, wnext - w, hv[u]);
+        p.e_out[at] = unit ? w - ev[u] : fma(p.alpha, w, p.beta * ev[u]);
+        wnext = w;
+      }
+    }
+  }
+  // face 0 (w_0 = 0) and the wall node 0
+  p.h_out[base] = fma(p.kd, wnext - T(0), p.h_in[base]);
+  const T e0 = p.e_in[base];
+  p.e_out[base] = unit ? T(0) - e0 : fma(p.alpha, T(0), p.beta * e0);
+}
+
 // H update, subtraction and store of one strided segment.
 template <typename T, int L>
 __device__ __forceinline__ void strided_store(const PairParams<T>& p, long long base, int j0, const T (&E)[L],
