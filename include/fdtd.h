@@ -92,8 +92,8 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * set: with fourth-order differences every line takes the one-thread-per-
  * line kernel instead of the block-tiled kernel (FP32 fields, lines of at
  * most 512 cells; the same arithmetic, the same results); tune[1] bit 10
- * set: lines along y and z of FP64 fields in homogeneous media (pairs of at
- * least 4096 lines) take the segmented solve instead of one thread per line
+ * set: lines along y and z of FP64 fields with uniform mu (pairs of at
+ * least 32768 lines) take the segmented solve instead of one thread per line
  * walking the Thomas recurrences (equal to rounding; the default needs a
  * scratch of three field arrays, allocated at the first fdtd_step). */
 typedef struct {

@@ -1259,21 +1259,24 @@ int launch_line4(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p, int
   return FDTD_OK;
 }
 
-// FP64 y/z lines of homogeneous media (tables on every node), pairs of at
-// least kSeqMinLines lines, take one thread per line (proc_strided_seq_kernel)
+// FP64 y/z lines (homogeneous media with the tables on every node, or
+// per-node media with uniform mu), pairs of at least kSeqMinLines lines, take
+// one thread per line (proc_strided_seq_kernel)
 // once the scratch of its forward values exists (ensure_yseq, before the
 // first step); tune[1] bit 10 keeps the segmented kernel.  Measured: 256^3
 // (65,280 lines per pair) 8.5 G cell-steps/s against 7.4 G segmented; 128^3
 // (16,256 lines, under one block per SM) 6.5 G against 7.8 G.
 constexpr long long kSeqMinLines = 32768;
 bool seq_wanted(const fdtd_t* h) {
-  return h->prec == FDTD_F64 && !h->per_node && !h->mu_var && h->order == 2 && (h->desc.tune[1] & 1024) == 0;
+  return h->prec == FDTD_F64 && !h->mu_var && h->order == 2 && (h->desc.tune[1] & 1024) == 0;
 }
 
 template <typename T>
 bool seq_eligible(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
-  return seq_wanted(h) && h->yseq && !g.rows && p.nq == nullptr && p.nkd == nullptr && p.d_out == nullptr &&
-         p.tab != nullptr && g.N >= 2 && p.tables_only && g.n_lines() >= kSeqMinLines;
+  if (!seq_wanted(h) || !h->yseq || g.rows || p.nkd != nullptr || p.d_out != nullptr || g.N < 2 ||
+      g.n_lines() < kSeqMinLines)
+    return false;
+  return p.nq != nullptr || (p.tab != nullptr && p.tables_only);
 }
 
 int ensure_yseq(fdtd_t* h) {
@@ -1335,8 +1338,11 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   } else if (sizeof(T) == 8 && seq_eligible(h, g, p)) {
     if constexpr (sizeof(T) == 8) {
       const long long nl = g.n_lines();
-      fdtd::proc_strided_seq_kernel<T><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(
-          p, (T*)h->yseq + (size_t)g.ec * h->count);
+      T* ys = (T*)h->yseq + (size_t)g.ec * h->count;
+      if (p.nq)
+        fdtd::proc_strided_seq_kernel<T, true><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(p, ys);
+      else
+        fdtd::proc_strided_seq_kernel<T, false><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(p, ys);
     }
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];

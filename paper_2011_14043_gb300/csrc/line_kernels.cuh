@@ -569,7 +569,7 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
 // write of the same line (in place is safe).  Chunks of SEQ_U = 8 nodes
 // (97 registers) measured faster than 16 (196 registers: 8.1 against 8.5 G
 // cell-steps/s at 256^3).
-template <typename T, int SEQ_U = 8>
+template <typename T, bool PER_NODE, int SEQ_U = 8>
 __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<T> p, T* __restrict__ ys) {
   const long long nl = p.lane_hi - p.lane_lo;
   const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -580,6 +580,9 @@ __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<
   if (!strided_line_ok(p, base)) return;
   const int N = p.N;
   const long long ls = p.ls;
+  // homogeneous media: tabulated m_j, 1/beta_j, c_j; per-node media (rows
+  // scaled by 1/b_j): r_j = q_j E_j + ks (H_j - H_{j-1}), m_j = off / beta_{j-1},
+  // c_j = off / beta_j from the per-node pivots, as in the segmented solve
   const T* tm = p.tab + TB_MH * p.tlen;
   const T* tib = p.tab + TB_IBH * p.tlen;
   const T* tc = p.tab + TB_CH * p.tlen;
@@ -590,8 +593,9 @@ __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<
   constexpr int U = SEQ_U;
   T hprev = p.h_in[base];
   T yprev = T(0);
+  T ibprev = PER_NODE ? p.nib[base] : T(0);
   for (int j0 = 1; j0 < N; j0 += U) {
-    T hv[U], ev[U], mv[U];
+    T hv[U], ev[U], mv[U], qv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u;
@@ -599,16 +603,29 @@ __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<
         const long long at = base + (long long)j * ls;
         hv[u] = p.h_in[at];
         ev[u] = p.e_in[at];
-        mv[u] = __ldg(tm + j);
+        if constexpr (PER_NODE) {
+          qv[u] = p.nq[at];
+          mv[u] = p.nib[at];  // 1/beta_j: m_{j+1} = off / beta_j
+        } else {
+          mv[u] = __ldg(tm + j);
+        }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u;
       if (j < N) {
-        const T r = fma(p.kb, hv[u] - hprev, ev[u]);
+        T r, m;
+        if constexpr (PER_NODE) {
+          r = fma(qv[u], ev[u], p.ks * (hv[u] - hprev));
+          m = p.offh * ibprev;
+          ibprev = mv[u];
+        } else {
+          r = fma(p.kb, hv[u] - hprev, ev[u]);
+          m = mv[u];
+        }
         hprev = hv[u];
-        const T y = fma(-mv[u], yprev, r);
+        const T y = fma(-m, yprev, r);
         ys[base + (long long)j * ls] = y;
         yprev = y;
       }
@@ -627,8 +644,12 @@ __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<
         yv[u] = ys[at];
         hv[u] = p.h_in[at];
         ev[u] = p.e_in[at];
-        bv[u] = __ldg(tib + j);
-        cv[u] = __ldg(tc + j);
+        if constexpr (PER_NODE) {
+          bv[u] = p.nib[at];
+        } else {
+          bv[u] = __ldg(tib + j);
+          cv[u] = __ldg(tc + j);
+        }
       }
     }
 #pragma unroll
@@ -636,7 +657,8 @@ __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<
       const int j = j1 - u;
       if (j >= 1) {
         const long long at = base + (long long)j * ls;
-        const T w = fma(yv[u], bv[u], -cv[u] * wnext);
+        const T c = PER_NODE ? p.offh * bv[u] : cv[u];
+        const T w = fma(yv[u], bv[u], -c * wnext);
         p.h_out[at] = fma(p.kd, wnext - w, hv[u]);
         p.e_out[at] = unit ? w - ev[u] : fma(p.alpha, w, p.beta * ev[u]);
         wnext = w;

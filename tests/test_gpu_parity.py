@@ -435,27 +435,30 @@ def test_lines_past_the_limit_are_rejected(dims, code):
     sim.close()
 
 
+@pytest.mark.parametrize("media", ["uniform", "blocks"])
 @pytest.mark.parametrize("scheme", ["fadi", "flod", "fss", "flod2"])
-def test_fp64_sequential_lines_match_segmented_solve(scheme):
+def test_fp64_sequential_lines_match_segmented_solve(scheme, media):
     """FP64 y and z lines of homogeneous media (pairs of at least 32768
     lines): one thread per line walking the Thomas recurrences against the
     segmented solve (tune[1] bit 10), equal to a few roundings, and against
     the oracle to 1e-12; ragged sizes, node chunks of 8 with a ragged last
-    chunk (lines of 130 and 90 cells)."""
+    chunk (lines of 130 and 90 cells); uniform eps_r (tabulated factors) and
+    eps_r blocks (per-node pivots)."""
     from paper_2011_14043_gb300 import Simulation
     nx, ny, nz = 400, 130, 90
     d = (1e-3, 0.9e-3, 1.2e-3)
     g = G.Grid(nx, ny, nz, *d)
     dt = 5.0 * g.dt_cfl()
     u0 = random_fields(nx, ny, nz, seed=31)
+    eps = np.full((nz, ny, nx), 1.7) if media == "uniform" else W.eps_blocks(5, nx, ny, nz, 1.0, 6.0)
     out = {}
     for tune in ((0, 0), (0, 1024)):
         sim = Simulation(nx, ny, nz, *d, scheme=scheme, precision="f64", dt=dt, tune=tune)
-        sim.set_material(np.full((nz, ny, nx), 1.7))
+        sim.set_material(eps)
         sim.set_fields(u0)
         sim.step(4)
         out[tune] = {c: sim.get_field(c) for c in G.COMPS}
         sim.close()
     assert energy_norm_rel(out[(0, 0)], out[(0, 1024)]) <= 1e-13
-    ref, _, _ = S.run_fundamental(S.Problem(g, dt, eps_r_cell=np.full((nz, ny, nx), 1.7)), scheme, u0, 4)
+    ref, _, _ = S.run_fundamental(S.Problem(g, dt, eps_r_cell=eps), scheme, u0, 4)
     assert energy_norm_rel(out[(0, 0)], ref) <= 1e-12
