@@ -1306,6 +1306,14 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
   h->launches++;
   if (h->order == 4) {
     launch_line4_raw<T>(h, g, p, 0);
+  } else if (sizeof(T) == 8 && seq_eligible(h, g, p)) {
+    if constexpr (sizeof(T) == 8) {
+      const long long nl = g.n_lines();
+      T* ys = (T*)h->yseq + (size_t)g.ec * h->count;
+      const unsigned blocks = (unsigned)((nl + 127) / 128);
+      if (p.nq) fdtd::proc_strided_seq_kernel<T, true><<<blocks, 128, 0, h->stream>>>(p, ys);
+      else fdtd::proc_strided_seq_kernel<T, false><<<blocks, 128, 0, h->stream>>>(p, ys);
+    }
   } else if (sizeof(T) == 8 && g.rows && rows_lanes(h, g) < 32) {
     if constexpr (sizeof(T) == 8) launch_rows_lpl<T>(h, g, p, rows_lanes(h, g));
   } else if (sizeof(T) == 4 && rows_tma_eligible(h, g) && p.e_in == (const T*)h->f[g.ec] &&
@@ -1334,15 +1342,6 @@ int launch_pair(fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>& p) {
     // tiles with one block per SM equal)
     if constexpr (sizeof(T) == 4) {
       if (int rc = launch_strided_tma<T, 16, 2, 2>(h, g, p)) return rc;
-    }
-  } else if (sizeof(T) == 8 && seq_eligible(h, g, p)) {
-    if constexpr (sizeof(T) == 8) {
-      const long long nl = g.n_lines();
-      T* ys = (T*)h->yseq + (size_t)g.ec * h->count;
-      if (p.nq)
-        fdtd::proc_strided_seq_kernel<T, true><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(p, ys);
-      else
-        fdtd::proc_strided_seq_kernel<T, false><<<(unsigned)((nl + 127) / 128), 128, 0, h->stream>>>(p, ys);
     }
   } else {
     const StridedCfg& cfg = h->strided_cfg[g.axis == AX_Y ? 0 : 1];

@@ -568,7 +568,8 @@ __device__ __forceinline__ void strided_solve_wall(const PairParams<T>& p, int j
 // 256 x 255 lines still keeps it busy.  Reads of E and H happen before any
 // write of the same line (in place is safe).  Chunks of SEQ_U = 8 nodes
 // (97 registers) measured faster than 16 (196 registers: 8.1 against 8.5 G
-// cell-steps/s at 256^3).
+// cell-steps/s at 256^3).  x lines keep the segmented solve: a thread per
+// row, its lanes a row pitch apart, measured slower (6.6 against 8.4 G).
 template <typename T, bool PER_NODE, int SEQ_U = 8>
 __global__ void __launch_bounds__(128) proc_strided_seq_kernel(const PairParams<T> p, T* __restrict__ ys) {
   const long long nl = p.lane_hi - p.lane_lo;

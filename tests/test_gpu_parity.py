@@ -438,12 +438,11 @@ def test_lines_past_the_limit_are_rejected(dims, code):
 @pytest.mark.parametrize("media", ["uniform", "blocks"])
 @pytest.mark.parametrize("scheme", ["fadi", "flod", "fss", "flod2"])
 def test_fp64_sequential_lines_match_segmented_solve(scheme, media):
-    """FP64 y and z lines of homogeneous media (pairs of at least 32768
-    lines): one thread per line walking the Thomas recurrences against the
-    segmented solve (tune[1] bit 10), equal to a few roundings, and against
-    the oracle to 1e-12; ragged sizes, node chunks of 8 with a ragged last
-    chunk (lines of 130 and 90 cells); uniform eps_r (tabulated factors) and
-    eps_r blocks (per-node pivots)."""
+    """FP64 y and z lines in pairs of at least 32768 lines: one thread per
+    line walking the Thomas recurrences against the segmented solve (tune[1]
+    bit 10), equal to a few roundings, and against the oracle to 1e-12;
+    lines of 130 and 90 cells, node chunks of 8 with a ragged last chunk;
+    uniform eps_r (tabulated factors) and eps_r blocks (per-node pivots)."""
     from paper_2011_14043_gb300 import Simulation
     nx, ny, nz = 400, 130, 90
     d = (1e-3, 0.9e-3, 1.2e-3)
