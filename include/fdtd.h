@@ -95,7 +95,10 @@ typedef enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, 
  * set: lines along y and z of FP64 fields with uniform mu (pairs of at
  * least 32768 lines) take the segmented solve instead of one thread per line
  * walking the Thomas recurrences (equal to rounding; the default needs a
- * scratch of three field arrays, allocated at the first fdtd_step). */
+ * scratch of three field arrays, allocated at the first fdtd_step); tune[1]
+ * bit 11 set: lines along x of exactly 32 L cells (FP32, homogeneous media,
+ * wall-corrected) keep the kernel with end-of-line masks instead of the one
+ * without them (the same results). */
 typedef struct {
   int32_t nx, ny, nz;        /* cells per axis: 2 <= nx <= 1024, 2 <= ny, 1 <= nz; lines
                                 along y and z are solved with at most 32 segments of

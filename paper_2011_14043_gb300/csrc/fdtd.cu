@@ -856,6 +856,9 @@ void launch_rows_L(const fdtd_t* h, const PairGeom& g, const fdtd::PairParams<T>
   const unsigned blocks = (unsigned)((nl + wpb - 1) / wpb);
   if (per_node)
     fdtd::proc_rows_kernel<T, L, true><<<blocks, wpb * 32, 0, h->stream>>>(p);
+  else if (sizeof(T) == 4 && L >= 2 && p.wall_fix && g.N == 32 * L && (h->desc.tune[1] & 2048) == 0)
+    fdtd::proc_rows_kernel<T, L, false, (sizeof(T) == 4 && L >= 2), (sizeof(T) == 4 && L >= 2)>
+        <<<blocks, wpb * 32, 0, h->stream>>>(p);
   else if (sizeof(T) == 4 && L >= 2 && p.wall_fix)
     fdtd::proc_rows_kernel<T, L, false, (sizeof(T) == 4 && L >= 2)><<<blocks, wpb * 32, 0, h->stream>>>(p);
   else

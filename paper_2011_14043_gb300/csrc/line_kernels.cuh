@@ -1317,7 +1317,7 @@ __device__ __forceinline__ void row_solve_store(const PairParams<T>& p, long lon
 // unknown: their right-hand side is zero, their factors 1/beta and c zero,
 // and node 0 is set to zero after the solve.  The result equals the
 // table-factor solve up to rounding (not bit for bit).
-template <typename T, int L>
+template <typename T, int L, bool FULL_LINE = false>
 __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, long long line, T (&E)[L],
                                                      T (&H)[L]) {
   const unsigned FULL = 0xffffffffu;
@@ -1345,7 +1345,11 @@ __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, lon
     const int j = j0 + t;
     T r = fma(p.kb, H[t] - hprev, E[t]);
     hprev = H[t];
-    r = (j == 0 || j >= N) ? T(0) : r;
+    if constexpr (FULL_LINE) {
+      if (t == 0) r = (lane == 0) ? T(0) : r;  // node 0: the wall
+    } else {
+      r = (j == 0 || j >= N) ? T(0) : r;
+    }
     y[t] = (t == 0) ? r : fma2(HiLo<T>{-m.hi, -m.lo}, y[t - 1], r);
   }
   const T yin = warp_chain_forward<T>(y[L - 1], HiLo<T>{p.qf[0][L - 1], p.qf[1][L - 1]});
@@ -1354,11 +1358,11 @@ __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, lon
   // backward sweep; nodes >= N hold w = 0 and do not couple (masks by
   // selects: one code path keeps the kernel at 48 registers, where two
   // paths needed 64 and ran slower)
-  const bool full = j0 + L <= N;
+  const bool full = FULL_LINE || j0 + L <= N;
   T wn = T(0);
 #pragma unroll
   for (int t = L - 1; t >= 0; --t) {
-    const bool in = j0 + t < N;
+    const bool in = FULL_LINE || j0 + t < N;
     const T ch = in ? c.hi : T(0), cl = in ? c.lo : T(0);
     const T ih = in ? ib.hi : T(0), il = in ? ib.lo : T(0);
     T u;
@@ -1389,7 +1393,7 @@ __device__ __forceinline__ void row_solve_store_wall(const PairParams<T>& p, lon
   }
   e_update<T, L>(p, y, E);
   if (!ok) return;
-  if (j0 + L <= N) {
+  if (FULL_LINE || j0 + L <= N) {
     store_seg<T, L>(p.e_out + base + j0, E);
     store_seg<T, L>(p.h_out + base + j0, H);
   } else if (j0 < N) {
@@ -1414,7 +1418,7 @@ __device__ __forceinline__ void row_solve_store_uniform(const PairParams<T>& p, 
 
 // Load this lane's segment of x line `line` (zeros past the line end).
 // Segments never run past the padded row (the row pitch is >= 32*L).
-template <typename T, int L, bool PER_NODE>
+template <typename T, int L, bool PER_NODE, bool FULL_LINE = false>
 __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line, T (&E)[L], T (&H)[L],
                                          T (&qn)[L], T (&ibn)[L], T (&ibl)[L]) {
   const int lane = threadIdx.x & 31;
@@ -1430,7 +1434,7 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
     ibn[t] = T(0);
     ibl[t] = T(0);
   }
-  if (j0 < p.N && row_ok<T, L>(p, base)) {  // lanes wholly past the line end touch no memory
+  if ((FULL_LINE || j0 < p.N) && row_ok<T, L>(p, base)) {  // lanes wholly past the line end touch no memory
     load_seg<T, L>(p.e_in + base + j0, E);
     load_seg<T, L>(p.h_in + base + j0, H);
     if constexpr (PER_NODE) {
@@ -1439,29 +1443,33 @@ __device__ __forceinline__ void row_load(const PairParams<T>& p, long long line,
       if constexpr (use_hilo<T>()) load_seg<T, L>(p.nibl + base + j0, ibl);
     }
   }
+  if constexpr (!FULL_LINE) {
 #pragma unroll
-  for (int t = 0; t < L; ++t) {
-    if (j0 + t >= p.N) {
-      E[t] = T(0);
-      H[t] = T(0);
-      qn[t] = T(0);
-      ibn[t] = T(0);
-      ibl[t] = T(0);
+    for (int t = 0; t < L; ++t) {
+      if (j0 + t >= p.N) {
+        E[t] = T(0);
+        H[t] = T(0);
+        qn[t] = T(0);
+        ibn[t] = T(0);
+        ibl[t] = T(0);
+      }
     }
   }
 }
 
 // One warp per x line.  WALL: homogeneous media with the rank-one wall
 // correction (p.wall_fix), a separate instantiation so that each path gets
-// its own register allocation.
-template <typename T, int L, bool PER_NODE, bool WALL = false>
+// its own register allocation.  FULL_LINE (with WALL): lines of exactly 32 L
+// cells, where every lane's nodes lie inside the line, so the end-of-line
+// masks go (the same arithmetic on every node that the masked path keeps).
+template <typename T, int L, bool PER_NODE, bool WALL = false, bool FULL_LINE = false>
 __global__ void proc_rows_kernel(const PairParams<T> p) {
   const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (line >= (long long)p.n_o * p.n_o2) return;  // whole warp leaves together
   T E[L], H[L], qn[L], ibn[L], ibl[L];
-  row_load<T, L, PER_NODE>(p, line, E, H, qn, ibn, ibl);
+  row_load<T, L, PER_NODE, FULL_LINE>(p, line, E, H, qn, ibn, ibl);
   if constexpr (PER_NODE) row_solve_store<T, L, true>(p, line, E, H, qn, ibn, ibl);
-  else if constexpr (WALL) row_solve_store_wall<T, L>(p, line, E, H);
+  else if constexpr (WALL) row_solve_store_wall<T, L, FULL_LINE>(p, line, E, H);
   else row_solve_store<T, L, false>(p, line, E, H, qn, ibn, ibl);
 }
 

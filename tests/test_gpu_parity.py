@@ -461,3 +461,25 @@ def test_fp64_sequential_lines_match_segmented_solve(scheme, media):
     assert energy_norm_rel(out[(0, 0)], out[(0, 1024)]) <= 1e-13
     ref, _, _ = S.run_fundamental(S.Problem(g, dt, eps_r_cell=eps), scheme, u0, 4)
     assert energy_norm_rel(out[(0, 0)], ref) <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["fadi", "fss"])
+def test_full_x_lines_without_masks_bit_identical(scheme):
+    """FP32 x lines of exactly 32 L cells (here 256 = 32 x 8) in homogeneous
+    media run the wall-corrected kernel without end-of-line masks; with
+    tune[1] bit 11 they keep the masked kernel: the same arithmetic on every
+    node, so the fields agree to the last bit."""
+    from paper_2011_14043_gb300 import Simulation
+    nx, ny, nz = 256, 20, 17
+    g = G.Grid(nx, ny, nz, 1e-3, 1e-3, 1e-3)
+    dt = 4.0 * g.dt_cfl()
+    u0 = random_fields(nx, ny, nz, seed=44)
+    out = []
+    for tune in ((0, 0), (0, 2048)):
+        sim = Simulation(nx, ny, nz, 1e-3, scheme=scheme, precision="f32", dt=dt, tune=tune)
+        sim.set_fields(u0)
+        sim.step(5)
+        out.append({c: sim.get_field(c) for c in G.COMPS})
+        sim.close()
+    for c in G.COMPS:
+        assert np.array_equal(out[0][c], out[1][c]), c
